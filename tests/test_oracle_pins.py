@@ -1,0 +1,394 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle (top_oracle.c through oracle.capi) against
+something other than itself: exact closed forms, the centralised optimum
+that the CADMM fixed point must equal (Sec. III-D.2: the CADMM solution
+space contains the optimum and ADMM converges to it), projections'
+defining properties, KKT certificates built from independent numpy
+matrices, and a long double re-run for the oracle's own rounding.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import centralized as CZ
+from paper_2507_10290_gb300 import workloads as W
+
+GOLDEN = __file__.rsplit("/", 1)[0] + "/golden/rest_to_rest_min_snap.txt"
+
+
+def scaled_relerr(c, ref, T):
+    """||c - ref|| / ||ref|| on time-normalised coefficients c_k T_i^k."""
+    sc = np.asarray(T)[:, None, None] ** np.arange(8)[None, None, :]
+    return float(np.linalg.norm((c - ref) * sc) / np.linalg.norm(ref * sc))
+
+
+def read_golden():
+    vals = {}
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        key, *rest = line.split()
+        vals[key] = rest
+    return vals
+
+
+# ---------------------------------------------------------------- P1 ----
+
+def test_golden_rest_to_rest_closed_form_exact():
+    """The golden smootherstep polynomial meets the 8 rest boundary conditions
+    and its snap integral / speed ratio are the stated exact constants."""
+    g = read_golden()
+    s = [Fraction(int(x)) for x in g["coeffs"]]
+
+    def deriv(poly, r):
+        out = list(poly)
+        for _ in range(r):
+            out = [k * out[k] for k in range(1, len(out))]
+        return out
+
+    def ev(poly, t):
+        return sum(ck * t ** k for k, ck in enumerate(poly))
+
+    for r in range(4):
+        assert ev(deriv(s, r), Fraction(0)) == (0 if r else 0)
+        assert ev(deriv(s, r), Fraction(1)) == (1 if r == 0 else 0)
+    snap = deriv(s, 4)
+    sq = [Fraction(0)] * (2 * len(snap) - 1)
+    for i, a in enumerate(snap):
+        for j, b in enumerate(snap):
+            sq[i + j] += a * b
+    integral = sum(ck / (k + 1) for k, ck in enumerate(sq))
+    assert integral == Fraction(int(g["snap_integral"][0]))
+    vel = deriv(s, 1)
+    assert ev(vel, Fraction(1, 2)) / 1 == Fraction(g["peak_to_mean_speed"][0])
+    # s'(tau) = 140 tau^3 (1 - tau)^3 >= 0: the peak is at tau = 1/2
+    assert vel == [0, 0, 0, 140, -420, 420, -140]
+
+
+@pytest.mark.parametrize("mode", ["pin", "free"])
+def test_p1_single_segment_matches_closed_form(mode):
+    g = read_golden()
+    s = np.array([float(x) for x in g["coeffs"]])
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        P = rng.uniform(-5, 5, size=(2, 3))
+        T = rng.uniform(0.6, 1.8)
+        w = W.tiny(N=1, mode=mode).with_(
+            waypoints=P, durations=np.array([T]),
+            start_state=np.concatenate([P[None, :1], np.zeros((1, 3, 3))], axis=1),
+            end_state=np.concatenate([P[None, 1:], np.zeros((1, 3, 3))], axis=1),
+            rho=1e5 / T ** 7, max_iters=500)
+        r = oracle.solve(w)
+        d = P[1] - P[0]
+        ref = np.zeros((1, 3, 8))
+        for a in range(3):
+            ref[0, a] = d[a] * s / T ** np.arange(8)
+            ref[0, a, 0] += P[0, a]
+        assert scaled_relerr(r["coeffs"], ref, [T]) < 1e-11
+        J_ref = float(g["snap_integral"][0]) * float(d @ d) / T ** 7
+        assert abs(r["cost"][0] - J_ref) <= 1e-10 * J_ref
+
+
+# ----------------------------------------------------- centralised aids ----
+
+def test_centralized_solvers_agree_and_meet_conditions():
+    w = W.tiny(seed=3, N=6, mode="pin", T_range=(0.5, 1.5))
+    P, T, s0, s1 = w.waypoints, w.durations, w.start_state[0], w.end_state[0]
+    c = CZ.pin_spline(P, T, s0, s1)
+    # interpolation, boundary orders 0..3 and C^6 continuity
+    for a in range(3):
+        for r in range(4):
+            assert abs(c[0, a] @ CZ.deriv_row(r, 0) - s0[r, a]) < 1e-9
+            assert abs(c[-1, a] @ CZ.deriv_row(r, T[-1]) - s1[r, a]) < 1e-9
+        for j in range(1, len(T)):
+            assert abs(c[j, a] @ CZ.deriv_row(0, 0) - P[j, a]) < 1e-9
+            for r in range(7):
+                left = c[j - 1, a] @ CZ.deriv_row(r, T[j - 1])
+                right = c[j, a] @ CZ.deriv_row(r, 0)
+                assert abs(left - right) < 1e-7 * max(1, abs(left))
+    kk, _ = CZ.kkt_qp(P, T, s0, s1, "pin")
+    assert scaled_relerr(kk, c, T) < 1e-7
+    f = CZ.free_polynomial(T, s0, s1)
+    kk, _ = CZ.kkt_qp(P, T, s0, s1, "free")
+    assert scaled_relerr(kk, f, T) < 1e-7
+    # single segment: both equal the closed-form smootherstep
+    g = read_golden()
+    sm = np.array([float(x) for x in g["coeffs"]])
+    d = P[-1] - P[0]
+    for sol in (CZ.pin_spline(P[[0, -1]], T[:1], s0, s1), CZ.free_polynomial(T[:1], s0, s1)):
+        ref = np.zeros((1, 3, 8))
+        for a in range(3):
+            ref[0, a] = d[a] * sm / T[0] ** np.arange(8)
+            ref[0, a, 0] += P[0, a]
+        assert scaled_relerr(sol, ref, T[:1]) < 1e-12
+
+
+# ---------------------------------------------------------------- P2/P3 --
+
+def test_p2_pin_mode_converges_to_spline():
+    w = W.tiny(seed=1, N=2, mode="pin", T_range=(0.8, 1.6)).with_(rho=1.0, max_iters=300000)
+    r = oracle.solve(w)
+    ref = CZ.pin_spline(w.waypoints, w.durations, w.start_state[0], w.end_state[0])
+    assert scaled_relerr(r["coeffs"], ref, w.durations) < 1e-6
+
+
+def test_p3_free_mode_converges_to_single_polynomial():
+    w = W.tiny(seed=1, N=8, mode="free", T_range=(0.8, 1.6)).with_(rho=1.0, max_iters=20000)
+    r = oracle.solve(w)
+    ref = CZ.free_polynomial(w.durations, w.start_state[0], w.end_state[0])
+    assert scaled_relerr(r["coeffs"], ref, w.durations) < 1e-10
+    J = CZ.segment_cost(ref, w.durations)
+    assert abs(r["cost"][0] - J) < 1e-9 * J
+
+
+# ---------------------------------------------------------------- P5/P6 --
+
+def _box_instance():
+    """Tiny FREE instance whose box limit is 80% of the unconstrained peak axis speed."""
+    w = W.tiny(seed=5, N=3, mode="free", T_range=(0.9, 1.3), step=2.0)
+    free = CZ.free_polynomial(w.durations, w.start_state[0], w.end_state[0])
+    M = 2
+    peak = max(abs(free[i, a] @ CZ.deriv_row(1, (j + 1) * w.durations[i] / M))
+               for i in range(3) for a in range(3) for j in range(M))
+    return w.with_(M_box=M, vbox=np.array([0.8 * peak]), rho=10.0, max_iters=100000)
+
+
+def test_p5_box_constrained_matches_active_set_qp():
+    w = _box_instance()
+    P, T = w.waypoints, w.durations
+    c_ref, act = CZ.active_set_qp(P, T, w.start_state[0], w.end_state[0], "free", w.M_box,
+                                  float(w.vbox[0]))
+    assert c_ref is not None and len(act) > 0, "the instance must have active box rows"
+    r = oracle.solve(w)
+    assert scaled_relerr(r["coeffs"], c_ref, T) < 1e-6
+
+
+def test_p6_kkt_certificate_of_converged_box_problem():
+    w = _box_instance()
+    r = oracle.solve(w, state=True)
+    T, rho, M = w.durations, w.rho, w.M_box
+    N = len(T)
+    c = r["coeffs"]
+    scale = 0.0
+    for i in range(N):
+        Mt = np.zeros((42, 24))
+        E = np.ones(42)
+        for a in range(3):
+            for side in range(2):
+                for rr in range(7):
+                    row = a * 14 + side * 7 + rr
+                    Mt[row, a * 8:(a + 1) * 8] = CZ.deriv_row(rr, T[i] if side else 0.0)
+                    if (side == 0 and i == 0 or side == 1 and i == N - 1) and rr >= 4:
+                        E[row] = 0
+        Ao, b = [], []
+        for j in range(1, M + 1):
+            for a in range(3):
+                for sg in (1.0, -1.0):
+                    row = np.zeros(24)
+                    row[a * 8:(a + 1) * 8] = sg * CZ.deriv_row(1, j * T[i] / M)
+                    Ao.append(row); b.append(float(w.vbox[0]))
+        Ao, b = np.array(Ao), np.array(b)
+        Qt = np.zeros((24, 24))
+        for a in range(3):
+            Qt[a * 8:(a + 1) * 8, a * 8:(a + 1) * 8] = CZ.snap_gram(T[i])
+        ci = c[i].reshape(24)
+        mu = rho * r["v"][i]
+        stat = 2 * Qt @ ci + rho * Mt.T @ (E * r["u"][i]) + Ao.T @ mu
+        scale = max(scale, float(np.abs(2 * Qt @ ci).max()))
+        assert np.abs(stat).max() < 1e-6 * scale
+        assert mu.min() > -1e-9 * scale                       # dual feasibility
+        assert (Ao @ ci - b).max() < 1e-7                     # primal feasibility
+        assert np.abs(mu * (Ao @ ci - b)).max() < 1e-6 * scale  # complementarity
+    # consensus stationarity: the two sides' multipliers cancel at free rows
+    u = r["u"]
+    for j in range(1, N):
+        for a in range(3):
+            end = u[j - 1, a * 14 + 7: a * 14 + 14]
+            start = u[j, a * 14: a * 14 + 7]
+            assert np.abs(end + start).max() < 1e-9 * max(1, np.abs(end).max())
+
+
+# ---------------------------------------------------------------- P7 ----
+
+def test_p7_ball_projection_properties():
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        o = rng.normal(size=3) if rng.random() < 0.7 else None
+        rad = rng.uniform(0.2, 3.0)
+        q1, q2 = rng.normal(scale=3.0, size=(2, 3))
+        p1 = oracle.project_ball(q1, o, rad)
+        p2 = oracle.project_ball(q2, o, rad)
+        oc = np.zeros(3) if o is None else o
+        assert np.linalg.norm(p1 - oc) <= rad * (1 + 1e-12)                 # feasible
+        assert np.allclose(oracle.project_ball(p1, o, rad), p1, atol=1e-12)  # idempotent
+        assert np.linalg.norm(p1 - p2) <= np.linalg.norm(q1 - q2) + 1e-12   # non-expansive
+        if np.linalg.norm(q1 - oc) <= rad:
+            assert np.allclose(p1, q1, atol=0)                              # identity inside
+        # brute force: no sampled feasible point is closer to q1
+        dirs = rng.normal(size=(2000, 3))
+        dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+        pts = oc + dirs * rad * rng.uniform(0, 1, size=(2000, 1)) ** (1 / 3)
+        pts = np.vstack([pts, oc + dirs * rad])
+        assert np.linalg.norm(p1 - q1) <= np.linalg.norm(pts - q1, axis=1).min() + 1e-12
+
+
+# ---------------------------------------------------------------- P8 ----
+
+def test_p8_dual_invariants():
+    w = W.tiny(seed=2, N=5, mode="free", T_range=(0.6, 1.4)).with_(max_iters=37)
+    r1 = oracle.solve(w, state=True)
+    r2 = oracle.solve(w.with_(max_iters=38), state=True)
+    T = w.durations
+    for j in range(1, 5):
+        for a in range(3):
+            for rr in range(7):
+                e, s = a * 14 + 7 + rr, a * 14 + rr
+                # free rows: u_end + u_start = 0 after every iteration
+                assert abs(r2["u"][j - 1, e] + r2["u"][j, s]) < 1e-9 * max(1, abs(r2["u"][j - 1, e]))
+                # the end-side increment is half the junction gap (Eq. 18b, 18c)
+                left = r2["coeffs"][j - 1, a] @ CZ.deriv_row(rr, T[j - 1])
+                right = r2["coeffs"][j, a] @ CZ.deriv_row(rr, 0.0)
+                inc = r2["u"][j - 1, e] - r1["u"][j - 1, e]
+                assert abs(inc - 0.5 * (left - right)) < 1e-8 * max(1, abs(left), abs(right))
+
+
+def test_pin_rows_and_ends_fixed():
+    w = W.tiny(seed=4, N=4, mode="pin").with_(max_iters=25)
+    r = oracle.solve(w, state=True)
+    z = r["z"]
+    assert np.allclose(z[:, :, 0], w.waypoints, atol=0)
+    assert np.allclose(z[0, :, :4], w.start_state[0].T, atol=0)
+    assert np.allclose(z[-1, :, :4], w.end_state[0].T, atol=0)
+    assert np.all(z[0, :, 4:] == 0) and np.all(z[-1, :, 4:] == 0)
+
+
+# ---------------------------------------------------------------- P9 ----
+
+def test_p9_long_double_rerun_bounds_rounding():
+    assert oracle.real_bytes("double") == 8 and oracle.real_bytes("long double") >= 10
+    for w in (W.single_box(), W.corridor(N=16).with_(max_iters=100)):
+        rd = oracle.solve(w)
+        rl = oracle.solve(w, real="long double")
+        err = scaled_relerr(rd["coeffs"], rl["coeffs"], w.durations)
+        assert err < 1e-11, err
+        assert abs(rd["cost"][0] - rl["cost"][0]) < 1e-11 * abs(rl["cost"][0])
+    # Jacobi equilibration is what keeps it small
+    w = W.corridor(N=16)
+    raw, eq = oracle.segment_cond(w, 0, 3)
+    assert raw > 1e4 * eq and eq < 1e4
+
+
+# ---------------------------------------------------- numerical step ----
+
+def test_numeric_step_with_inactive_bounds_equals_closed_form():
+    w = W.tiny(seed=8, N=6, mode="pin").with_(max_iters=60)
+    rc = oracle.solve(w)
+    wn = w.with_(inner="numeric", M_gen=8, gen_vmax=np.array([1e6]), gen_amax=np.array([1e6]))
+    rn = oracle.solve(wn, state=True)
+    assert scaled_relerr(rn["coeffs"], rc["coeffs"], w.durations) < 1e-12
+    assert np.all(rn["y_gen"] == 0)
+
+
+def _numpy_F(c, T, first, last, zt, u, y, rho, M, vmax, amax):
+    """F of Eq. 16 for one segment, from independent numpy matrices."""
+    Mt = np.zeros((42, 24))
+    E = np.ones(42)
+    for a in range(3):
+        for side in range(2):
+            for rr in range(7):
+                row = a * 14 + side * 7 + rr
+                Mt[row, a * 8:(a + 1) * 8] = CZ.deriv_row(rr, T if side else 0.0)
+                if (side == 0 and first or side == 1 and last) and rr >= 4:
+                    E[row] = 0
+    G = CZ.snap_gram(T)
+    F = sum(c[a * 8:(a + 1) * 8] @ G @ c[a * 8:(a + 1) * 8] for a in range(3))
+    res = E * (Mt @ c - zt + u)
+    F += rho / 2 * res @ res
+    for j in range(M):
+        t = (j + 1) * T / M
+        for order, gmax, yy in ((1, vmax, y[j, 0]), (2, amax, y[j, 1])):
+            vec = np.array([c[a * 8:(a + 1) * 8] @ CZ.deriv_row(order, t) for a in range(3)])
+            h = vec @ vec - gmax ** 2
+            g = max(0.0, h) ** 2
+            F += rho / 2 * g * g + yy * g
+    return F
+
+
+def test_numeric_local_step_is_stationary_point():
+    """With active norm bounds, the L-BFGS result is a minimiser of an independently
+    coded F: central differences of F vanish there and F is lower than nearby."""
+    w = W.tiny(seed=9, N=3, mode="pin", step=6.0, T_range=(0.8, 1.0)).with_(
+        inner="numeric", M_gen=6, gen_vmax=np.array([4.0]), gen_amax=np.array([8.0]), rho=1e4)
+    rng = np.random.default_rng(0)
+    i = 1
+    T = w.durations[i]
+    # consensus target: the boundary derivatives of the pinned spline (fast: |v| > 4)
+    spl = CZ.pin_spline(w.waypoints, w.durations, w.start_state[0], w.end_state[0])
+    zt = np.zeros(42)
+    for a in range(3):
+        for rr in range(7):
+            zt[a * 14 + rr] = spl[i, a] @ CZ.deriv_row(rr, 0.0)
+            zt[a * 14 + 7 + rr] = spl[i, a] @ CZ.deriv_row(rr, T)
+    u = rng.normal(scale=0.01, size=42)
+    y = np.abs(rng.normal(size=(6, 2)))
+    c, it = oracle.numeric_local(w, 0, i, zt, u, y)
+    assert it > 0
+    args = (T, False, False, zt, u, y, 1e4, 6, 4.0, 8.0)
+    # the bounds are active at the minimiser
+    vel = [np.linalg.norm([c[a * 8:(a + 1) * 8] @ CZ.deriv_row(1, (j + 1) * T / 6) for a in range(3)])
+           for j in range(6)]
+    assert max(vel) > 4.0
+    F0 = _numpy_F(c, *args)
+    # scale each coordinate by the curvature of the quadratic part
+    Hd = np.array([max(1e-12, (_numpy_F(c + e, *args) + _numpy_F(c - e, *args) - 2 * F0))
+                   for e in np.eye(24) * 1e-3]) / 1e-6
+    h = 1e-4 / np.sqrt(Hd)
+    grad = np.array([(_numpy_F(c + h[k] * np.eye(24)[k], *args) - _numpy_F(c - h[k] * np.eye(24)[k], *args))
+                     / (2 * h[k]) for k in range(24)])
+    gscaled = np.abs(grad / np.sqrt(Hd))
+    c_q = oracle.numeric_local(w.with_(gen_vmax=np.array([1e6]), gen_amax=np.array([1e6])), 0, i, zt, u, y)[0]
+    assert _numpy_F(c_q, *args) > F0   # the constraint terms moved the minimiser
+    assert gscaled.max() < 1e-5 * max(1.0, math.sqrt(abs(F0)))
+    for _ in range(50):
+        d = rng.normal(size=24) * h * 10
+        assert _numpy_F(c + d, *args) >= F0 - 1e-9 * abs(F0)
+
+
+def test_numeric_duals_nondecreasing():
+    w = W.tiny(seed=9, N=4, mode="pin", step=4.0, T_range=(0.8, 1.0)).with_(
+        inner="numeric", M_gen=4, gen_vmax=np.array([4.0]), gen_amax=np.array([8.0]), max_iters=5,
+        rho=1e4)
+    r5 = oracle.solve(w, state=True)
+    r6 = oracle.solve(w.with_(max_iters=6), state=True)
+    assert np.all(r5["y_gen"] >= 0) and r5["y_gen"].max() > 0
+    assert np.all(r6["y_gen"] >= r5["y_gen"])
+
+
+# ---------------------------------------------------------- stopping ----
+
+def test_stopping_rule_and_history():
+    w = W.tiny(seed=1, N=8, mode="free", T_range=(0.8, 1.6)).with_(eps=1e-3, max_iters=5000)
+    r = oracle.solve(w, history=True)
+    k = int(r["iters"][0])
+    h = r["history"][:, 0]
+    N = 8
+    assert r["status"][0] == 0 and 0 < k < 5000
+    assert h[k - 1, 0] < N * 1e-3 and h[k - 1, 1] < N * 1e-3
+    assert not (h[: k - 1, 0] < N * 1e-3).__and__(h[: k - 1, 1] < N * 1e-3).any()
+    assert r["r_primal"][0] == h[k - 1, 0] and r["r_dual"][0] == h[k - 1, 1]
+
+
+def test_batch_is_per_trajectory_and_handles_empty():
+    a = W.tiny(seed=6, N=[3, 0, 5, 1], mode="pin").with_(max_iters=40)
+    r = oracle.solve(a)
+    assert r["cost"][1] == 0 and r["iters"][1] == 0
+    for b in (0, 2, 3):
+        rb = oracle.solve(a.subset([b]))
+        s0, s1 = a.seg_offset[b], a.seg_offset[b + 1]
+        assert np.array_equal(rb["coeffs"], r["coeffs"][s0:s1])
+        assert rb["cost"][0] == r["cost"][b]
