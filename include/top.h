@@ -1,0 +1,174 @@
+/*
+ * top.h -- C ABI of the GB300 (sm_103a) consensus-ADMM trajectory optimiser.
+ *
+ * The library solves, for a batch of B trajectories, the piecewise-polynomial
+ * minimum-control-effort problem of arXiv 2507.10290 ("TOP: Trajectory
+ * Optimization via Parallel Optimization towards Constant Time Complexity"),
+ * Sec. III-B, Eq. 2:
+ *
+ *   min  sum_i int_0^{T_i} ||sigma_i^{(p)}(t)||^2 dt          (p = 4, min snap)
+ *   s.t. sigma_i^{[d-1]}(T_i) = sigma_{i+1}^{[d-1]}(0)        (continuity, orders 0..6)
+ *        sigma_1^{[p-1]}(0) = start, sigma_N^{[p-1]}(T_N) = end (orders 0..3)
+ *        G_i(sigma_i, ...) <= 0                                (sampled constraints)
+ *
+ * by the consensus ADMM iteration of Sec. III-D (Algorithm 1, Eq. 18a-g): a
+ * per-segment closed-form local QP solve (or the numerical L-BFGS step of
+ * Sec. III-C.3, Eq. 15-17), the junction consensus average, the scaled dual
+ * updates, the slack and projection steps for linear / quadratic
+ * constraints, the primal / dual residuals of Eq. 19-20 and the stopping rule
+ * of Eq. 21.  Each segment's flat output is a degree-7 polynomial per axis
+ * (m = 3 axes, 8 coefficients, Sec. III-D.1, Eq. 18 with d = 2p-1).
+ *
+ * Conventions for every entry point:
+ *   - return TOP_OK (0) on success, a negative TOP_E_* code on error; no
+ *     C++ exception crosses the ABI; top_strerror() names a code.
+ *   - the caller owns every input and output buffer; the handle owns its
+ *     device workspace (allocated by top_create, freed by top_destroy).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; top_solve synchronises it once to
+ *     read the batch layout unless the problem's memory is TOP_MEM_HOST.
+ *   - one handle serves one stream at a time (calls on a handle are not
+ *     thread-safe).
+ *   - every floating-point input and output is IEEE double.
+ *
+ * Basis of the returned coefficients (the paper's, Sec. III-D.1):
+ *   sigma_i(t)[a] = sum_{k=0}^{7} coeffs[i][a][k] * (t - t_{i-1})^k.
+ */
+#ifndef TOP_H
+#define TOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TOP_API_VERSION 1
+
+/* return codes */
+#define TOP_OK          0
+#define TOP_E_INVAL    -1  /* invalid argument (sizes, NULL, T <= 0, non-monotone offsets, ...) */
+#define TOP_E_NOMEM    -2  /* workspace allocation failed or the batch exceeds the handle's capacity */
+#define TOP_E_CUDA     -3  /* a CUDA runtime call failed (the CUDA error is kept for top_last_cuda_error) */
+#define TOP_E_TIMEOUT  -4  /* a bounded device wait ran out */
+#define TOP_E_NOTSUP   -5  /* a valid but unsupported combination (e.g. numeric step with box rows) */
+#define TOP_E_STATE    -6  /* call out of order (e.g. top_grad without a matching top_solve) */
+#define TOP_E_NUMERIC  -7  /* a local KKT matrix was not positive definite in FP64 */
+
+/* per-trajectory status written to top_result.status */
+#define TOP_CONVERGED      0  /* ||r_p|| < N eps and ||r_d|| < N eps (Eq. 21) */
+#define TOP_NOT_CONVERGED  1  /* max_iters reached first (always the case for eps = 0) */
+#define TOP_NONFINITE      2  /* a residual became NaN or Inf; results are those of that iteration */
+
+enum top_precision { TOP_FP32 = 0, TOP_FP64 = 1 };     /* arithmetic of the iteration */
+enum top_mode      { TOP_PIN = 0, TOP_FREE = 1 };      /* interior waypoints pinned or free */
+enum top_inner     { TOP_CLOSED_FORM = 0, TOP_NUMERIC = 1 };
+enum top_memory    { TOP_MEM_DEVICE = 0, TOP_MEM_HOST = 1 };
+enum top_schedule  { TOP_SCHED_AUTO = 0, TOP_SCHED_RESIDENT = 1, TOP_SCHED_STREAM = 2 };
+
+typedef struct top_handle top_handle;
+
+/* Fixed at creation: capacities of the device workspace and the precision. */
+typedef struct top_config {
+  int32_t precision;      /* TOP_FP32: FP32 iteration with FP64 KKT inverse and FP64 reductions;
+                             TOP_FP64: everything in FP64 */
+  int32_t max_batch;      /* largest B a call may pass */
+  int32_t max_segments;   /* largest total segment count S a call may pass */
+  int32_t max_samples;    /* largest M (samples per segment) of any constraint family */
+  int32_t schedule;       /* TOP_SCHED_AUTO picks per trajectory length; the others force one form */
+  int32_t segs_per_cta;   /* resident-form capacity per CTA; 0 = chosen from shared-memory size */
+  int32_t ckpt_interval;  /* adjoint checkpoint interval in iterations (0 = 10) */
+  int32_t reserved[9];    /* must be zero */
+} top_config;
+
+/* One batch.  Pointers are device pointers for TOP_MEM_DEVICE and host
+ * pointers for TOP_MEM_HOST (the library then stages them through its
+ * workspace); optional families pass M_* = 0 and NULL pointers. */
+typedef struct top_problem {
+  int32_t B;                  /* trajectories */
+  int32_t memory;             /* enum top_memory */
+  const int32_t *seg_offset;  /* [B+1] CSR: trajectory b owns segments seg_offset[b] .. seg_offset[b+1]-1;
+                                 N_b = 0 is allowed (empty trajectory) */
+  const double *waypoints;    /* [S+B][3] path P (Algorithm 1 input): trajectory b owns rows
+                                 seg_offset[b]+b .. seg_offset[b+1]+b (N_b+1 points) */
+  const double *durations;    /* [S] segment durations T_i > 0 (Sec. III-B) */
+  const double *start_state;  /* [B][4][3] boundary state, derivative order r = 0..3 x axis (Eq. 2b) */
+  const double *end_state;    /* [B][4][3] */
+  int32_t mode;               /* enum top_mode: PIN fixes interior junction positions to the waypoints */
+  int32_t inner;              /* enum top_inner (Algorithm 1: ClosedFormSolve / NumericSolve) */
+  double rho;                 /* ADMM penalty rho > 0 (fixed) */
+  double eps;                 /* stopping tolerance of Eq. 21 (E_r = E_d = N_b eps); 0 = run max_iters */
+  int32_t max_iters;          /* >= 0 */
+  int32_t check_every;        /* evaluate residuals / stop every this many iterations (>= 1) */
+  /* linear box rows |v_axis(t_ij)| <= vbox[b] (Sec. III-C.1, Eq. 8-10, 18d-e) */
+  int32_t M_box;  const double *vbox;     /* [B] */
+  /* ball corridor ||p(t_ij) - ball_c[i]|| <= ball_r[i] (Sec. III-C.2, Eq. 11-14, shifted) */
+  int32_t M_ball; const double *ball_c;   /* [S][3] */
+  const double *ball_r;                   /* [S] */
+  /* velocity norm ||v(t_ij)|| <= vnorm[b] by projection (Eq. 18f-g) */
+  int32_t M_vn;   const double *vnorm;    /* [B] */
+  /* general convex bounds through the numerical step (Eq. 15-17): ||v|| <= gen_vmax, ||a|| <= gen_amax */
+  int32_t M_gen;  const double *gen_vmax; /* [B] */
+  const double *gen_amax;                 /* [B] */
+  int32_t lbfgs_mem;          /* numerical step: L-BFGS memory (0 = 8) */
+  int32_t lbfgs_max_iters;    /* numerical step: iteration cap per local solve (0 = 50) */
+  double lbfgs_tol;           /* numerical step: relative gradient tolerance (0 = 1e-6 FP32 / 1e-12 FP64) */
+} top_problem;
+
+/* Outputs (same memory kind as the problem).  history may be NULL. */
+typedef struct top_result {
+  double *coeffs;    /* [S][3][8] paper basis (see above) */
+  double *cost;      /* [B] J = sum_i c_i^T Qt(T_i) c_i of the returned coefficients */
+  double *r_primal;  /* [B] ||r_p|| (Eq. 19) at the last evaluated iteration */
+  double *r_dual;    /* [B] ||r_d|| (Eq. 20) at the last evaluated iteration */
+  int32_t *iters;    /* [B] iterations run */
+  int32_t *status;   /* [B] TOP_CONVERGED | TOP_NOT_CONVERGED | TOP_NONFINITE */
+  double *history;   /* optional [max_iters][B][2]: (||r_p||, ||r_d||) at every evaluated iteration
+                        (entries of iterations that were not evaluated are left untouched) */
+} top_result;
+
+/* Allocate a handle and its device workspace on the current CUDA device.
+ * Errors: TOP_E_INVAL (NULL or non-positive capacities), TOP_E_NOMEM, TOP_E_CUDA. */
+int top_create(const top_config *cfg, top_handle **out);
+
+/* Run the CADMM iteration (Algorithm 1 / Eq. 18-21) on every trajectory of
+ * the batch and write the coefficients, costs, residuals, iteration counts
+ * and statuses.  Trajectories are independent; each stops on its own.
+ * Errors: TOP_E_INVAL, TOP_E_NOMEM (batch above capacity), TOP_E_NOTSUP,
+ * TOP_E_NUMERIC, TOP_E_CUDA, TOP_E_TIMEOUT. */
+int top_solve(top_handle *h, const top_problem *pb, top_result *res, void *stream);
+
+/* Gradient of sum_b dJ[b] * J_b, J_b the cost of trajectory b after exactly
+ * pb->max_iters iterations of the closed-form iteration without inequality
+ * constraints (eps ignored), with respect to the waypoints and the
+ * durations, by a hand-written adjoint through the unrolled iterations with
+ * checkpoints every ckpt_interval iterations.  dJ: [B]; dwaypoints: [S+B][3];
+ * ddurations: [S] (same memory kind as the problem; outputs are
+ * overwritten).  The paper has no gradient; this is an extension.
+ * Errors: as top_solve; TOP_E_NOTSUP with inequality families or the numerical step. */
+int top_grad(top_handle *h, const top_problem *pb, const double *dJ, double *dwaypoints,
+             double *ddurations, void *stream);
+
+/* Kernel timing.  With profiling enabled, top_solve records CUDA events on
+ * the launching stream around each kernel it launches; top_kernel_times then
+ * returns, for the last top_solve, ms[0] = local-matrix precompute, ms[1] =
+ * resident iteration kernel, ms[2] = streaming iteration kernels (0 for a
+ * kernel that did not run), for up to n entries.  Returns the number of
+ * entries written, or TOP_E_INVAL / TOP_E_STATE (profiling off). */
+int top_set_profiling(top_handle *h, int enable);
+int top_kernel_times(const top_handle *h, float *ms, int n);
+
+/* Free the workspace and the handle (NULL is a no-op). */
+void top_destroy(top_handle *h);
+
+/* Static description of a return code. */
+const char *top_strerror(int code);
+
+/* The last CUDA error seen by the handle (as a cudaError_t value), 0 if none. */
+int top_last_cuda_error(const top_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOP_H */

@@ -1,0 +1,465 @@
+// top_api.cu -- host driver behind the C ABI of include/top.h: argument
+// validation, workspace ownership, batch planning (packing trajectories into
+// resident CTAs, routing long ones to the streaming kernels) and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/top.h"
+#include "top_internal.h"
+#include "top_math.cuh"
+
+using namespace top;
+
+struct top_handle {
+  top_config cfg{};
+  int device = 0;
+  int sm_count = 0;
+  int smem_optin = 0;
+  int last_cuda = 0;
+  // device workspace
+  void *G = nullptr;          // [36][max_segments] of the iteration type
+  Pack *d_packs = nullptr;    // [max_segments]
+  int *d_err = nullptr;       // error flag of the precompute kernel
+  // staging for TOP_MEM_HOST problems
+  unsigned char *d_stage = nullptr;
+  size_t stage_bytes = 0;
+  // pinned host memory
+  int32_t *h_off = nullptr;   // [max_batch + 1]
+  Pack *h_packs = nullptr;    // [max_segments]
+  int *h_lt = nullptr;        // [2 * max_batch + 1] streaming trajectory list and prefix
+  int *h_err = nullptr;
+  // streaming-form workspace (allocated on first use)
+  unsigned char *d_stream = nullptr;
+  size_t stream_bytes = 0;
+  // kernel timing (top_set_profiling)
+  bool profiling = false;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool ran[3] = {false, false, false};
+};
+
+namespace {
+
+int cuda_fail(top_handle *h, cudaError_t e) {
+  if (h) h->last_cuda = (int)e;
+  return TOP_E_CUDA;
+}
+
+#define TOP_CUDA(h, expr)                              \
+  do {                                                 \
+    cudaError_t e__ = (expr);                          \
+    if (e__ != cudaSuccess) return cuda_fail(h, e__);  \
+  } while (0)
+
+size_t rbytes(const top_handle *h) { return h->cfg.precision == TOP_FP64 ? 8 : 4; }
+
+int families(const top_problem *pb) {
+  int f = 0;
+  if (pb->inner == TOP_CLOSED_FORM) {
+    if (pb->M_box > 0) f |= FAM_BOX;
+    if (pb->M_ball > 0) f |= FAM_BALL;
+    if (pb->M_vn > 0) f |= FAM_VN;
+  }
+  return f;
+}
+
+// largest resident capacity (threads = segments per CTA, multiple of 32, <= 512)
+// whose shared-memory layout fits the device's opt-in limit
+int resident_capacity(const top_handle *h, const top_problem *pb) {
+  const int fam = families(pb);
+  const int Mb = (fam & FAM_BOX) ? pb->M_box : 0;
+  const int Mq = (fam & FAM_BALL) ? pb->M_ball : 0;
+  const int Mv = (fam & FAM_VN) ? pb->M_vn : 0;
+  int cap = h->cfg.segs_per_cta > 0 ? std::min(512, h->cfg.segs_per_cta / 32 * 32) : 512;
+  for (int C = cap; C >= 32; C -= 32) {
+    ResLayout L = res_layout(C, C / 4, Mb, Mq, Mv, (int)rbytes(h));
+    if (L.total <= (size_t)h->smem_optin) return C;
+  }
+  return 0;
+}
+
+struct StagePlan {
+  size_t off_seg, off_wp, off_T, off_s0, off_s1, off_vbox, off_bc, off_br, off_vn, off_gv, off_ga;
+  size_t off_coef, off_cost, off_rp, off_rd, off_it, off_st, total;
+};
+
+StagePlan stage_plan(int Bmax, int Smax) {
+  StagePlan P{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes, 256); return at; };
+  P.off_seg = take(sizeof(int32_t) * (Bmax + 1));
+  P.off_wp = take(sizeof(double) * 3 * (size_t)(Smax + Bmax));
+  P.off_T = take(sizeof(double) * Smax);
+  P.off_s0 = take(sizeof(double) * 12 * (size_t)Bmax);
+  P.off_s1 = take(sizeof(double) * 12 * (size_t)Bmax);
+  P.off_vbox = take(sizeof(double) * Bmax);
+  P.off_bc = take(sizeof(double) * 3 * (size_t)Smax);
+  P.off_br = take(sizeof(double) * Smax);
+  P.off_vn = take(sizeof(double) * Bmax);
+  P.off_gv = take(sizeof(double) * Bmax);
+  P.off_ga = take(sizeof(double) * Bmax);
+  P.off_coef = take(sizeof(double) * 24 * (size_t)Smax);
+  P.off_cost = take(sizeof(double) * Bmax);
+  P.off_rp = take(sizeof(double) * Bmax);
+  P.off_rd = take(sizeof(double) * Bmax);
+  P.off_it = take(sizeof(int32_t) * Bmax);
+  P.off_st = take(sizeof(int32_t) * Bmax);
+  P.total = o;
+  return P;
+}
+
+int validate(const top_handle *h, const top_problem *pb, const top_result *res) {
+  if (!h || !pb || !res) return TOP_E_INVAL;
+  if (pb->B < 0 || pb->B > h->cfg.max_batch) return pb->B < 0 ? TOP_E_INVAL : TOP_E_NOMEM;
+  if (pb->memory != TOP_MEM_DEVICE && pb->memory != TOP_MEM_HOST) return TOP_E_INVAL;
+  if (pb->mode != TOP_PIN && pb->mode != TOP_FREE) return TOP_E_INVAL;
+  if (pb->inner != TOP_CLOSED_FORM && pb->inner != TOP_NUMERIC) return TOP_E_INVAL;
+  if (!(pb->rho > 0.0) || !(pb->rho < 1e300)) return TOP_E_INVAL;
+  if (!(pb->eps >= 0.0)) return TOP_E_INVAL;
+  if (pb->max_iters < 0 || pb->check_every < 0) return TOP_E_INVAL;
+  if (pb->M_box < 0 || pb->M_ball < 0 || pb->M_vn < 0 || pb->M_gen < 0) return TOP_E_INVAL;
+  const int mmax = std::max(std::max(pb->M_box, pb->M_ball), std::max(pb->M_vn, pb->M_gen));
+  if (mmax > h->cfg.max_samples) return TOP_E_NOMEM;
+  if (pb->M_box > 0 && !pb->vbox) return TOP_E_INVAL;
+  if (pb->M_ball > 0 && (!pb->ball_c || !pb->ball_r)) return TOP_E_INVAL;
+  if (pb->M_vn > 0 && !pb->vnorm) return TOP_E_INVAL;
+  if (pb->M_gen > 0 && (!pb->gen_vmax || !pb->gen_amax)) return TOP_E_INVAL;
+  if (pb->inner == TOP_NUMERIC) return TOP_E_NOTSUP;  // numerical step: not in this build yet
+  if (pb->inner == TOP_CLOSED_FORM && pb->M_gen) return TOP_E_NOTSUP;
+  if (pb->B > 0 && (!pb->seg_offset || !pb->waypoints || !pb->start_state || !pb->end_state))
+    return TOP_E_INVAL;
+  if (pb->B > 0 && (!res->coeffs || !res->cost || !res->r_primal || !res->r_dual || !res->iters ||
+                    !res->status))
+    return TOP_E_INVAL;
+  return TOP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *top_strerror(int code) {
+  switch (code) {
+    case TOP_OK: return "success";
+    case TOP_E_INVAL: return "invalid argument";
+    case TOP_E_NOMEM: return "out of workspace memory or batch above the handle's capacity";
+    case TOP_E_CUDA: return "CUDA runtime error";
+    case TOP_E_TIMEOUT: return "bounded device wait timed out";
+    case TOP_E_NOTSUP: return "unsupported combination of options";
+    case TOP_E_STATE: return "call out of order";
+    case TOP_E_NUMERIC: return "local KKT matrix not positive definite";
+    default: return "unknown error code";
+  }
+}
+
+int top_last_cuda_error(const top_handle *h) { return h ? h->last_cuda : 0; }
+
+int top_set_profiling(top_handle *h, int enable) {
+  if (!h) return TOP_E_INVAL;
+  if (enable && !h->ev[0]) {
+    for (auto &e : h->ev) {
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return cuda_fail(h, err);
+    }
+  }
+  h->profiling = enable != 0;
+  return TOP_OK;
+}
+
+int top_kernel_times(const top_handle *h, float *ms, int n) {
+  if (!h || !ms || n < 0) return TOP_E_INVAL;
+  if (!h->profiling) return TOP_E_STATE;
+  int w = 0;
+  for (int q = 0; q < 3 && w < n; ++q, ++w) {
+    ms[q] = 0.0f;
+    if (h->ran[q] && cudaEventElapsedTime(&ms[q], h->ev[2 * q], h->ev[2 * q + 1]) != cudaSuccess) ms[q] = -1.0f;
+  }
+  return w;
+}
+
+void top_destroy(top_handle *h) {
+  if (!h) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  cudaFree(h->G);
+  cudaFree(h->d_packs);
+  cudaFree(h->d_err);
+  cudaFree(h->d_stage);
+  cudaFree(h->d_stream);
+  cudaFreeHost(h->h_off);
+  cudaFreeHost(h->h_packs);
+  cudaFreeHost(h->h_lt);
+  cudaFreeHost(h->h_err);
+  for (auto &e : h->ev)
+    if (e) cudaEventDestroy(e);
+  cudaSetDevice(prev);
+  delete h;
+}
+
+int top_create(const top_config *cfg, top_handle **out) {
+  if (!cfg || !out) return TOP_E_INVAL;
+  *out = nullptr;
+  if (cfg->max_batch <= 0 || cfg->max_segments <= 0 || cfg->max_samples < 0) return TOP_E_INVAL;
+  if (cfg->precision != TOP_FP32 && cfg->precision != TOP_FP64) return TOP_E_INVAL;
+  if (cfg->schedule < TOP_SCHED_AUTO || cfg->schedule > TOP_SCHED_STREAM) return TOP_E_INVAL;
+  for (int q = 0; q < 9; ++q)
+    if (cfg->reserved[q] != 0) return TOP_E_INVAL;
+  top_handle *h = new (std::nothrow) top_handle;
+  if (!h) return TOP_E_NOMEM;
+  h->cfg = *cfg;
+  if (h->cfg.ckpt_interval <= 0) h->cfg.ckpt_interval = 10;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  const size_t S = (size_t)cfg->max_segments, B = (size_t)cfg->max_batch;
+  if (e == cudaSuccess) e = cudaMalloc(&h->G, (size_t)NG * S * rbytes(h));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_packs, sizeof(Pack) * S);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_err, sizeof(int));
+  if (e == cudaSuccess) {
+    h->stage_bytes = stage_plan((int)B, (int)S).total;
+    e = cudaMalloc((void **)&h->d_stage, h->stage_bytes);
+  }
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_off, sizeof(int32_t) * (B + 1));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_packs, sizeof(Pack) * S);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_lt, sizeof(int) * (2 * B + 1));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_err, sizeof(int));
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? TOP_E_NOMEM : TOP_E_CUDA;
+    h->last_cuda = (int)e;
+    top_destroy(h);
+    cudaGetLastError();
+    return code;
+  }
+  *out = h;
+  return TOP_OK;
+}
+
+int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void *stream) {
+  int rc = validate(h, pb_in, res_in);
+  if (rc != TOP_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  TOP_CUDA(h, cudaSetDevice(h->device));
+  const int B = pb_in->B;
+  if (B == 0) return TOP_OK;
+  // ---- batch layout on the host ----
+  if (pb_in->memory == TOP_MEM_HOST) {
+    std::memcpy(h->h_off, pb_in->seg_offset, sizeof(int32_t) * (B + 1));
+  } else {
+    TOP_CUDA(h, cudaMemcpyAsync(h->h_off, pb_in->seg_offset, sizeof(int32_t) * (B + 1),
+                                cudaMemcpyDeviceToHost, st));
+    TOP_CUDA(h, cudaStreamSynchronize(st));
+  }
+  const int32_t *off = h->h_off;
+  if (off[0] != 0) return TOP_E_INVAL;
+  for (int b = 0; b < B; ++b)
+    if (off[b + 1] < off[b]) return TOP_E_INVAL;
+  const int S = off[B];
+  if (S > h->cfg.max_segments) return TOP_E_NOMEM;
+  if (S > 0 && !pb_in->durations) return TOP_E_INVAL;
+  // ---- device views of inputs and outputs ----
+  top_problem pb = *pb_in;
+  top_result res = *res_in;
+  const bool host = pb_in->memory == TOP_MEM_HOST;
+  const StagePlan SP = stage_plan(h->cfg.max_batch, h->cfg.max_segments);
+  double *d_hist = nullptr;
+  if (host) {
+    unsigned char *base = h->d_stage;
+    auto up = [&](const void *src, size_t off_, size_t bytes) -> const void * {
+      if (!src || bytes == 0) return nullptr;
+      cudaMemcpyAsync(base + off_, src, bytes, cudaMemcpyHostToDevice, st);
+      return base + off_;
+    };
+    pb.seg_offset = (const int32_t *)up(pb_in->seg_offset, SP.off_seg, sizeof(int32_t) * (B + 1));
+    pb.waypoints = (const double *)up(pb_in->waypoints, SP.off_wp, sizeof(double) * 3 * (S + B));
+    pb.durations = (const double *)up(pb_in->durations, SP.off_T, sizeof(double) * S);
+    pb.start_state = (const double *)up(pb_in->start_state, SP.off_s0, sizeof(double) * 12 * B);
+    pb.end_state = (const double *)up(pb_in->end_state, SP.off_s1, sizeof(double) * 12 * B);
+    pb.vbox = pb.M_box ? (const double *)up(pb_in->vbox, SP.off_vbox, sizeof(double) * B) : nullptr;
+    pb.ball_c = pb.M_ball ? (const double *)up(pb_in->ball_c, SP.off_bc, sizeof(double) * 3 * S) : nullptr;
+    pb.ball_r = pb.M_ball ? (const double *)up(pb_in->ball_r, SP.off_br, sizeof(double) * S) : nullptr;
+    pb.vnorm = pb.M_vn ? (const double *)up(pb_in->vnorm, SP.off_vn, sizeof(double) * B) : nullptr;
+    pb.gen_vmax = pb.M_gen ? (const double *)up(pb_in->gen_vmax, SP.off_gv, sizeof(double) * B) : nullptr;
+    pb.gen_amax = pb.M_gen ? (const double *)up(pb_in->gen_amax, SP.off_ga, sizeof(double) * B) : nullptr;
+    TOP_CUDA(h, cudaGetLastError());
+    res.coeffs = (double *)(base + SP.off_coef);
+    res.cost = (double *)(base + SP.off_cost);
+    res.r_primal = (double *)(base + SP.off_rp);
+    res.r_dual = (double *)(base + SP.off_rd);
+    res.iters = (int32_t *)(base + SP.off_it);
+    res.status = (int32_t *)(base + SP.off_st);
+    res.history = nullptr;
+    if (res_in->history && pb.max_iters > 0) {
+      TOP_CUDA(h, cudaMalloc((void **)&d_hist, sizeof(double) * 2 * (size_t)pb.max_iters * B));
+      TOP_CUDA(h, cudaMemcpyAsync(d_hist, res_in->history, sizeof(double) * 2 * (size_t)pb.max_iters * B,
+                                  cudaMemcpyHostToDevice, st));
+      res.history = d_hist;
+    }
+  }
+  DevProblem dp{};
+  dp.B = B; dp.S = S;
+  dp.seg_offset = pb.seg_offset; dp.waypoints = pb.waypoints; dp.durations = pb.durations;
+  dp.start_state = pb.start_state; dp.end_state = pb.end_state;
+  dp.mode = pb.mode; dp.inner = pb.inner; dp.rho = pb.rho; dp.eps = pb.eps;
+  dp.max_iters = pb.max_iters; dp.check_every = pb.check_every > 0 ? pb.check_every : 1;
+  dp.M_box = pb.M_box; dp.vbox = pb.vbox;
+  dp.M_ball = pb.M_ball; dp.ball_c = pb.ball_c; dp.ball_r = pb.ball_r;
+  dp.M_vn = pb.M_vn; dp.vnorm = pb.vnorm;
+  dp.M_gen = pb.M_gen; dp.gen_vmax = pb.gen_vmax; dp.gen_amax = pb.gen_amax;
+  dp.lbfgs_mem = pb.lbfgs_mem > 0 ? pb.lbfgs_mem : 8;
+  dp.lbfgs_max_iters = pb.lbfgs_max_iters > 0 ? pb.lbfgs_max_iters : 50;
+  dp.lbfgs_tol = pb.lbfgs_tol > 0 ? pb.lbfgs_tol : (h->cfg.precision == TOP_FP64 ? 1e-12 : 1e-6);
+  DevResult dr{};
+  dr.coeffs = res.coeffs; dr.cost = res.cost; dr.r_primal = res.r_primal; dr.r_dual = res.r_dual;
+  dr.history = res.history; dr.iters = res.iters; dr.status = res.status;
+
+  // ---- per-trajectory outputs start at zero (covers empty trajectories) ----
+  TOP_CUDA(h, cudaMemsetAsync(dr.cost, 0, sizeof(double) * B, st));
+  TOP_CUDA(h, cudaMemsetAsync(dr.r_primal, 0, sizeof(double) * B, st));
+  TOP_CUDA(h, cudaMemsetAsync(dr.r_dual, 0, sizeof(double) * B, st));
+  TOP_CUDA(h, cudaMemsetAsync(dr.iters, 0, sizeof(int32_t) * B, st));
+  TOP_CUDA(h, cudaMemsetAsync(dr.status, 0, sizeof(int32_t) * B, st));
+  // ---- FP64 local-matrix inverses (Eq. 18a) ----
+  TOP_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+  const bool fp64 = h->cfg.precision == TOP_FP64;
+  h->ran[0] = h->ran[1] = h->ran[2] = false;
+  {
+    if (h->profiling) cudaEventRecord(h->ev[0], st);
+    int e = launch_kinv(dp, pb.rho, fp64 ? nullptr : h->G, fp64 ? h->G : nullptr, h->d_err, st);
+    if (e) return cuda_fail(h, (cudaError_t)e);
+    if (h->profiling) { cudaEventRecord(h->ev[1], st); h->ran[0] = true; }
+  }
+  // ---- plan: resident packs of whole trajectories ----
+  const int fam = families(&pb);
+  const int cap = (h->cfg.schedule == TOP_SCHED_STREAM || pb.inner == TOP_NUMERIC) ? 0 : resident_capacity(h, &pb);
+  int npack = 0, max_nseg = 0, max_ntraj = 0;
+  bool has_long = false;
+  {
+    const int ntp_cap = std::max(1, cap / 4);
+    int b = 0;
+    while (b < B) {
+      const int nb = off[b + 1] - off[b];
+      if (cap == 0 || nb > cap) { has_long = true; ++b; continue; }
+      Pack pk{off[b], 0, b, 0};
+      while (b < B) {
+        const int n2 = off[b + 1] - off[b];
+        if (n2 > cap || pk.nseg + n2 > cap || pk.ntraj + 1 > ntp_cap) break;
+        pk.nseg += n2;
+        pk.ntraj += 1;
+        ++b;
+      }
+      h->h_packs[npack++] = pk;
+      max_nseg = std::max(max_nseg, pk.nseg);
+      max_ntraj = std::max(max_ntraj, pk.ntraj);
+    }
+  }
+  if (has_long && h->cfg.schedule == TOP_SCHED_RESIDENT) {
+    if (d_hist) cudaFree(d_hist);
+    return TOP_E_NOTSUP;
+  }
+  if (npack > 0) {
+    TOP_CUDA(h, cudaMemcpyAsync(h->d_packs, h->h_packs, sizeof(Pack) * npack, cudaMemcpyHostToDevice, st));
+    const int C = std::max(32, (max_nseg + 31) / 32 * 32);
+    const int ntp = std::max(1, max_ntraj);
+    const int Mb = (fam & FAM_BOX) ? pb.M_box : 0, Mq = (fam & FAM_BALL) ? pb.M_ball : 0,
+              Mv = (fam & FAM_VN) ? pb.M_vn : 0;
+    const ResLayout L = res_layout(C, ntp, Mb, Mq, Mv, (int)rbytes(h));
+    ResidentArgs ra{};
+    ra.p = dp; ra.r = dr; ra.G = h->G; ra.packs = h->d_packs; ra.ntp = ntp;
+    if (h->profiling) cudaEventRecord(h->ev[2], st);
+    int e = fp64 ? launch_resident_f64(ra, npack, C, L.total, fam, st)
+                 : launch_resident_f32(ra, npack, C, L.total, fam, st);
+    if (e) return cuda_fail(h, (cudaError_t)e);
+    if (h->profiling) { cudaEventRecord(h->ev[3], st); h->ran[1] = true; }
+  }
+  // ---- streaming form for trajectories longer than a resident CTA ----
+  if (has_long) {
+    int nl = 0, total = 0;
+    h->h_lt[0] = 0;  // h_lt = [lt_b (B) | lt_prefix (B+1)]
+    int *lt_b = h->h_lt, *lt_pre = h->h_lt + h->cfg.max_batch;
+    lt_pre[0] = 0;
+    for (int b = 0; b < B; ++b) {
+      const int nb = off[b + 1] - off[b];
+      if (nb > 0 && (cap == 0 || nb > cap)) {
+        lt_b[nl] = b;
+        total += nb;
+        lt_pre[++nl] = total;
+      }
+    }
+    const size_t rb = rbytes(h);
+    const size_t Jn = (size_t)S + B;
+    const int Mb = (fam & FAM_BOX) ? pb.M_box : 0, Mq = (fam & FAM_BALL) ? pb.M_ball : 0,
+              Mv = (fam & FAM_VN) ? pb.M_vn : 0;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes, 256); return at; };
+    const size_t o_z = take(rb * 21 * Jn), o_uL = take(rb * 21 * Jn), o_dz = take(rb * 21 * Jn);
+    const size_t o_uRp = take(rb * 3 * Jn), o_uR0 = take(rb * 12 * (size_t)B);
+    const size_t o_eS = take(rb * 21 * (size_t)S), o_eE = take(rb * 21 * (size_t)S), o_ch = take(rb * 24 * (size_t)S);
+    const size_t o_yb = take(rb * 6 * Mb * (size_t)S), o_qb = take(rb * 3 * Mq * (size_t)S);
+    const size_t o_qv = take(rb * 3 * Mv * (size_t)S);
+    const size_t o_rp = take(sizeof(double) * total), o_rd = take(sizeof(double) * total);
+    const size_t o_done = take(sizeof(int) * nl), o_trp = take(sizeof(double) * nl), o_trd = take(sizeof(double) * nl);
+    const size_t o_lt = take(sizeof(int) * (2 * (size_t)nl + 1));
+    if (o > h->stream_bytes) {
+      cudaFree(h->d_stream);
+      h->d_stream = nullptr;
+      h->stream_bytes = 0;
+      cudaError_t e = cudaMalloc((void **)&h->d_stream, o);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (d_hist) cudaFree(d_hist);
+        return e == cudaErrorMemoryAllocation ? TOP_E_NOMEM : cuda_fail(h, e);
+      }
+      h->stream_bytes = o;
+    }
+    unsigned char *base = h->d_stream;
+    TOP_CUDA(h, cudaMemcpyAsync(base + o_lt, lt_b, sizeof(int) * nl, cudaMemcpyHostToDevice, st));
+    TOP_CUDA(h, cudaMemcpyAsync(base + o_lt + sizeof(int) * nl, lt_pre, sizeof(int) * (nl + 1),
+                                cudaMemcpyHostToDevice, st));
+    StreamArgs sa{};
+    sa.p = dp; sa.r = dr; sa.G = h->G;
+    sa.lt_b = (const int *)(base + o_lt);
+    sa.lt_prefix = (const int *)(base + o_lt) + nl;
+    sa.nl = nl; sa.total = total; sa.S = S; sa.Jn = (int)Jn;
+    sa.z = base + o_z; sa.uL = base + o_uL; sa.dz = base + o_dz; sa.uRp = base + o_uRp; sa.uR0 = base + o_uR0;
+    sa.eS = base + o_eS; sa.eE = base + o_eE; sa.ch = base + o_ch;
+    sa.ybox = base + o_yb; sa.qball = base + o_qb; sa.qvn = base + o_qv;
+    sa.rp2 = (double *)(base + o_rp); sa.rd2 = (double *)(base + o_rd);
+    sa.done = (int *)(base + o_done); sa.tr_rp = (double *)(base + o_trp); sa.tr_rd = (double *)(base + o_trd);
+    if (h->profiling) cudaEventRecord(h->ev[4], st);
+    int e = fp64 ? launch_stream_f64(sa, fam, st) : launch_stream_f32(sa, fam, st);
+    if (e) return cuda_fail(h, (cudaError_t)e);
+    if (h->profiling) { cudaEventRecord(h->ev[5], st); h->ran[2] = true; }
+  }
+  // ---- outputs back to the host, error flags ----
+  if (host) {
+    TOP_CUDA(h, cudaMemcpyAsync(res_in->coeffs, res.coeffs, sizeof(double) * 24 * S, cudaMemcpyDeviceToHost, st));
+    TOP_CUDA(h, cudaMemcpyAsync(res_in->cost, res.cost, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+    TOP_CUDA(h, cudaMemcpyAsync(res_in->r_primal, res.r_primal, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+    TOP_CUDA(h, cudaMemcpyAsync(res_in->r_dual, res.r_dual, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+    TOP_CUDA(h, cudaMemcpyAsync(res_in->iters, res.iters, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
+    TOP_CUDA(h, cudaMemcpyAsync(res_in->status, res.status, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
+    if (d_hist)
+      TOP_CUDA(h, cudaMemcpyAsync(res_in->history, d_hist, sizeof(double) * 2 * (size_t)pb.max_iters * B,
+                                  cudaMemcpyDeviceToHost, st));
+  }
+  TOP_CUDA(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TOP_CUDA(h, cudaStreamSynchronize(st));
+  if (d_hist) cudaFree(d_hist);
+  if (*h->h_err & 1) return TOP_E_INVAL;
+  if (*h->h_err & 2) return TOP_E_NUMERIC;
+  return TOP_OK;
+}
+
+int top_grad(top_handle *h, const top_problem *pb, const double *dJ, double *dwaypoints, double *ddurations,
+             void *stream) {
+  (void)h; (void)pb; (void)dJ; (void)dwaypoints; (void)ddurations; (void)stream;
+  return TOP_E_NOTSUP;
+}
+
+}  // extern "C"

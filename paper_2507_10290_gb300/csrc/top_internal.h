@@ -1,0 +1,120 @@
+// top_internal.h -- argument blocks shared by the host driver and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace top {
+
+enum Family : int { FAM_BOX = 1, FAM_BALL = 2, FAM_VN = 4 };
+
+// A pack is a run of consecutive whole trajectories processed by one CTA of
+// the resident kernel (all of its state stays in shared memory for every
+// iteration).
+struct Pack {
+  int seg0;   // first global segment
+  int nseg;   // segments in the pack (<= CTA capacity)
+  int traj0;  // first global trajectory
+  int ntraj;  // trajectories in the pack
+};
+
+// Problem data, all device pointers (FP64, the ABI layout).
+struct DevProblem {
+  int B, S;
+  const int32_t *seg_offset;
+  const double *waypoints, *durations, *start_state, *end_state;
+  int mode;       // 0 pin, 1 free
+  int inner;      // 0 closed form, 1 numeric
+  double rho, eps;
+  int max_iters, check_every;
+  int M_box;  const double *vbox;
+  int M_ball; const double *ball_c, *ball_r;
+  int M_vn;   const double *vnorm;
+  int M_gen;  const double *gen_vmax, *gen_amax;
+  int lbfgs_mem, lbfgs_max_iters;
+  double lbfgs_tol;
+};
+
+struct DevResult {
+  double *coeffs, *cost, *r_primal, *r_dual, *history;
+  int32_t *iters, *status;
+};
+
+struct ResidentArgs {
+  DevProblem p;
+  DevResult r;
+  const void *G;        // [36][S] packed (D K D)^{-1}, element type = iteration type
+  const Pack *packs;
+  int ntp;              // trajectory slots per pack (shared-memory sizing)
+};
+
+// Shared-memory layout of the resident kernel; the same function sizes the
+// launch on the host and carves the buffer on the device.
+struct ResLayout {
+  size_t red_rp, red_rd, tr_rp, tr_rd;           // double arrays
+  size_t z, uL, uRp, eS, dz, ybox, qball, qvn, uR0, tabB, tabQ, tabV;  // element arrays
+  size_t off, done;                              // int arrays
+  size_t total;
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, int Mv, int rb) {
+  ResLayout L{};
+  const size_t J = size_t(C) + size_t(ntp);
+  size_t o = 0;
+  L.red_rp = o; o += sizeof(double) * C;
+  L.red_rd = o; o += sizeof(double) * C;
+  L.tr_rp = o;  o += sizeof(double) * ntp;
+  L.tr_rd = o;  o += sizeof(double) * ntp;
+  o = align_up(o, 16);
+  L.z = o;      o += size_t(rb) * 21 * J;
+  L.uL = o;     o += size_t(rb) * 21 * J;
+  L.uRp = o;    o += size_t(rb) * 3 * J;
+  L.eS = o;     o += size_t(rb) * 21 * C;
+  L.dz = o;     o += size_t(rb) * 21 * J;
+  L.ybox = o;   o += size_t(rb) * 6 * Mb * C;
+  L.qball = o;  o += size_t(rb) * 3 * Mq * C;
+  L.qvn = o;    o += size_t(rb) * 3 * Mv * C;
+  L.uR0 = o;    o += size_t(rb) * 12 * ntp;
+  L.tabB = o;   o += size_t(rb) * 8 * Mb;
+  L.tabQ = o;   o += size_t(rb) * 8 * Mq;
+  L.tabV = o;   o += size_t(rb) * 8 * Mv;
+  o = align_up(o, 16);
+  L.off = o;    o += sizeof(int) * (ntp + 1);
+  L.done = o;   o += sizeof(int) * ntp;
+  L.total = align_up(o, 16);
+  return L;
+}
+
+// Streaming form (trajectories longer than a resident CTA): state in global
+// memory.  Compact segment index x over the streaming trajectories:
+// lt_prefix[t] .. lt_prefix[t+1]-1 belong to trajectory lt_b[t].
+struct StreamArgs {
+  DevProblem p;
+  DevResult r;
+  const void *G;           // [36][S]
+  const int *lt_b;         // [nl]
+  const int *lt_prefix;    // [nl+1]
+  int nl, total;           // trajectories, segments in the streaming set
+  int S, Jn;               // global segments, global junctions (S + B)
+  // state, element type = iteration type; junction arrays indexed like the waypoints
+  void *z, *uL, *dz;       // [21][Jn]
+  void *uRp;               // [3][Jn]
+  void *uR0;               // [12][B]
+  void *eS, *eE;           // [21][S]
+  void *ch;                // [24][S]
+  void *ybox, *qball, *qvn;  // [6 M_box][S], [3 M_ball][S], [3 M_vn][S]
+  double *rp2, *rd2;       // [total]
+  int *done;               // [nl]
+  double *tr_rp, *tr_rd;   // [nl]
+};
+
+// launchers (defined in the .cu files)
+int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_flag, void *stream);
+int launch_resident_f32(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
+int launch_resident_f64(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
+int launch_stream_f32(const StreamArgs &a, int fam, void *stream);
+int launch_stream_f64(const StreamArgs &a, int fam, void *stream);
+
+}  // namespace top

@@ -1,0 +1,346 @@
+// top_stream.cuh -- the streaming CADMM form for trajectories longer than one
+// CTA's shared memory holds: all iteration state in global memory, one launch
+// per phase of each iteration (Algorithm 1, Eq. 18a-g, 19-21):
+//   stream_local     every segment: local step + projections (shared
+//                    local_step), end derivatives to global memory
+//   stream_junction  every segment's end junction: consensus average, scaled
+//                    duals, primal-residual share, consensus change
+//   stream_reduce    on check iterations: dual-residual shares, then one block
+//                    per trajectory sums the shares in a fixed order, records
+//                    the history and applies the stopping rule
+//   stream_output    coefficients in the paper's basis and per-trajectory cost
+// Segments are addressed through a compact index x over the long
+// trajectories (lt_prefix[t] .. lt_prefix[t+1]-1 belong to trajectory lt_b[t]);
+// junction state is indexed like the waypoints (segment g of trajectory b ends
+// at junction g + b + 1).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "top_internal.h"
+#include "top_math.cuh"
+#include "top_step.cuh"
+
+namespace top {
+
+__device__ __forceinline__ void stream_locate(const StreamArgs &A, int x, int &t, int &b, int &i, int &N, int &g) {
+  int lo = 0, hi = A.nl - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (A.lt_prefix[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  t = lo;
+  b = A.lt_b[t];
+  i = x - A.lt_prefix[t];
+  N = A.lt_prefix[t + 1] - A.lt_prefix[t];
+  g = A.p.seg_offset[b] + i;
+}
+
+template <class R, int F>
+__global__ void stream_init(const StreamArgs A) {
+  constexpr bool BOX = (F & FAM_BOX) != 0, BALL = (F & FAM_BALL) != 0, VN = (F & FAM_VN) != 0;
+  const DevProblem &p = A.p;
+  R *z = (R *)A.z, *uL = (R *)A.uL, *uRp = (R *)A.uRp, *dz = (R *)A.dz, *uR0 = (R *)A.uR0;
+  R *ch = (R *)A.ch, *ybox = (R *)A.ybox, *qball = (R *)A.qball, *qvn = (R *)A.qvn;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
+    int t, b, i, N, g;
+    stream_locate(A, x, t, b, i, N, g);
+    const bool first = i == 0, last = i == N - 1;
+    const int jS = g + b, jE = g + b + 1;
+    for (int a = 0; a < AX; ++a)
+      for (int r = 0; r < ND; ++r) {
+        R zv = R(0);
+        if (!last) {
+          if (r == 0) zv = R(p.waypoints[(size_t)jE * 3 + a]);
+        } else if (r < PO) {
+          zv = R(p.end_state[((size_t)b * PO + r) * 3 + a]);
+        }
+        const size_t row = (size_t)(a * ND + r) * A.Jn;
+        z[row + jE] = zv;
+        uL[row + jE] = R(0);
+        dz[row + jE] = R(0);
+        if (first) {
+          z[row + jS] = r < PO ? R(p.start_state[((size_t)b * PO + r) * 3 + a]) : R(0);
+          uL[row + jS] = R(0);
+          dz[row + jS] = R(0);
+        }
+      }
+    for (int a = 0; a < 3; ++a) {
+      uRp[(size_t)a * A.Jn + jE] = R(0);
+      if (first) uRp[(size_t)a * A.Jn + jS] = R(0);
+    }
+    if (first)
+      for (int q = 0; q < 12; ++q) uR0[(size_t)q * p.B + b] = R(0);
+    for (int q = 0; q < 24; ++q) ch[(size_t)q * A.S + g] = R(0);
+    if (BOX) for (int q = 0; q < 6 * p.M_box; ++q) ybox[(size_t)q * A.S + g] = R(0);
+    if (BALL) for (int q = 0; q < 3 * p.M_ball; ++q) qball[(size_t)q * A.S + g] = R(0);
+    if (VN) for (int q = 0; q < 3 * p.M_vn; ++q) qvn[(size_t)q * A.S + g] = R(0);
+    if (first) { A.done[t] = 0; A.tr_rp[t] = 0.0; A.tr_rd[t] = 0.0; }
+  }
+}
+
+template <class R, int F>
+__global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
+  constexpr bool BOX = (F & FAM_BOX) != 0, BALL = (F & FAM_BALL) != 0, VN = (F & FAM_VN) != 0;
+  const DevProblem &p = A.p;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int Mb = BOX ? p.M_box : 0, Mq = BALL ? p.M_ball : 0, Mv = VN ? p.M_vn : 0;
+  R *tabB = (R *)smem, *tabQ = tabB + 8 * Mb, *tabV = tabQ + 8 * Mq;
+  if (BOX) fill_sample_table(tabB, Mb, 1, threadIdx.x, blockDim.x);
+  if (BALL) fill_sample_table(tabQ, Mq, 0, threadIdx.x, blockDim.x);
+  if (VN) fill_sample_table(tabV, Mv, 1, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const R *z = (const R *)A.z, *uL = (const R *)A.uL, *uRp = (const R *)A.uRp, *uR0 = (const R *)A.uR0;
+  const R *Gp = (const R *)A.G;
+  R *eS = (R *)A.eS, *eE = (R *)A.eE, *chg = (R *)A.ch;
+  const R rho = R(p.rho);
+  const bool pin = p.mode == 0;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
+    int t, b, i, N, g;
+    stream_locate(A, x, t, b, i, N, g);
+    if (A.done[t]) continue;
+    const bool first = i == 0, last = i == N - 1;
+    const int jS = g + b, jE = g + b + 1;
+    SegConst<R> sc;
+#pragma unroll
+    for (int q = 0; q < NG; ++q) sc.G[q] = Gp[(size_t)q * A.S + g];
+    inv_powers(R(p.durations[g]), sc.s);
+    sc.vbox = BOX ? R(p.vbox[b]) : R(0);
+    sc.vnorm = VN ? R(p.vnorm[b]) : R(0);
+    sc.brad = BALL ? R(p.ball_r[g]) : R(0);
+    for (int a = 0; a < 3; ++a) sc.bo[a] = BALL ? R(p.ball_c[(size_t)g * 3 + a]) : R(0);
+    R wS[AX][ND], wE[AX][ND];
+#pragma unroll
+    for (int a = 0; a < AX; ++a)
+#pragma unroll
+      for (int r = 0; r < ND; ++r) {
+        const size_t row = (size_t)(a * ND + r) * A.Jn;
+        R us;
+        if (first) us = (r < PO) ? uR0[(size_t)(a * PO + r) * p.B + b] : R(0);
+        else if (pin && r == 0) us = uRp[(size_t)a * A.Jn + jS];
+        else us = -uL[row + jS];
+        wS[a][r] = (first && r >= PO) ? R(0) : sc.s[r] * (z[row + jS] - us);
+        wE[a][r] = (last && r >= PO) ? R(0) : sc.s[r] * (z[row + jE] - uL[row + jE]);
+      }
+    R ch[AX][NC];
+    local_step<R, F>(sc, wS, wE, rho, k == 0, (R *)A.ybox + g, (R *)A.qball + g, (R *)A.qvn + g, A.S, tabB,
+                     tabQ, tabV, Mb, Mq, Mv, ch);
+#pragma unroll
+    for (int a = 0; a < AX; ++a) {
+      R s7[ND], e7[ND];
+      end_derivs(ch[a], sc.s, s7, e7);
+#pragma unroll
+      for (int r = 0; r < ND; ++r) {
+        eS[(size_t)(a * ND + r) * A.S + g] = s7[r];
+        eE[(size_t)(a * ND + r) * A.S + g] = e7[r];
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) chg[(size_t)(a * NC + q) * A.S + g] = ch[a][q];
+    }
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) stream_junction(const StreamArgs A, int check) {
+  const DevProblem &p = A.p;
+  R *z = (R *)A.z, *uL = (R *)A.uL, *uRp = (R *)A.uRp, *dz = (R *)A.dz, *uR0 = (R *)A.uR0;
+  const R *eS = (const R *)A.eS, *eE = (const R *)A.eE;
+  const bool pin = p.mode == 0;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
+    int t, b, i, N, g;
+    stream_locate(A, x, t, b, i, N, g);
+    if (A.done[t]) continue;
+    const bool first = i == 0, last = i == N - 1;
+    const int jS = g + b, jE = g + b + 1;
+    double rp2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < AX; ++a)
+#pragma unroll
+      for (int r = 0; r < ND; ++r) {
+        const size_t row = (size_t)(a * ND + r) * A.Jn;
+        const R ee = eE[(size_t)(a * ND + r) * A.S + g];
+        if (!last) {
+          const R en = eS[(size_t)(a * ND + r) * A.S + g + 1];
+          const R gap = ee - en;
+          rp2 += double(gap) * double(gap);
+          if (pin && r == 0) {
+            const R P = z[row + jE];
+            uL[row + jE] += ee - P;
+            uRp[(size_t)a * A.Jn + jE] += en - P;
+            if (check) dz[row + jE] = R(0);
+          } else {
+            const R zo = z[row + jE];
+            const R zn = R(0.5) * (ee + en);
+            uL[row + jE] += ee - zn;
+            z[row + jE] = zn;
+            if (check) dz[row + jE] = zn - zo;
+          }
+        } else if (r < PO) {
+          uL[row + jE] += ee - z[row + jE];
+        }
+        if (first && r < PO) {
+          const R es = eS[(size_t)(a * ND + r) * A.S + g];
+          uR0[(size_t)(a * PO + r) * p.B + b] += es - z[row + jS];
+        }
+      }
+    A.rp2[x] = rp2;
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) stream_dual(const StreamArgs A) {
+  const DevProblem &p = A.p;
+  const R *dz = (const R *)A.dz;
+  const R rho = R(p.rho);
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
+    int t, b, i, N, g;
+    stream_locate(A, x, t, b, i, N, g);
+    if (A.done[t]) continue;
+    const bool first = i == 0, last = i == N - 1;
+    const int jS = g + b, jE = g + b + 1;
+    R s[NC], Tk[NC];
+    const R T = R(p.durations[g]);
+    inv_powers(T, s);
+    Tk[0] = R(1);
+#pragma unroll
+    for (int q = 1; q < NC; ++q) Tk[q] = Tk[q - 1] * T;
+    double rd2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < AX; ++a) {
+      R dS[ND], dE[ND];
+#pragma unroll
+      for (int r = 0; r < ND; ++r) {
+        const size_t row = (size_t)(a * ND + r) * A.Jn;
+        dS[r] = first ? R(0) : s[r] * dz[row + jS];
+        dE[r] = last ? R(0) : s[r] * dz[row + jE];
+      }
+      rd2 += dual_residual_sq(dS, dE, rho, Tk);
+    }
+    A.rd2[x] = rd2;
+  }
+}
+
+// one block per streaming trajectory: fixed-order sums, history, stopping rule
+template <class R>
+__global__ void __launch_bounds__(256) stream_reduce(const StreamArgs A, int k) {
+  __shared__ double s1[256], s2[256];
+  const int t = blockIdx.x;
+  if (t >= A.nl || A.done[t]) return;
+  const int b = A.lt_b[t];
+  const int x0 = A.lt_prefix[t], x1 = A.lt_prefix[t + 1];
+  double a1 = 0.0, a2 = 0.0;
+  for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) { a1 += A.rp2[x]; a2 += A.rd2[x]; }
+  s1[threadIdx.x] = a1;
+  s2[threadIdx.x] = a2;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) { s1[threadIdx.x] += s1[threadIdx.x + o]; s2[threadIdx.x] += s2[threadIdx.x + o]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double rp = sqrt(s1[0]), rd = sqrt(s2[0]);
+    A.tr_rp[t] = rp;
+    A.tr_rd[t] = rd;
+    if (A.r.history) {
+      A.r.history[((size_t)k * A.p.B + b) * 2 + 0] = rp;
+      A.r.history[((size_t)k * A.p.B + b) * 2 + 1] = rd;
+    }
+    const double tol = double(x1 - x0) * A.p.eps;
+    int st = -1;
+    if (!finite_d(rp) || !finite_d(rd)) st = 2;
+    else if (A.p.eps > 0.0 && rp < tol && rd < tol) st = 0;
+    if (st >= 0) {
+      A.done[t] = 1;
+      A.r.iters[b] = k + 1;
+      A.r.status[b] = st;
+    }
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) stream_output(const StreamArgs A) {
+  const DevProblem &p = A.p;
+  const R *chg = (const R *)A.ch;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
+    int t, b, i, N, g;
+    stream_locate(A, x, t, b, i, N, g);
+    const double T = p.durations[g];
+    double sd[NC];
+    sd[0] = 1.0;
+    for (int q = 1; q < NC; ++q) sd[q] = sd[q - 1] / T;
+    R ch[AX][NC];
+#pragma unroll
+    for (int a = 0; a < AX; ++a)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        ch[a][q] = chg[(size_t)(a * NC + q) * A.S + g];
+        A.r.coeffs[((size_t)g * AX + a) * NC + q] = double(ch[a][q]) * sd[q];
+      }
+    A.rp2[x] = segment_cost(ch, sd[7]);
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) stream_finish(const StreamArgs A, int K) {
+  __shared__ double s1[256];
+  const int t = blockIdx.x;
+  if (t >= A.nl) return;
+  const int b = A.lt_b[t];
+  const int x0 = A.lt_prefix[t], x1 = A.lt_prefix[t + 1];
+  double a1 = 0.0;
+  for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) a1 += A.rp2[x];
+  s1[threadIdx.x] = a1;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s1[threadIdx.x] += s1[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    A.r.cost[b] = s1[0];
+    A.r.r_primal[b] = A.tr_rp[t];
+    A.r.r_dual[b] = A.tr_rd[t];
+    if (!A.done[t]) {
+      A.r.iters[b] = K;
+      A.r.status[b] = 1;
+    }
+  }
+}
+
+template <class R>
+int run_stream_t(const StreamArgs &A, int fam, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (A.total == 0) return 0;
+  const int threads = 256;
+  int blocks = (A.total + threads - 1) / threads;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  const DevProblem &p = A.p;
+  const int Mb = (fam & FAM_BOX) ? p.M_box : 0, Mq = (fam & FAM_BALL) ? p.M_ball : 0,
+            Mv = (fam & FAM_VN) ? p.M_vn : 0;
+  const size_t tab_bytes = sizeof(R) * 8 * (size_t)(Mb + Mq + Mv);
+  void (*init)(const StreamArgs) = nullptr;
+  void (*local)(const StreamArgs, int) = nullptr;
+  switch (fam) {
+#define TOP_ST_CASE(FV) case FV: init = stream_init<R, FV>; local = stream_local<R, FV>; break;
+    TOP_ST_CASE(0) TOP_ST_CASE(1) TOP_ST_CASE(2) TOP_ST_CASE(3)
+    TOP_ST_CASE(4) TOP_ST_CASE(5) TOP_ST_CASE(6) TOP_ST_CASE(7)
+#undef TOP_ST_CASE
+    default: return (int)cudaErrorInvalidValue;
+  }
+  init<<<blocks, threads, 0, st>>>(A);
+  const int K = p.max_iters;
+  const int cev = p.check_every > 0 ? p.check_every : 1;
+  for (int k = 0; k < K; ++k) {
+    const bool check = (k == K - 1) || ((p.eps > 0.0 || A.r.history) && ((k + 1) % cev == 0));
+    local<<<blocks, threads, tab_bytes, st>>>(A, k);
+    stream_junction<R><<<blocks, threads, 0, st>>>(A, check ? 1 : 0);
+    if (check) {
+      stream_dual<R><<<blocks, threads, 0, st>>>(A);
+      stream_reduce<R><<<A.nl, 256, 0, st>>>(A, k);
+    }
+  }
+  stream_output<R><<<blocks, threads, 0, st>>>(A);
+  stream_finish<R><<<A.nl, 256, 0, st>>>(A, K);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace top

@@ -1,0 +1,293 @@
+"""ctypes binding of the C ABI in include/top.h (argument marshalling only).
+
+The functions `top_create`, `top_solve`, `top_grad`, `top_destroy`,
+`top_strerror` and `top_last_cuda_error` have the names and arguments of the
+C entry points.  `Solver` wraps them for torch tensors: torch supplies the
+device memory and the stream, every step of the iteration runs in the CUDA
+library.  Importing this module loads libtop.so and raises ImportError if it
+has not been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtop.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "top.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+        "(the CUDA library is required; there is no CPU fallback)")
+_lib = C.CDLL(LIB_PATH)
+
+
+def _header_constants():
+    vals = {}
+    with open(HEADER_PATH) as f:
+        for m in re.finditer(r"#define\s+(TOP_\w+)\s+(-?\d+)", f.read()):
+            vals[m.group(1)] = int(m.group(2))
+    return vals
+
+
+_K = _header_constants()
+TOP_OK = _K["TOP_OK"]
+TOP_E_INVAL = _K["TOP_E_INVAL"]
+TOP_E_NOMEM = _K["TOP_E_NOMEM"]
+TOP_E_CUDA = _K["TOP_E_CUDA"]
+TOP_E_TIMEOUT = _K["TOP_E_TIMEOUT"]
+TOP_E_NOTSUP = _K["TOP_E_NOTSUP"]
+TOP_E_STATE = _K["TOP_E_STATE"]
+TOP_E_NUMERIC = _K["TOP_E_NUMERIC"]
+TOP_CONVERGED, TOP_NOT_CONVERGED, TOP_NONFINITE = 0, 1, 2
+TOP_FP32, TOP_FP64 = 0, 1
+TOP_PIN, TOP_FREE = 0, 1
+TOP_CLOSED_FORM, TOP_NUMERIC = 0, 1
+TOP_MEM_DEVICE, TOP_MEM_HOST = 0, 1
+TOP_SCHED_AUTO, TOP_SCHED_RESIDENT, TOP_SCHED_STREAM = 0, 1, 2
+
+
+class top_config(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_batch", C.c_int32), ("max_segments", C.c_int32),
+                ("max_samples", C.c_int32), ("schedule", C.c_int32), ("segs_per_cta", C.c_int32),
+                ("ckpt_interval", C.c_int32), ("reserved", C.c_int32 * 9)]
+
+
+class top_problem(C.Structure):
+    _fields_ = [("B", C.c_int32), ("memory", C.c_int32), ("seg_offset", C.c_void_p),
+                ("waypoints", C.c_void_p), ("durations", C.c_void_p), ("start_state", C.c_void_p),
+                ("end_state", C.c_void_p), ("mode", C.c_int32), ("inner", C.c_int32),
+                ("rho", C.c_double), ("eps", C.c_double), ("max_iters", C.c_int32),
+                ("check_every", C.c_int32),
+                ("M_box", C.c_int32), ("vbox", C.c_void_p),
+                ("M_ball", C.c_int32), ("ball_c", C.c_void_p), ("ball_r", C.c_void_p),
+                ("M_vn", C.c_int32), ("vnorm", C.c_void_p),
+                ("M_gen", C.c_int32), ("gen_vmax", C.c_void_p), ("gen_amax", C.c_void_p),
+                ("lbfgs_mem", C.c_int32), ("lbfgs_max_iters", C.c_int32), ("lbfgs_tol", C.c_double)]
+
+
+class top_result(C.Structure):
+    _fields_ = [("coeffs", C.c_void_p), ("cost", C.c_void_p), ("r_primal", C.c_void_p),
+                ("r_dual", C.c_void_p), ("iters", C.c_void_p), ("status", C.c_void_p),
+                ("history", C.c_void_p)]
+
+
+_lib.top_create.argtypes = [C.POINTER(top_config), C.POINTER(C.c_void_p)]
+_lib.top_create.restype = C.c_int
+_lib.top_solve.argtypes = [C.c_void_p, C.POINTER(top_problem), C.POINTER(top_result), C.c_void_p]
+_lib.top_solve.restype = C.c_int
+_lib.top_grad.argtypes = [C.c_void_p, C.POINTER(top_problem), C.c_void_p, C.c_void_p, C.c_void_p,
+                          C.c_void_p]
+_lib.top_grad.restype = C.c_int
+_lib.top_destroy.argtypes = [C.c_void_p]
+_lib.top_destroy.restype = None
+_lib.top_strerror.argtypes = [C.c_int]
+_lib.top_strerror.restype = C.c_char_p
+_lib.top_last_cuda_error.argtypes = [C.c_void_p]
+_lib.top_last_cuda_error.restype = C.c_int
+_lib.top_set_profiling.argtypes = [C.c_void_p, C.c_int]
+_lib.top_set_profiling.restype = C.c_int
+_lib.top_kernel_times.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int]
+_lib.top_kernel_times.restype = C.c_int
+
+
+def top_create(cfg: top_config):
+    """int top_create(const top_config*, top_handle**) -> (code, handle)"""
+    h = C.c_void_p()
+    rc = _lib.top_create(C.byref(cfg), C.byref(h))
+    return rc, h
+
+
+def top_solve(handle, problem: top_problem, result: top_result, stream: int = 0) -> int:
+    return _lib.top_solve(handle, C.byref(problem), C.byref(result), C.c_void_p(stream))
+
+
+def top_grad(handle, problem: top_problem, dJ: int, dwaypoints: int, ddurations: int, stream: int = 0) -> int:
+    return _lib.top_grad(handle, C.byref(problem), C.c_void_p(dJ), C.c_void_p(dwaypoints),
+                         C.c_void_p(ddurations), C.c_void_p(stream))
+
+
+def top_destroy(handle) -> None:
+    _lib.top_destroy(handle)
+
+
+def top_strerror(code: int) -> str:
+    return _lib.top_strerror(int(code)).decode()
+
+
+def top_last_cuda_error(handle) -> int:
+    return _lib.top_last_cuda_error(handle)
+
+
+def top_set_profiling(handle, enable: bool) -> int:
+    return _lib.top_set_profiling(handle, int(bool(enable)))
+
+
+def top_kernel_times(handle, n: int = 3):
+    """(code, [ms...]) of the last top_solve's kernels: precompute, resident, streaming."""
+    buf = (C.c_float * n)()
+    rc = _lib.top_kernel_times(handle, buf, n)
+    return rc, [float(x) for x in buf]
+
+
+class TopError(RuntimeError):
+    def __init__(self, code: int, where: str, cuda: int = 0):
+        msg = f"{where}: {top_strerror(code)} ({code})"
+        if cuda:
+            msg += f", cudaError {cuda}"
+        super().__init__(msg)
+        self.code = code
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class Solver:
+    """One handle of the library, sized for a batch capacity.
+
+    precision: "fp32" (FP32 iteration, FP64 KKT inverses and reductions) or "fp64".
+    """
+
+    def __init__(self, max_batch: int, max_segments: int, precision: str = "fp32", max_samples: int = 16,
+                 schedule: str = "auto", segs_per_cta: int = 0, ckpt_interval: int = 10):
+        import torch  # device memory and streams only
+        self.torch = torch
+        cfg = top_config()
+        cfg.precision = {"fp32": TOP_FP32, "fp64": TOP_FP64}[precision]
+        cfg.max_batch = int(max_batch)
+        cfg.max_segments = int(max(1, max_segments))
+        cfg.max_samples = int(max_samples)
+        cfg.schedule = {"auto": TOP_SCHED_AUTO, "resident": TOP_SCHED_RESIDENT, "stream": TOP_SCHED_STREAM}[schedule]
+        cfg.segs_per_cta = int(segs_per_cta)
+        cfg.ckpt_interval = int(ckpt_interval)
+        self.precision = precision
+        rc, h = top_create(cfg)
+        if rc != TOP_OK:
+            raise TopError(rc, "top_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            top_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- marshalling --------------------------------------------------------
+    def device_inputs(self, w, device="cuda"):
+        """Copy a Workload's arrays into device tensors (FP64, ABI layout)."""
+        torch = self.torch
+
+        def t(x, dtype=torch.float64):
+            return None if x is None else torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=device)
+
+        return {
+            "seg_offset": t(w.seg_offset, torch.int32), "waypoints": t(w.waypoints), "durations": t(w.durations),
+            "start_state": t(w.start_state), "end_state": t(w.end_state),
+            "vbox": t(getattr(w, "vbox", None)), "ball_c": t(getattr(w, "ball_c", None)),
+            "ball_r": t(getattr(w, "ball_r", None)), "vnorm": t(getattr(w, "vnorm", None)),
+            "gen_vmax": t(getattr(w, "gen_vmax", None)), "gen_amax": t(getattr(w, "gen_amax", None)),
+        }
+
+    def make_problem(self, w, tensors, memory=TOP_MEM_DEVICE, max_iters=None, eps=None, check_every=1):
+        pb = top_problem()
+        pb.B = int(np.asarray(w.seg_offset).shape[0] - 1)
+        pb.memory = memory
+        for k in ("seg_offset", "waypoints", "durations", "start_state", "end_state", "vbox", "ball_c",
+                  "ball_r", "vnorm", "gen_vmax", "gen_amax"):
+            x = tensors.get(k)
+            if x is None:
+                setattr(pb, k, None)
+            elif memory == TOP_MEM_DEVICE:
+                setattr(pb, k, x.data_ptr())
+            else:
+                setattr(pb, k, x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr())
+        pb.mode = {"pin": TOP_PIN, "free": TOP_FREE}[w.mode]
+        pb.inner = {"closed": TOP_CLOSED_FORM, "numeric": TOP_NUMERIC}[getattr(w, "inner", "closed")]
+        pb.rho = float(w.rho)
+        pb.eps = float(w.eps if eps is None else eps)
+        pb.max_iters = int(w.max_iters if max_iters is None else max_iters)
+        pb.check_every = int(check_every)
+        pb.M_box = int(getattr(w, "M_box", 0) or 0)
+        pb.M_ball = int(getattr(w, "M_ball", 0) or 0)
+        pb.M_vn = int(getattr(w, "M_vn", 0) or 0)
+        pb.M_gen = int(getattr(w, "M_gen", 0) or 0)
+        return pb
+
+    def alloc_result(self, B: int, S: int, max_iters: int = 0, history: bool = False, device="cuda"):
+        torch = self.torch
+        out = {
+            "coeffs": torch.empty((S, 3, 8), dtype=torch.float64, device=device),
+            "cost": torch.empty(B, dtype=torch.float64, device=device),
+            "r_primal": torch.empty(B, dtype=torch.float64, device=device),
+            "r_dual": torch.empty(B, dtype=torch.float64, device=device),
+            "iters": torch.empty(B, dtype=torch.int32, device=device),
+            "status": torch.empty(B, dtype=torch.int32, device=device),
+        }
+        if history:
+            out["history"] = torch.full((max(1, max_iters), B, 2), float("nan"), dtype=torch.float64, device=device)
+        return out
+
+    @staticmethod
+    def result_struct(out):
+        r = top_result()
+        for k in ("coeffs", "cost", "r_primal", "r_dual", "iters", "status", "history"):
+            x = out.get(k)
+            setattr(r, k, None if x is None else (x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()))
+        return r
+
+    def solve(self, w, history: bool = False, max_iters=None, eps=None, check_every: int = 1, stream=None,
+              tensors=None, out=None):
+        """Solve a Workload on the GPU; returns a dict of device tensors."""
+        torch = self.torch
+        tensors = tensors if tensors is not None else self.device_inputs(w)
+        K = int(w.max_iters if max_iters is None else max_iters)
+        B = int(np.asarray(w.seg_offset).shape[0] - 1)
+        S = int(np.asarray(w.seg_offset)[-1])
+        out = out if out is not None else self.alloc_result(B, S, K, history)
+        pb = self.make_problem(w, tensors, TOP_MEM_DEVICE, max_iters=K, eps=eps, check_every=check_every)
+        r = self.result_struct(out)
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        rc = top_solve(self.handle, pb, r, s)
+        if rc != TOP_OK:
+            raise TopError(rc, "top_solve", top_last_cuda_error(self.handle))
+        return out
+
+    def solve_host(self, w, history: bool = False, max_iters=None, eps=None, check_every: int = 1,
+                   arrays=None, out=None, stream=None):
+        """Solve with HOST buffers (numpy): the library stages the copies itself."""
+        B = int(np.asarray(w.seg_offset).shape[0] - 1)
+        S = int(np.asarray(w.seg_offset)[-1])
+        K = int(w.max_iters if max_iters is None else max_iters)
+        if arrays is None:
+            arrays = {
+                "seg_offset": np.ascontiguousarray(w.seg_offset, dtype=np.int32),
+                "waypoints": np.ascontiguousarray(w.waypoints, dtype=np.float64),
+                "durations": np.ascontiguousarray(w.durations, dtype=np.float64),
+                "start_state": np.ascontiguousarray(w.start_state, dtype=np.float64),
+                "end_state": np.ascontiguousarray(w.end_state, dtype=np.float64),
+            }
+            for k in ("vbox", "ball_c", "ball_r", "vnorm", "gen_vmax", "gen_amax"):
+                x = getattr(w, k, None)
+                arrays[k] = None if x is None else np.ascontiguousarray(x, dtype=np.float64)
+        if out is None:
+            out = {"coeffs": np.empty((S, 3, 8)), "cost": np.empty(B), "r_primal": np.empty(B),
+                   "r_dual": np.empty(B), "iters": np.empty(B, np.int32), "status": np.empty(B, np.int32)}
+            if history:
+                out["history"] = np.full((max(1, K), B, 2), np.nan)
+        pb = self.make_problem(w, arrays, TOP_MEM_HOST, max_iters=K, eps=eps, check_every=check_every)
+        r = self.result_struct(out)
+        s = stream if stream is not None else self.torch.cuda.current_stream().cuda_stream
+        rc = top_solve(self.handle, pb, r, s)
+        if rc != TOP_OK:
+            raise TopError(rc, "top_solve", top_last_cuda_error(self.handle))
+        return out

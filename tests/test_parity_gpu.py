@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Both sides get the same seeded inputs and run the same number of CADMM
+iterations; coefficients are compared on the time-normalised scale
+c_k T^k (relative 2-norm over the batch), costs relative, iteration counts
+and statuses exactly.  Tolerances: 1e-9 for the FP64 path, 1e-4 for the
+FP32 path (FP32 state with FP64 KKT inverses and FP64 reductions).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_10290_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-9, "fp32": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2507_10290_gb300 import build
+    build.build()
+    from paper_2507_10290_gb300 import top
+    return top
+
+
+_solvers = {}
+
+
+def solver(T, precision, max_batch=4096, max_segments=1100000, max_samples=16):
+    key = (precision, max_batch, max_segments, max_samples)
+    if key not in _solvers:
+        _solvers[key] = T.Solver(max_batch, max_segments, precision=precision, max_samples=max_samples)
+    return _solvers[key]
+
+
+def to_np(out):
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def scaled(c, T):
+    return c * np.asarray(T)[:, None, None] ** np.arange(8)[None, None, :]
+
+
+def compare(g, o, w, tol, check_iters=True):
+    """Returns the measured errors after asserting them."""
+    T = w.durations
+    if w.S:
+        ref = scaled(o["coeffs"], T)
+        err = float(np.linalg.norm(scaled(g["coeffs"], T) - ref) / max(np.linalg.norm(ref), 1e-300))
+        assert err <= tol, f"coefficient error {err:.3e} > {tol:.1e}"
+    else:
+        err = 0.0
+    cref = np.abs(o["cost"]).max() if len(o["cost"]) else 0.0
+    cerr = float(np.abs(g["cost"] - o["cost"]).max() / max(cref, 1e-300)) if len(o["cost"]) else 0.0
+    assert cerr <= tol, f"cost error {cerr:.3e}"
+    if check_iters:
+        assert np.array_equal(g["iters"], o["iters"]), (g["iters"], o["iters"])
+        assert np.array_equal(g["status"], o["status"]), (g["status"], o["status"])
+    for k in ("r_primal", "r_dual"):
+        scale = max(np.abs(o[k]).max(), 1e-12)
+        assert np.abs(g[k] - o[k]).max() <= max(tol, 1e-6) * 10 * scale, k
+    return err, cerr
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_single_box_N8(T, precision):
+    w = W.single_box()
+    o = oracle.solve(w)
+    g = to_np(solver(T, precision).solve(w))
+    compare(g, o, w, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("mode", ["pin", "free"])
+def test_edge_shapes(T, precision, mode):
+    # ragged batch: single-segment, empty, lengths straddling warps and a CTA
+    Ns = [1, 0, 2, 3, 33, 31, 32, 64, 0, 5, 127, 1]
+    w = W.tiny(seed=12, N=Ns, mode=mode).with_(max_iters=60)
+    o = oracle.solve(w)
+    g = to_np(solver(T, precision).solve(w))
+    compare(g, o, w, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_zero_and_one_iteration(T, precision):
+    w = W.tiny(seed=3, N=[4, 7], mode="pin")
+    for K in (0, 1):
+        o = oracle.solve(w.with_(max_iters=K))
+        g = to_np(solver(T, precision).solve(w, max_iters=K))
+        compare(g, o, w, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_subset_300_iterations(T, precision):
+    full = W.batch(B=64)
+    w = full
+    o = oracle.solve(w)
+    g = to_np(solver(T, precision).solve(w))
+    compare(g, o, w, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_corridor_box_and_ball(T, precision):
+    N = 64 if precision == "fp64" else 128
+    w = W.corridor(N=N)
+    o = oracle.solve(w)
+    g = to_np(solver(T, precision).solve(w))
+    compare(g, o, w, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_velocity_norm_projection(T, precision):
+    w = W.tiny(seed=21, N=[6, 9], mode="free", step=3.0).with_(M_vn=8, vnorm=np.array([2.0, 2.5]),
+                                                                max_iters=150)
+    o = oracle.solve(w)
+    g = to_np(solver(T, precision).solve(w))
+    compare(g, o, w, TOL[precision])
+
+
+def test_stopping_rule_and_history_fp64(T):
+    w = W.tiny(seed=1, N=[8, 5, 12], mode="free", T_range=(0.8, 1.6)).with_(eps=1e-3, max_iters=5000)
+    o = oracle.solve(w, history=True)
+    g = to_np(solver(T, "fp64").solve(w, history=True, check_every=1))
+    compare(g, o, w, TOL["fp64"])
+    k = int(o["iters"].max())
+    for b in range(w.B):
+        kb = int(o["iters"][b])
+        # residuals are differences of O(|z|) quantities: absolute rounding ~ 1e-9 of their peak
+        scale = np.abs(o["history"][:kb, b]).max(axis=0)
+        assert np.all(np.abs(g["history"][:kb, b] - o["history"][:kb, b]) <= 1e-9 * scale)
+
+
+def test_host_memory_path_matches_device_path(T):
+    w = W.tiny(seed=5, N=[10, 3, 20], mode="pin").with_(max_iters=80)
+    s = solver(T, "fp32")
+    gd = to_np(s.solve(w))
+    gh = s.solve_host(w)
+    for k in ("coeffs", "cost", "r_primal", "r_dual", "iters", "status"):
+        assert np.array_equal(gd[k], gh[k]), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_run_to_run_deterministic(T, precision):
+    w = W.batch(B=32, seed=4).with_(max_iters=50)
+    s = solver(T, precision)
+    a = to_np(s.solve(w))
+    b = to_np(s.solve(w))
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_invalid_inputs_are_rejected(T):
+    s = solver(T, "fp32", max_batch=8, max_segments=64)
+    w = W.tiny(seed=2, N=[4, 4], mode="pin")
+    bad = w.with_(durations=np.where(np.arange(8) == 3, -1.0, w.durations))
+    with pytest.raises(T.TopError) as e:
+        s.solve(bad)
+    assert e.value.code == T.TOP_E_INVAL
+    big = W.tiny(seed=2, N=[40, 40], mode="pin")
+    with pytest.raises(T.TopError) as e:
+        s.solve(big)
+    assert e.value.code == T.TOP_E_NOMEM
+    num = w.with_(inner="numeric", M_box=2, vbox=np.array([1.0, 1.0]), M_gen=2,
+                  gen_vmax=np.ones(2), gen_amax=np.ones(2))
+    with pytest.raises(T.TopError) as e:
+        s.solve(num)
+    assert e.value.code == T.TOP_E_NOTSUP
+    # the handle still works afterwards
+    o = oracle.solve(w)
+    compare(to_np(s.solve(w)), o, w, TOL["fp32"])
+
+
+def test_full_size_batch_sampled(T):
+    """The 4096-trajectory workload at full size, 300 iterations, FP32: sampled
+    trajectories against the oracle (each trajectory is independent)."""
+    w = W.batch()
+    g = to_np(solver(T, "fp32").solve(w))
+    rng = np.random.default_rng(0)
+    ids = sorted(rng.choice(w.B, size=12, replace=False).tolist())
+    sub = w.subset(ids)
+    o = oracle.solve(sub)
+    gs = {k: v[ids] for k, v in g.items() if k != "coeffs"}
+    segs = np.concatenate([np.arange(w.seg_offset[b], w.seg_offset[b + 1]) for b in ids])
+    gs["coeffs"] = g["coeffs"][segs]
+    compare(gs, o, sub, TOL["fp32"])
+    assert np.all(np.isfinite(g["coeffs"])) and np.all(g["iters"] == 300)
