@@ -54,6 +54,11 @@ extern "C" {
 #define TOP_E_NOTSUP   -5  /* a valid but unsupported combination (e.g. numeric step with box rows) */
 #define TOP_E_STATE    -6  /* call out of order (e.g. top_grad without a matching top_solve) */
 #define TOP_E_NUMERIC  -7  /* a local KKT matrix was not positive definite in FP64 */
+#define TOP_E_LIMIT    -8  /* the problem exceeds the fixed scratch of top_solve_noalloc */
+
+/* fixed limits of top_solve_noalloc */
+#define TOP_NOALLOC_MAX_SEGMENTS 16384
+#define TOP_NOALLOC_MAX_BATCH    1024
 
 /* per-trajectory status written to top_result.status */
 #define TOP_CONVERGED      0  /* ||r_p|| < N eps and ||r_d|| < N eps (Eq. 21) */
@@ -157,6 +162,26 @@ int top_grad(top_handle *h, const top_problem *pb, const double *dJ, double *dwa
  * entries written, or TOP_E_INVAL / TOP_E_STATE (profiling off). */
 int top_set_profiling(top_handle *h, int enable);
 int top_kernel_times(const top_handle *h, float *ms, int n);
+
+/* A solve for callers that cannot allocate device memory (a framework whose
+ * allocator forbids side allocations, a real-time loop that must not call
+ * cudaMalloc, a process with a memory budget fixed at start-up): it needs no
+ * handle and calls no cudaMalloc, cudaFree or allocating library routine.
+ * The paper has no counterpart; it is the same computation as top_solve with
+ * the resident kernel.  Its scratch (local-matrix inverses, CTA pack table,
+ * error flag) is one file-scope device array of about 5 MB that every GPU
+ * which loads the library keeps until the process exits.
+ *   pb, res    device memory only (TOP_MEM_DEVICE); closed-form step only.
+ *   precision  TOP_FP32 or TOP_FP64.
+ * Limits: S <= TOP_NOALLOC_MAX_SEGMENTS, B <= TOP_NOALLOC_MAX_BATCH and every
+ * trajectory short enough for one CTA of the resident kernel; otherwise
+ * TOP_E_LIMIT.  The first call on a device looks up the array's device
+ * address (once, with that device current): make it before any stream
+ * capture.  All calls share the array; calls whose GPU work overlaps race on
+ * it and must be serialised by the caller.  Synchronises `stream` like
+ * top_solve.  Errors: TOP_E_INVAL, TOP_E_NOTSUP, TOP_E_LIMIT, TOP_E_NUMERIC,
+ * TOP_E_CUDA. */
+int top_solve_noalloc(const top_problem *pb, top_result *res, int precision, void *stream);
 
 /* Free the workspace and the handle (NULL is a no-op). */
 void top_destroy(top_handle *h);

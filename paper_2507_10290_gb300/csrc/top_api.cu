@@ -152,6 +152,7 @@ const char *top_strerror(int code) {
     case TOP_E_NOTSUP: return "unsupported combination of options";
     case TOP_E_STATE: return "call out of order";
     case TOP_E_NUMERIC: return "local KKT matrix not positive definite";
+    case TOP_E_LIMIT: return "problem larger than the fixed scratch of top_solve_noalloc";
     default: return "unknown error code";
   }
 }

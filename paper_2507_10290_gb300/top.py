@@ -43,6 +43,9 @@ TOP_E_TIMEOUT = _K["TOP_E_TIMEOUT"]
 TOP_E_NOTSUP = _K["TOP_E_NOTSUP"]
 TOP_E_STATE = _K["TOP_E_STATE"]
 TOP_E_NUMERIC = _K["TOP_E_NUMERIC"]
+TOP_E_LIMIT = _K["TOP_E_LIMIT"]
+TOP_NOALLOC_MAX_SEGMENTS = _K["TOP_NOALLOC_MAX_SEGMENTS"]
+TOP_NOALLOC_MAX_BATCH = _K["TOP_NOALLOC_MAX_BATCH"]
 TOP_CONVERGED, TOP_NOT_CONVERGED, TOP_NONFINITE = 0, 1, 2
 TOP_FP32, TOP_FP64 = 0, 1
 TOP_PIN, TOP_FREE = 0, 1
@@ -89,6 +92,8 @@ _lib.top_strerror.argtypes = [C.c_int]
 _lib.top_strerror.restype = C.c_char_p
 _lib.top_last_cuda_error.argtypes = [C.c_void_p]
 _lib.top_last_cuda_error.restype = C.c_int
+_lib.top_solve_noalloc.argtypes = [C.POINTER(top_problem), C.POINTER(top_result), C.c_int, C.c_void_p]
+_lib.top_solve_noalloc.restype = C.c_int
 _lib.top_set_profiling.argtypes = [C.c_void_p, C.c_int]
 _lib.top_set_profiling.restype = C.c_int
 _lib.top_kernel_times.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int]
@@ -121,6 +126,12 @@ def top_strerror(code: int) -> str:
 
 def top_last_cuda_error(handle) -> int:
     return _lib.top_last_cuda_error(handle)
+
+
+def top_solve_noalloc(problem: top_problem, result: top_result, precision: int, stream: int = 0) -> int:
+    """int top_solve_noalloc(const top_problem*, top_result*, int precision, void* stream):
+    the solve for callers that cannot allocate device memory (fixed scratch, no handle)."""
+    return _lib.top_solve_noalloc(C.byref(problem), C.byref(result), int(precision), C.c_void_p(stream))
 
 
 def top_set_profiling(handle, enable: bool) -> int:
