@@ -40,10 +40,10 @@
  *       to the centre o.
  *   R9  general convex constraints use g0 = ||A c||^2 - g_max^2 and
  *       g = max(0, g0)^2 (Eq. 15); y <- y + rho*g (Eq. 17 "updated like
- *       Eq. 7c").  L-BFGS: memory m, initial scaling gamma = s'y / y'y, Armijo
- *       backtracking (c1 = 1e-4, halving), run in the Jacobi-equilibrated
- *       variable, started from the minimiser of the quadratic part, stopped
- *       on an infinity-norm gradient test.
+ *       Eq. 7c").  L-BFGS: memory m, initial inverse Hessian = inverse of
+ *       the quadratic part's Hessian (2 Qt + rho Mt^T E Mt), Armijo
+ *       backtracking (c1 = 1e-4, halving), started from the minimiser of the
+ *       quadratic part, stopped when g^T K^-1 g <= tol^2 rhs^T K^-1 rhs.
  *   R10 dual residual stacked per segment: rho * Mt_i^T E_i (zt_i^{k+1} - zt_i^k).
  *
  * Compile-time type: OR_REAL (default double; the oracle's own rounding is
@@ -390,48 +390,39 @@ static real dotn(const real *a, const real *b, int n) {
   return acc;
 }
 
-static real infnorm(const real *a, int n) {
-  real m = 0;
-  for (int i = 0; i < n; ++i) { real v = a[i] < 0 ? -a[i] : a[i]; if (v > m) m = v; }
-  return m;
-}
-
-/* L-BFGS (R9) on F(S x); c in/out is the start point / minimiser. returns iterations. */
-static int lbfgs_solve(const num_ctx *cx, real *c, real tol, int max_it, int mem) {
-  const real *S = cx->sd->S;
-  real x[NL], g[NL], gc[NL], xn[NL], gn[NL], d[NL], alpha[64];
+/* L-BFGS (R9) on F with the initial inverse-Hessian approximation
+ * H0 = K^-1, K = 2 Qt + rho Mt^T E Mt the Hessian of F's quadratic part
+ * (factored by chol_equil); c in/out is the start point / minimiser.  Stops
+ * when g^T K^-1 g <= tol^2 * scale.  Returns the iteration count. */
+static int lbfgs_solve(const num_ctx *cx, real *c, real tol, real scale, int max_it, int mem) {
+  const seg_data *sd = cx->sd;
+  real g[NL], xn[NL], gn[NL], d[NL], q[NL], alpha[64];
   real *sv = (real *)calloc((size_t)mem * NL, sizeof(real));
   real *yv = (real *)calloc((size_t)mem * NL, sizeof(real));
   real *rh = (real *)calloc((size_t)mem, sizeof(real));
   int npair = 0, head = 0, it = 0;
-  for (int i = 0; i < NL; ++i) x[i] = c[i] / S[i];
-  real cc[NL];
-  for (int i = 0; i < NL; ++i) cc[i] = S[i] * x[i];
-  real f = num_eval(cx, cc, gc);
-  for (int i = 0; i < NL; ++i) g[i] = S[i] * gc[i];
+  real f = num_eval(cx, c, g);
   for (it = 0; it < max_it; ++it) {
-    if (infnorm(g, NL) <= tol) break;
-    /* two-loop recursion */
-    for (int i = 0; i < NL; ++i) d[i] = -g[i];
-    for (int q = 0; q < npair; ++q) {
-      int idx = (head - 1 - q + mem) % mem;
-      alpha[q] = rh[idx] * dotn(sv + idx * NL, d, NL);
-      for (int i = 0; i < NL; ++i) d[i] -= alpha[q] * yv[idx * NL + i];
+    chol_solve(NL, sd->L, sd->S, g, d);
+    if (!(dotn(g, d, NL) > tol * tol * scale)) break;
+    /* two-loop recursion, H0 = K^-1 */
+    for (int i = 0; i < NL; ++i) q[i] = g[i];
+    for (int k = 0; k < npair; ++k) {
+      int idx = (head - 1 - k + mem) % mem;
+      alpha[k] = rh[idx] * dotn(sv + idx * NL, q, NL);
+      for (int i = 0; i < NL; ++i) q[i] -= alpha[k] * yv[idx * NL + i];
     }
-    real gamma = 1;
-    if (npair > 0) {
-      int idx = (head - 1 + mem) % mem;
-      gamma = dotn(sv + idx * NL, yv + idx * NL, NL) / dotn(yv + idx * NL, yv + idx * NL, NL);
-    }
-    for (int i = 0; i < NL; ++i) d[i] *= gamma;
-    for (int q = npair - 1; q >= 0; --q) {
-      int idx = (head - 1 - q + mem) % mem;
+    chol_solve(NL, sd->L, sd->S, q, d);
+    for (int k = npair - 1; k >= 0; --k) {
+      int idx = (head - 1 - k + mem) % mem;
       real beta = rh[idx] * dotn(yv + idx * NL, d, NL);
-      for (int i = 0; i < NL; ++i) d[i] += (alpha[q] - beta) * sv[idx * NL + i];
+      for (int i = 0; i < NL; ++i) d[i] += (alpha[k] - beta) * sv[idx * NL + i];
     }
+    for (int i = 0; i < NL; ++i) d[i] = -d[i];
     real gd = dotn(g, d, NL);
-    if (!(gd < 0)) { /* not a descent direction: restart from steepest descent */
-      for (int i = 0; i < NL; ++i) d[i] = -g[i];
+    if (!(gd < 0)) { /* not a descent direction: restart from -K^-1 g */
+      chol_solve(NL, sd->L, sd->S, g, d);
+      for (int i = 0; i < NL; ++i) d[i] = -d[i];
       gd = dotn(g, d, NL);
       npair = 0;
     }
@@ -439,28 +430,26 @@ static int lbfgs_solve(const num_ctx *cx, real *c, real tol, int max_it, int mem
     real step = 1, fn = f;
     int ok = 0;
     for (int bt = 0; bt < 60; ++bt) {
-      for (int i = 0; i < NL; ++i) { xn[i] = x[i] + step * d[i]; cc[i] = S[i] * xn[i]; }
-      fn = num_eval(cx, cc, gc);
+      for (int i = 0; i < NL; ++i) xn[i] = c[i] + step * d[i];
+      fn = num_eval(cx, xn, gn);
       if (fn <= f + (real)1e-4 * step * gd) { ok = 1; break; }
       step /= 2;
     }
     if (!ok) break;
-    for (int i = 0; i < NL; ++i) gn[i] = S[i] * gc[i];
-    real sy = 0, yy = 0;
+    real sy = 0;
     real sk[NL], yk[NL];
-    for (int i = 0; i < NL; ++i) { sk[i] = xn[i] - x[i]; yk[i] = gn[i] - g[i]; sy += sk[i] * yk[i]; yy += yk[i] * yk[i]; }
-    if (sy > 0 && yy > 0) {
+    for (int i = 0; i < NL; ++i) { sk[i] = xn[i] - c[i]; yk[i] = gn[i] - g[i]; sy += sk[i] * yk[i]; }
+    if (sy > 0) {
       memcpy(sv + head * NL, sk, sizeof(sk));
       memcpy(yv + head * NL, yk, sizeof(yk));
       rh[head] = 1 / sy;
       head = (head + 1) % mem;
       if (npair < mem) ++npair;
     }
-    memcpy(x, xn, sizeof(x));
-    memcpy(g, gn, sizeof(g));
+    memcpy(c, xn, sizeof(xn));
+    memcpy(g, gn, sizeof(gn));
     f = fn;
   }
-  for (int i = 0; i < NL; ++i) c[i] = S[i] * x[i];
   free(sv); free(yv); free(rh);
   return it;
 }
@@ -578,12 +567,10 @@ static int solve_one(const or_problem *pb, or_result *res, int b) {
         num_ctx cx;
         cx.sd = &sd[i]; cx.zt = zt; cx.u = u + (size_t)i * NR; cx.y = yg + (size_t)i * Mg * 2;
         cx.M_gen = Mg; cx.rho = rho; cx.vmax = pb->gen_vmax[b]; cx.amax = pb->gen_amax[b];
-        real gs[NL];
-        /* tolerance relative to the linear term's size in the equilibrated variable */
-        for (int l = 0; l < NL; ++l) gs[l] = sd[i].S[l] * rhs[l];
-        real scale = infnorm(gs, NL);
-        if (scale < 1) scale = 1;
-        inner_it[i] += lbfgs_solve(&cx, c0, (real)pb->lbfgs_tol * scale, pb->lbfgs_max_iters,
+        /* tolerance relative to the linear term's size in the K^-1 metric */
+        real scale = dotn(rhs, c0, NL);
+        if (!(scale > 0)) scale = 1;
+        inner_it[i] += lbfgs_solve(&cx, c0, (real)pb->lbfgs_tol, scale, pb->lbfgs_max_iters,
                                    pb->lbfgs_mem > 0 ? pb->lbfgs_mem : 8);
         memcpy(c + (size_t)i * NL, c0, sizeof(c0));
       }
@@ -781,7 +768,7 @@ int oracle_numeric_local(const or_problem *pb, int b, int i_local, const double 
   int s0 = pb->seg_offset[b], N = pb->seg_offset[b + 1] - s0;
   seg_data sd;
   if (build_segment(&sd, pb, b, s0 + i_local, i_local == 0, i_local == N - 1) != 0) return -1;
-  real ztr[NR], ur[NR], rhs[NL], t42[NR], c0[NL], gs[NL];
+  real ztr[NR], ur[NR], rhs[NL], t42[NR], c0[NL];
   real *yr = (real *)calloc((size_t)(pb->M_gen ? pb->M_gen : 1) * 2, sizeof(real));
   for (int q = 0; q < NR; ++q) { ztr[q] = zt[q]; ur[q] = u[q]; }
   for (int q = 0; q < 2 * pb->M_gen; ++q) yr[q] = y[q];
@@ -792,10 +779,9 @@ int oracle_numeric_local(const or_problem *pb, int b, int i_local, const double 
   num_ctx cx;
   cx.sd = &sd; cx.zt = ztr; cx.u = ur; cx.y = yr; cx.M_gen = pb->M_gen; cx.rho = pb->rho;
   cx.vmax = pb->gen_vmax[b]; cx.amax = pb->gen_amax[b];
-  for (int l = 0; l < NL; ++l) gs[l] = sd.S[l] * rhs[l];
-  real scale = infnorm(gs, NL);
-  if (scale < 1) scale = 1;
-  int it = lbfgs_solve(&cx, c0, (real)pb->lbfgs_tol * scale, pb->lbfgs_max_iters,
+  real scale = dotn(rhs, c0, NL);
+  if (!(scale > 0)) scale = 1;
+  int it = lbfgs_solve(&cx, c0, (real)pb->lbfgs_tol, scale, pb->lbfgs_max_iters,
                        pb->lbfgs_mem > 0 ? pb->lbfgs_mem : 8);
   for (int l = 0; l < NL; ++l) c_out[l] = (double)c0[l];
   free(yr);
