@@ -193,7 +193,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(0, target_s=args.ref_seconds)
 
-    w = W.batch(seed=rank)
+    w = W.batch(seed=rank, B=args.trajectories)
     iters = w.max_iters
     S, B = w.S, w.B
     solver = top.Solver(max_batch=B, max_segments=S, precision=args.precision, max_samples=0)
@@ -317,6 +317,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trajectories", type=int, default=4096,
+                    help="batch size (4096 = the benchmark workload; smaller only for profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

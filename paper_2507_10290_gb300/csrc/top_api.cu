@@ -63,6 +63,8 @@ int families(const top_problem *pb) {
     if (pb->M_box > 0) f |= FAM_BOX;
     if (pb->M_ball > 0) f |= FAM_BALL;
     if (pb->M_vn > 0) f |= FAM_VN;
+  } else if (pb->M_gen > 0) {
+    f |= FAM_GEN;
   }
   return f;
 }
@@ -128,7 +130,7 @@ int validate(const top_handle *h, const top_problem *pb, const top_result *res) 
   if (pb->M_ball > 0 && (!pb->ball_c || !pb->ball_r)) return TOP_E_INVAL;
   if (pb->M_vn > 0 && !pb->vnorm) return TOP_E_INVAL;
   if (pb->M_gen > 0 && (!pb->gen_vmax || !pb->gen_amax)) return TOP_E_INVAL;
-  if (pb->inner == TOP_NUMERIC) return TOP_E_NOTSUP;  // numerical step: not in this build yet
+  if (pb->inner == TOP_NUMERIC && (pb->M_box || pb->M_ball || pb->M_vn)) return TOP_E_NOTSUP;
   if (pb->inner == TOP_CLOSED_FORM && pb->M_gen) return TOP_E_NOTSUP;
   if (pb->B > 0 && (!pb->seg_offset || !pb->waypoints || !pb->start_state || !pb->end_state))
     return TOP_E_INVAL;
@@ -403,6 +405,8 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     const size_t o_eS = take(rb * 21 * (size_t)S), o_eE = take(rb * 21 * (size_t)S), o_ch = take(rb * 24 * (size_t)S);
     const size_t o_yb = take(rb * 6 * Mb * (size_t)S), o_qb = take(rb * 3 * Mq * (size_t)S);
     const size_t o_qv = take(rb * 3 * Mv * (size_t)S);
+    const int Mg = (fam & FAM_GEN) ? pb.M_gen : 0;
+    const size_t o_yg = take(rb * 2 * Mg * (size_t)S);
     const size_t o_rp = take(sizeof(double) * total), o_rd = take(sizeof(double) * total);
     const size_t o_done = take(sizeof(int) * nl), o_trp = take(sizeof(double) * nl), o_trd = take(sizeof(double) * nl);
     const size_t o_lt = take(sizeof(int) * (2 * (size_t)nl + 1));
@@ -430,6 +434,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     sa.z = base + o_z; sa.uL = base + o_uL; sa.dz = base + o_dz; sa.uRp = base + o_uRp; sa.uR0 = base + o_uR0;
     sa.eS = base + o_eS; sa.eE = base + o_eE; sa.ch = base + o_ch;
     sa.ybox = base + o_yb; sa.qball = base + o_qb; sa.qvn = base + o_qv;
+    sa.ygen = base + o_yg; sa.inner_iters = nullptr;
     sa.rp2 = (double *)(base + o_rp); sa.rd2 = (double *)(base + o_rd);
     sa.done = (int *)(base + o_done); sa.tr_rp = (double *)(base + o_trp); sa.tr_rd = (double *)(base + o_trd);
     if (h->profiling) cudaEventRecord(h->ev[4], st);
@@ -457,10 +462,155 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   return TOP_OK;
 }
 
-int top_grad(top_handle *h, const top_problem *pb, const double *dJ, double *dwaypoints, double *ddurations,
+int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *dwaypoints, double *ddurations,
              void *stream) {
-  (void)h; (void)pb; (void)dJ; (void)dwaypoints; (void)ddurations; (void)stream;
-  return TOP_E_NOTSUP;
+  if (!h || !pb_in || !dJ || !dwaypoints || !ddurations) return TOP_E_INVAL;
+  top_result fake{};
+  fake.coeffs = fake.cost = fake.r_primal = fake.r_dual = ddurations;
+  fake.iters = fake.status = (int32_t *)ddurations;
+  int rc = validate(h, pb_in, &fake);
+  if (rc != TOP_OK) return rc;
+  if (pb_in->M_box || pb_in->M_ball || pb_in->M_vn || pb_in->M_gen) return TOP_E_NOTSUP;
+  cudaStream_t st = (cudaStream_t)stream;
+  TOP_CUDA(h, cudaSetDevice(h->device));
+  const int B = pb_in->B;
+  if (B == 0) return TOP_OK;
+  const bool host = pb_in->memory == TOP_MEM_HOST;
+  if (host) {
+    std::memcpy(h->h_off, pb_in->seg_offset, sizeof(int32_t) * (B + 1));
+  } else {
+    TOP_CUDA(h, cudaMemcpyAsync(h->h_off, pb_in->seg_offset, sizeof(int32_t) * (B + 1),
+                                cudaMemcpyDeviceToHost, st));
+    TOP_CUDA(h, cudaStreamSynchronize(st));
+  }
+  const int32_t *off = h->h_off;
+  if (off[0] != 0) return TOP_E_INVAL;
+  for (int b = 0; b < B; ++b)
+    if (off[b + 1] < off[b]) return TOP_E_INVAL;
+  const int S = off[B];
+  if (S > h->cfg.max_segments) return TOP_E_NOMEM;
+  if (S > 0 && !pb_in->durations) return TOP_E_INVAL;
+  const size_t Jn = (size_t)S + B;
+  const int K = pb_in->max_iters;
+  const int ckpt = h->cfg.ckpt_interval > 0 ? h->cfg.ckpt_interval : 10;
+  const int nblk = K > 0 ? (K + ckpt - 1) / ckpt : 0;
+  // segment list: every non-empty trajectory
+  int nl = 0, total = 0;
+  int *lt_b = h->h_lt, *lt_pre = h->h_lt + h->cfg.max_batch;
+  lt_pre[0] = 0;
+  for (int b = 0; b < B; ++b) {
+    const int nb = off[b + 1] - off[b];
+    if (nb > 0) { lt_b[nl] = b; total += nb; lt_pre[++nl] = total; }
+  }
+  // ---- workspace ----
+  const size_t rb = rbytes(h);
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes, 256); return at; };
+  const size_t bz = rb * 21 * Jn, buRp = rb * 3 * Jn, buR0 = rb * 12 * (size_t)B;
+  const size_t o_z = take(bz), o_uL = take(bz), o_dz = take(bz), o_uRp = take(buRp), o_uR0 = take(buR0);
+  const size_t o_eS = take(rb * 21 * (size_t)S), o_eE = take(rb * 21 * (size_t)S), o_ch = take(rb * 24 * (size_t)S);
+  const size_t o_rp = take(sizeof(double) * total), o_rd = take(sizeof(double) * total);
+  const size_t o_done = take(sizeof(int) * nl), o_trp = take(sizeof(double) * nl), o_trd = take(sizeof(double) * nl);
+  const size_t o_lt = take(sizeof(int) * (2 * (size_t)nl + 1));
+  const size_t o_ck = take((bz * 2 + buRp + buR0 + 4 * 256) * (size_t)nblk);
+  const size_t o_tape = take((bz * 2 + buRp + buR0 + 4 * 256) * (size_t)ckpt);
+  const size_t o_zb = take(bz), o_uLb = take(bz), o_uRb = take(bz), o_uR0b = take(buR0);
+  const size_t o_eSb = take(rb * 21 * (size_t)S), o_eEb = take(rb * 21 * (size_t)S);
+  const size_t o_wbS = take(rb * 21 * (size_t)S), o_wbE = take(rb * 21 * (size_t)S);
+  const size_t o_Tb = take(sizeof(double) * S), o_Pb = take(sizeof(double) * 3 * Jn);
+  const size_t o_dJ = take(sizeof(double) * B), o_dw = take(sizeof(double) * 3 * Jn), o_dT = take(sizeof(double) * S);
+  if (o > h->stream_bytes) {
+    cudaFree(h->d_stream);
+    h->d_stream = nullptr;
+    h->stream_bytes = 0;
+    cudaError_t e = cudaMalloc((void **)&h->d_stream, o);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? TOP_E_NOMEM : cuda_fail(h, e);
+    }
+    h->stream_bytes = o;
+  }
+  unsigned char *base = h->d_stream;
+  // ---- device views of the inputs and outputs ----
+  top_problem pb = *pb_in;
+  const double *d_dJ = dJ;
+  double *d_dw = dwaypoints, *d_dT = ddurations;
+  if (host) {
+    const StagePlan SP = stage_plan(h->cfg.max_batch, h->cfg.max_segments);
+    unsigned char *sb = h->d_stage;
+    TOP_CUDA(h, cudaMemcpyAsync(sb + SP.off_seg, pb_in->seg_offset, sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, st));
+    TOP_CUDA(h, cudaMemcpyAsync(sb + SP.off_wp, pb_in->waypoints, sizeof(double) * 3 * Jn, cudaMemcpyHostToDevice, st));
+    TOP_CUDA(h, cudaMemcpyAsync(sb + SP.off_T, pb_in->durations, sizeof(double) * S, cudaMemcpyHostToDevice, st));
+    TOP_CUDA(h, cudaMemcpyAsync(sb + SP.off_s0, pb_in->start_state, sizeof(double) * 12 * B, cudaMemcpyHostToDevice, st));
+    TOP_CUDA(h, cudaMemcpyAsync(sb + SP.off_s1, pb_in->end_state, sizeof(double) * 12 * B, cudaMemcpyHostToDevice, st));
+    TOP_CUDA(h, cudaMemcpyAsync(base + o_dJ, dJ, sizeof(double) * B, cudaMemcpyHostToDevice, st));
+    pb.seg_offset = (const int32_t *)(sb + SP.off_seg);
+    pb.waypoints = (const double *)(sb + SP.off_wp);
+    pb.durations = (const double *)(sb + SP.off_T);
+    pb.start_state = (const double *)(sb + SP.off_s0);
+    pb.end_state = (const double *)(sb + SP.off_s1);
+    d_dJ = (const double *)(base + o_dJ);
+    d_dw = (double *)(base + o_dw);
+    d_dT = (double *)(base + o_dT);
+  }
+  DevProblem dp{};
+  dp.B = B; dp.S = S;
+  dp.seg_offset = pb.seg_offset; dp.waypoints = pb.waypoints; dp.durations = pb.durations;
+  dp.start_state = pb.start_state; dp.end_state = pb.end_state;
+  dp.mode = pb.mode; dp.inner = TOP_CLOSED_FORM; dp.rho = pb.rho; dp.eps = 0.0;
+  dp.max_iters = K; dp.check_every = 1;
+  DevResult dr{};
+  TOP_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+  const bool fp64 = h->cfg.precision == TOP_FP64;
+  {
+    int e = launch_kinv(dp, pb.rho, fp64 ? nullptr : h->G, fp64 ? h->G : nullptr, h->d_err, st);
+    if (e) return cuda_fail(h, (cudaError_t)e);
+  }
+  TOP_CUDA(h, cudaMemsetAsync(d_dw, 0, sizeof(double) * 3 * Jn, st));
+  TOP_CUDA(h, cudaMemsetAsync(d_dT, 0, sizeof(double) * S, st));
+  if (nl > 0 && K > 0) {
+    TOP_CUDA(h, cudaMemcpyAsync(base + o_lt, lt_b, sizeof(int) * nl, cudaMemcpyHostToDevice, st));
+    TOP_CUDA(h, cudaMemcpyAsync(base + o_lt + sizeof(int) * nl, lt_pre, sizeof(int) * (nl + 1),
+                                cudaMemcpyHostToDevice, st));
+    StreamArgs sa{};
+    sa.p = dp; sa.r = dr; sa.G = h->G;
+    sa.lt_b = (const int *)(base + o_lt);
+    sa.lt_prefix = (const int *)(base + o_lt) + nl;
+    sa.nl = nl; sa.total = total; sa.S = S; sa.Jn = (int)Jn;
+    sa.z = base + o_z; sa.uL = base + o_uL; sa.dz = base + o_dz; sa.uRp = base + o_uRp; sa.uR0 = base + o_uR0;
+    sa.eS = base + o_eS; sa.eE = base + o_eE; sa.ch = base + o_ch;
+    sa.ybox = sa.qball = sa.qvn = sa.ygen = nullptr;
+    sa.inner_iters = nullptr;
+    sa.rp2 = (double *)(base + o_rp); sa.rd2 = (double *)(base + o_rd);
+    sa.done = (int *)(base + o_done); sa.tr_rp = (double *)(base + o_trp); sa.tr_rd = (double *)(base + o_trd);
+    AdjArgs aa{};
+    aa.f = sa;
+    aa.zb = base + o_zb; aa.uLb = base + o_uLb; aa.uRb = base + o_uRb; aa.uR0b = base + o_uR0b;
+    aa.eSb = base + o_eSb; aa.eEb = base + o_eEb; aa.wbS = base + o_wbS; aa.wbE = base + o_wbE;
+    aa.Tbar = (double *)(base + o_Tb); aa.Pbar = (double *)(base + o_Pb); aa.dJ = d_dJ;
+    TOP_CUDA(h, cudaMemsetAsync(base + o_zb, 0, o_eSb - o_zb, st));        // zb, uLb, uRb, uR0b
+    TOP_CUDA(h, cudaMemsetAsync(base + o_wbS, 0, o_Tb - o_wbS, st));       // wbS, wbE
+    TOP_CUDA(h, cudaMemsetAsync(base + o_Tb, 0, o_dJ - o_Tb, st));         // Tbar, Pbar
+    const size_t bytes[4] = {bz, bz, buRp, buR0};
+    std::vector<void *> ck((size_t)nblk * 4), tape((size_t)ckpt * 4);
+    size_t oc = o_ck, ot = o_tape;
+    for (int c = 0; c < nblk; ++c)
+      for (int q = 0; q < 4; ++q) { ck[(size_t)c * 4 + q] = base + oc; oc = align_up(oc + bytes[q], 256); }
+    for (int c = 0; c < ckpt; ++c)
+      for (int q = 0; q < 4; ++q) { tape[(size_t)c * 4 + q] = base + ot; ot = align_up(ot + bytes[q], 256); }
+    int e = fp64 ? launch_adjoint_f64(sa, aa, ckpt, ck.data(), tape.data(), bytes, d_dw, d_dT, st)
+                 : launch_adjoint_f32(sa, aa, ckpt, ck.data(), tape.data(), bytes, d_dw, d_dT, st);
+    if (e) return cuda_fail(h, (cudaError_t)e);
+  }
+  if (host) {
+    TOP_CUDA(h, cudaMemcpyAsync(dwaypoints, d_dw, sizeof(double) * 3 * Jn, cudaMemcpyDeviceToHost, st));
+    TOP_CUDA(h, cudaMemcpyAsync(ddurations, d_dT, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
+  }
+  TOP_CUDA(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TOP_CUDA(h, cudaStreamSynchronize(st));
+  if (*h->h_err & 1) return TOP_E_INVAL;
+  if (*h->h_err & 2) return TOP_E_NUMERIC;
+  return TOP_OK;
 }
 
 }  // extern "C"

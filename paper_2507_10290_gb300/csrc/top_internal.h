@@ -6,7 +6,7 @@
 
 namespace top {
 
-enum Family : int { FAM_BOX = 1, FAM_BALL = 2, FAM_VN = 4 };
+enum Family : int { FAM_BOX = 1, FAM_BALL = 2, FAM_VN = 4, FAM_GEN = 8 };
 
 // A pack is a run of consecutive whole trajectories processed by one CTA of
 // the resident kernel (all of its state stays in shared memory for every
@@ -105,6 +105,8 @@ struct StreamArgs {
   void *eS, *eE;           // [21][S]
   void *ch;                // [24][S]
   void *ybox, *qball, *qvn;  // [6 M_box][S], [3 M_ball][S], [3 M_vn][S]
+  void *ygen;              // [2 M_gen][S] numerical-step duals (velocity, acceleration)
+  int *inner_iters;        // [S] L-BFGS iterations summed over the run (numerical step), or null
   double *rp2, *rd2;       // [total]
   int *done;               // [nl]
   double *tr_rp, *tr_rd;   // [nl]
@@ -116,5 +118,21 @@ int launch_resident_f32(const ResidentArgs &a, int nblocks, int C, size_t smem, 
 int launch_resident_f64(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
 int launch_stream_f32(const StreamArgs &a, int fam, void *stream);
 int launch_stream_f64(const StreamArgs &a, int fam, void *stream);
+// Adjoint of the unrolled iteration (top_grad)
+struct AdjArgs {
+  StreamArgs f;              // forward views (segment list, problem, G)
+  const void *tz, *tuL, *tuRp, *tuR0;  // x^k from the tape
+  void *zb, *uLb, *uRb;      // [21][Jn] adjoint of the junction state
+  void *uR0b;                // [12][B]
+  void *eSb, *eEb;           // [21][S] adjoint of the end derivatives
+  void *wbS, *wbE;           // [21][S] adjoint of the targets
+  double *Tbar;              // [S]
+  double *Pbar;              // [Jn][3]
+  const double *dJ;          // [B]
+};
+int launch_adjoint_f32(const StreamArgs &f, const AdjArgs &a, int ckpt, void *const *ck, void *const *tape,
+                       const size_t *bytes, double *dw, double *dT, void *stream);
+int launch_adjoint_f64(const StreamArgs &f, const AdjArgs &a, int ckpt, void *const *ck, void *const *tape,
+                       const size_t *bytes, double *dw, double *dT, void *stream);
 
 }  // namespace top

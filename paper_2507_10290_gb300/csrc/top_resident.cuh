@@ -142,8 +142,9 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
     for (int k = 0; k < NC; ++k) ch[a][k] = R(0);
 
   const int cev = p.check_every > 0 ? p.check_every : 1;
+  const bool periodic = p.eps > 0.0 || res.history != nullptr;
   for (int k = 0; k < K; ++k) {
-    const bool check = (k == K - 1) || ((p.eps > 0.0 || res.history) && ((k + 1) % cev == 0));
+    const bool check = (k == K - 1) || (periodic && ((k + 1) % cev == 0));
     const bool act = valid && !sdone[tb];
     R eE[AX][ND];
     R eSv[AX][ND];
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
     }
     __syncthreads();
     // ---- 3. junction update (Eq. 18b, 18c) and primal residual (Eq. 19) ----
-    double rp2 = 0.0;
+    R rp2 = R(0);  // this segment's share of ||r_p||^2, only formed on check iterations
     if (act) {
 #pragma unroll
       for (int a = 0; a < AX; ++a) {
@@ -184,8 +185,10 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
           const int idx = (a * ND + r) * J + jE;
           if (!last) {
             const R en = seS[(a * ND + r) * C + l + 1];
-            const R gap = eE[a][r] - en;
-            rp2 += double(gap) * double(gap);
+            if (check) {
+              const R gap = eE[a][r] - en;
+              rp2 += gap * gap;
+            }
             if (pin && r == 0) {
               const R P = sz[idx];
               suL[idx] += eE[a][r] - P;
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
           rd2 += dual_residual_sq(dS, dE, rho, Tk);
         }
       }
-      red_rp[l] = rp2;
+      red_rp[l] = double(rp2);
       red_rd[l] = rd2;
       __syncthreads();
       const int warp = l >> 5, lane = l & 31, nw = C >> 5;

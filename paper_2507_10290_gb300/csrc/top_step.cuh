@@ -193,4 +193,229 @@ __device__ __forceinline__ double segment_cost(const R (&ch)[AX][NC], double t7)
 
 __device__ __forceinline__ bool finite_d(double x) { return x == x && x - x == 0.0; }
 
+// ---------------------------------------------------------------------------
+// Numerical local step for general convex constraints (Sec. III-C.3, Eq.
+// 15-17): per segment, minimise
+//   F(c) = c^T Qt c + rho/2 ||E(Mt c - z~ + u)||^2
+//          + sum_j [rho/2 g_vj^2 + y_vj g_vj + rho/2 g_aj^2 + y_aj g_aj],
+//   g = max(0, ||A c||^2 - g_max^2)^2   (velocity / acceleration norm at t_j)
+// by L-BFGS in the normalised coordinates, with the exact inverse Hessian of
+// the quadratic part (G, precomputed in FP64) as the initial inverse-Hessian
+// approximation, starting from the minimiser of the quadratic part (which is
+// the answer whenever no bound is violated there).  Then y += rho g (Eq. 17).
+// ---------------------------------------------------------------------------
+constexpr int LBFGS_MAX_MEM = 8;
+
+template <class R>
+__device__ __forceinline__ R num_F(const R (&ch)[AX][NC], const R (&w)[AX][2][ND], const SegConst<R> &sc, R rho,
+                                   bool first, bool last, const R *yg, int stride, const R *tabV, const R *tabA,
+                                   int Mg, R vmax, R amax, R (&gr)[AX][NC]) {
+  R F = R(0);
+  const R t7 = sc.s[7];
+#pragma unroll
+  for (int a = 0; a < AX; ++a) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) gr[a][k] = R(0);
+#pragma unroll
+    for (int k = PO; k < NC; ++k) {
+      R acc = R(0);
+#pragma unroll
+      for (int l = PO; l < NC; ++l) acc += R(qhat(k, l)) * ch[a][l];
+      F += t7 * ch[a][k] * acc;
+      gr[a][k] = R(2) * t7 * acc;
+    }
+    R eS[ND], eE[ND], dS[ND], dE[ND];
+    end_derivs(ch[a], sc.s, eS, eE);
+#pragma unroll
+    for (int r = 0; r < ND; ++r) {
+      const R a0 = (first && r >= PO) ? R(0) : eS[r] - w[a][0][r];
+      const R a1 = (last && r >= PO) ? R(0) : eE[r] - w[a][1][r];
+      F += R(0.5) * rho * (a0 * a0 + a1 * a1);
+      dS[r] = sc.s[r] * a0;
+      dE[r] = sc.s[r] * a1;
+    }
+    consensus_rhs(dS, dE, rho, gr[a]);
+  }
+  for (int j = 0; j < Mg; ++j) {
+#pragma unroll
+    for (int kind = 0; kind < 2; ++kind) {
+      const R *tab = kind ? tabA + j * 8 : tabV + j * 8;
+      const R sc_t = kind ? sc.s[2] : sc.s[1];
+      const R gmax = kind ? amax : vmax;
+      R v[AX];
+      R n2 = R(0);
+#pragma unroll
+      for (int a = 0; a < AX; ++a) {
+        R acc = R(0);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) acc += tab[k] * ch[a][k];
+        v[a] = sc_t * acc;
+        n2 += v[a] * v[a];
+      }
+      const R h = n2 - gmax * gmax;
+      if (h > R(0)) {
+        const R g = h * h;
+        const R y = yg[(j * 2 + kind) * stride];
+        F += R(0.5) * rho * g * g + y * g;
+        const R coef = (rho * g + y) * R(4) * h * sc_t;
+#pragma unroll
+        for (int a = 0; a < AX; ++a)
+#pragma unroll
+          for (int k = 0; k < NC; ++k) gr[a][k] += coef * v[a] * tab[k];
+      }
+    }
+  }
+  return F;
+}
+
+template <class R>
+__device__ __forceinline__ R dot24(const R (&x)[AX][NC], const R (&y)[AX][NC]) {
+  R acc = R(0);
+#pragma unroll
+  for (int a = 0; a < AX; ++a)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) acc += x[a][k] * y[a][k];
+  return acc;
+}
+
+// returns the L-BFGS iteration count; ch receives the minimiser, y is advanced
+template <class R>
+__device__ int numeric_step(const SegConst<R> &sc, const R (&w)[AX][2][ND], R rho, bool first, bool last, R *yg,
+                            int stride, const R *tabV, const R *tabA, int Mg, R vmax, R amax, int mem, int max_it,
+                            R tol, R (&ch)[AX][NC]) {
+  // start: minimiser of the quadratic part (the closed-form step without constraint rows)
+  R rhs[AX][NC];
+#pragma unroll
+  for (int a = 0; a < AX; ++a) {
+    R oS[ND], oE[ND];
+#pragma unroll
+    for (int r = 0; r < ND; ++r) {
+      oS[r] = (first && r >= PO) ? R(0) : sc.s[r] * w[a][0][r];
+      oE[r] = (last && r >= PO) ? R(0) : sc.s[r] * w[a][1][r];
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) rhs[a][q] = R(0);
+    consensus_rhs(oS, oE, rho, rhs[a]);
+    apply_g(sc.G, rhs[a], ch[a]);
+  }
+  R scale = dot24(rhs, ch);  // rhs^T G rhs: size of the linear term in the G metric
+  if (!(scale > R(0))) scale = R(1);
+  R g[AX][NC], gn[AX][NC], d[AX][NC], xn[AX][NC];
+  R Fv = num_F(ch, w, sc, rho, first, last, yg, stride, tabV, tabA, Mg, vmax, amax, g);
+  R Sh[LBFGS_MAX_MEM][AX][NC], Yh[LBFGS_MAX_MEM][AX][NC], rh[LBFGS_MAX_MEM], al[LBFGS_MAX_MEM];
+  if (mem > LBFGS_MAX_MEM) mem = LBFGS_MAX_MEM;
+  if (mem < 1) mem = 1;
+  int npair = 0, head = 0, it = 0;
+  for (it = 0; it < max_it; ++it) {
+    // preconditioned gradient norm g^T G g
+#pragma unroll
+    for (int a = 0; a < AX; ++a) apply_g(sc.G, g[a], d[a]);
+    const R gGg = dot24(g, d);
+    if (!(gGg > tol * tol * scale)) break;
+    // two-loop recursion with H0 = G
+#pragma unroll
+    for (int a = 0; a < AX; ++a)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) xn[a][k] = g[a][k];
+    for (int q = 0; q < npair; ++q) {
+      const int idx = (head - 1 - q + mem) % mem;
+      al[q] = rh[idx] * dot24(Sh[idx], xn);
+#pragma unroll
+      for (int a = 0; a < AX; ++a)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) xn[a][k] -= al[q] * Yh[idx][a][k];
+    }
+#pragma unroll
+    for (int a = 0; a < AX; ++a) apply_g(sc.G, xn[a], d[a]);
+    for (int q = npair - 1; q >= 0; --q) {
+      const int idx = (head - 1 - q + mem) % mem;
+      const R be = rh[idx] * dot24(Yh[idx], d);
+#pragma unroll
+      for (int a = 0; a < AX; ++a)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) d[a][k] += (al[q] - be) * Sh[idx][a][k];
+    }
+#pragma unroll
+    for (int a = 0; a < AX; ++a)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) d[a][k] = -d[a][k];
+    R gd = dot24(g, d);
+    if (!(gd < R(0))) {  // not a descent direction: restart from the preconditioned gradient
+#pragma unroll
+      for (int a = 0; a < AX; ++a) {
+        apply_g(sc.G, g[a], d[a]);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) d[a][k] = -d[a][k];
+      }
+      gd = dot24(g, d);
+      npair = 0;
+    }
+    // Armijo backtracking (c1 = 1e-4, halving)
+    R step = R(1), Fn = Fv;
+    bool ok = false;
+    for (int bt = 0; bt < 40; ++bt) {
+#pragma unroll
+      for (int a = 0; a < AX; ++a)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) xn[a][k] = ch[a][k] + step * d[a][k];
+      Fn = num_F(xn, w, sc, rho, first, last, yg, stride, tabV, tabA, Mg, vmax, amax, gn);
+      if (Fn <= Fv + R(1e-4) * step * gd) { ok = true; break; }
+      step *= R(0.5);
+    }
+    if (!ok) break;
+    R sy = R(0);
+    const int slot = head;
+#pragma unroll
+    for (int a = 0; a < AX; ++a)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        Sh[slot][a][k] = xn[a][k] - ch[a][k];
+        Yh[slot][a][k] = gn[a][k] - g[a][k];
+        sy += Sh[slot][a][k] * Yh[slot][a][k];
+      }
+    if (sy > R(0)) {
+      rh[slot] = R(1) / sy;
+      head = (head + 1) % mem;
+      if (npair < mem) ++npair;
+    }
+#pragma unroll
+    for (int a = 0; a < AX; ++a)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) { ch[a][k] = xn[a][k]; g[a][k] = gn[a][k]; }
+    Fv = Fn;
+  }
+  // general-constraint duals (Eq. 17 dual update, y += rho g)
+  for (int j = 0; j < Mg; ++j) {
+#pragma unroll
+    for (int kind = 0; kind < 2; ++kind) {
+      const R *tab = kind ? tabA + j * 8 : tabV + j * 8;
+      const R sc_t = kind ? sc.s[2] : sc.s[1];
+      const R gmax = kind ? amax : vmax;
+      R n2 = R(0);
+#pragma unroll
+      for (int a = 0; a < AX; ++a) {
+        R acc = R(0);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) acc += tab[k] * ch[a][k];
+        n2 += (sc_t * acc) * (sc_t * acc);
+      }
+      const R h = n2 - gmax * gmax;
+      if (h > R(0)) yg[(j * 2 + kind) * stride] += rho * h * h;
+    }
+  }
+  return it;
+}
+
+// acceleration rows: tab[j*8 + k] = k (k-1) tau_j^{k-2}
+template <class R>
+__device__ __forceinline__ void fill_accel_table(R *tab, int M, int tid, int nthreads) {
+  for (int q = tid; q < 8 * M; q += nthreads) {
+    const int j = q / 8 + 1, k = q % 8;
+    const double tau = double(j) / double(M);
+    double t = 1.0;
+    for (int x = 0; x < k - 2; ++x) t *= tau;
+    tab[q] = R(k < 2 ? 0.0 : double(k) * double(k - 1) * t);
+  }
+}
+
 }  // namespace top

@@ -75,6 +75,10 @@ __global__ void stream_init(const StreamArgs A) {
     if (BOX) for (int q = 0; q < 6 * p.M_box; ++q) ybox[(size_t)q * A.S + g] = R(0);
     if (BALL) for (int q = 0; q < 3 * p.M_ball; ++q) qball[(size_t)q * A.S + g] = R(0);
     if (VN) for (int q = 0; q < 3 * p.M_vn; ++q) qvn[(size_t)q * A.S + g] = R(0);
+    if (F & FAM_GEN) {
+      for (int q = 0; q < 2 * p.M_gen; ++q) ((R *)A.ygen)[(size_t)q * A.S + g] = R(0);
+      if (A.inner_iters) A.inner_iters[g] = 0;
+    }
     if (first) { A.done[t] = 0; A.tr_rp[t] = 0.0; A.tr_rd[t] = 0.0; }
   }
 }
@@ -89,6 +93,13 @@ __global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
   if (BOX) fill_sample_table(tabB, Mb, 1, threadIdx.x, blockDim.x);
   if (BALL) fill_sample_table(tabQ, Mq, 0, threadIdx.x, blockDim.x);
   if (VN) fill_sample_table(tabV, Mv, 1, threadIdx.x, blockDim.x);
+  constexpr bool GEN = (F & FAM_GEN) != 0;
+  const int Mg = GEN ? p.M_gen : 0;
+  R *tabGV = tabV + 8 * Mv, *tabGA = tabGV + 8 * Mg;
+  if (GEN) {
+    fill_sample_table(tabGV, Mg, 1, threadIdx.x, blockDim.x);
+    fill_accel_table(tabGA, Mg, threadIdx.x, blockDim.x);
+  }
   __syncthreads();
   const R *z = (const R *)A.z, *uL = (const R *)A.uL, *uRp = (const R *)A.uRp, *uR0 = (const R *)A.uR0;
   const R *Gp = (const R *)A.G;
@@ -109,7 +120,7 @@ __global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
     sc.vnorm = VN ? R(p.vnorm[b]) : R(0);
     sc.brad = BALL ? R(p.ball_r[g]) : R(0);
     for (int a = 0; a < 3; ++a) sc.bo[a] = BALL ? R(p.ball_c[(size_t)g * 3 + a]) : R(0);
-    R wS[AX][ND], wE[AX][ND];
+    R w[AX][2][ND];  // E (z~ - u) at both ends, unscaled
 #pragma unroll
     for (int a = 0; a < AX; ++a)
 #pragma unroll
@@ -119,12 +130,27 @@ __global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
         if (first) us = (r < PO) ? uR0[(size_t)(a * PO + r) * p.B + b] : R(0);
         else if (pin && r == 0) us = uRp[(size_t)a * A.Jn + jS];
         else us = -uL[row + jS];
-        wS[a][r] = (first && r >= PO) ? R(0) : sc.s[r] * (z[row + jS] - us);
-        wE[a][r] = (last && r >= PO) ? R(0) : sc.s[r] * (z[row + jE] - uL[row + jE]);
+        w[a][0][r] = (first && r >= PO) ? R(0) : z[row + jS] - us;
+        w[a][1][r] = (last && r >= PO) ? R(0) : z[row + jE] - uL[row + jE];
       }
     R ch[AX][NC];
-    local_step<R, F>(sc, wS, wE, rho, k == 0, (R *)A.ybox + g, (R *)A.qball + g, (R *)A.qvn + g, A.S, tabB,
-                     tabQ, tabV, Mb, Mq, Mv, ch);
+    if (GEN) {
+      const int its = numeric_step<R>(sc, w, rho, first, last, (R *)A.ygen + g, A.S, tabGV, tabGA, Mg,
+                                      R(p.gen_vmax[b]), R(p.gen_amax[b]), p.lbfgs_mem, p.lbfgs_max_iters,
+                                      R(p.lbfgs_tol), ch);
+      if (A.inner_iters) A.inner_iters[g] += its;
+    } else {
+      R wS[AX][ND], wE[AX][ND];
+#pragma unroll
+      for (int a = 0; a < AX; ++a)
+#pragma unroll
+        for (int r = 0; r < ND; ++r) {
+          wS[a][r] = sc.s[r] * w[a][0][r];
+          wE[a][r] = sc.s[r] * w[a][1][r];
+        }
+      local_step<R, F & 7>(sc, wS, wE, rho, k == 0, (R *)A.ybox + g, (R *)A.qball + g, (R *)A.qvn + g, A.S,
+                           tabB, tabQ, tabV, Mb, Mq, Mv, ch);
+    }
 #pragma unroll
     for (int a = 0; a < AX; ++a) {
       R s7[ND], e7[ND];
@@ -152,7 +178,7 @@ __global__ void __launch_bounds__(256) stream_junction(const StreamArgs A, int c
     if (A.done[t]) continue;
     const bool first = i == 0, last = i == N - 1;
     const int jS = g + b, jE = g + b + 1;
-    double rp2 = 0.0;
+    R rp2 = R(0);
 #pragma unroll
     for (int a = 0; a < AX; ++a)
 #pragma unroll
@@ -161,8 +187,10 @@ __global__ void __launch_bounds__(256) stream_junction(const StreamArgs A, int c
         const R ee = eE[(size_t)(a * ND + r) * A.S + g];
         if (!last) {
           const R en = eS[(size_t)(a * ND + r) * A.S + g + 1];
-          const R gap = ee - en;
-          rp2 += double(gap) * double(gap);
+          if (check) {
+            const R gap = ee - en;
+            rp2 += gap * gap;
+          }
           if (pin && r == 0) {
             const R P = z[row + jE];
             uL[row + jE] += ee - P;
@@ -183,7 +211,7 @@ __global__ void __launch_bounds__(256) stream_junction(const StreamArgs A, int c
           uR0[(size_t)(a * PO + r) * p.B + b] += es - z[row + jS];
         }
       }
-    A.rp2[x] = rp2;
+    if (check) A.rp2[x] = double(rp2);
   }
 }
 
@@ -316,13 +344,14 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
   const DevProblem &p = A.p;
   const int Mb = (fam & FAM_BOX) ? p.M_box : 0, Mq = (fam & FAM_BALL) ? p.M_ball : 0,
             Mv = (fam & FAM_VN) ? p.M_vn : 0;
-  const size_t tab_bytes = sizeof(R) * 8 * (size_t)(Mb + Mq + Mv);
+  const int Mg = (fam & FAM_GEN) ? p.M_gen : 0;
+  const size_t tab_bytes = sizeof(R) * 8 * (size_t)(Mb + Mq + Mv + 2 * Mg);
   void (*init)(const StreamArgs) = nullptr;
   void (*local)(const StreamArgs, int) = nullptr;
   switch (fam) {
 #define TOP_ST_CASE(FV) case FV: init = stream_init<R, FV>; local = stream_local<R, FV>; break;
     TOP_ST_CASE(0) TOP_ST_CASE(1) TOP_ST_CASE(2) TOP_ST_CASE(3)
-    TOP_ST_CASE(4) TOP_ST_CASE(5) TOP_ST_CASE(6) TOP_ST_CASE(7)
+    TOP_ST_CASE(4) TOP_ST_CASE(5) TOP_ST_CASE(6) TOP_ST_CASE(7) TOP_ST_CASE(8)
 #undef TOP_ST_CASE
     default: return (int)cudaErrorInvalidValue;
   }

@@ -232,6 +232,9 @@ class Solver:
         pb.M_ball = int(getattr(w, "M_ball", 0) or 0)
         pb.M_vn = int(getattr(w, "M_vn", 0) or 0)
         pb.M_gen = int(getattr(w, "M_gen", 0) or 0)
+        pb.lbfgs_mem = int(getattr(w, "lbfgs_mem", 0) or 0)
+        pb.lbfgs_max_iters = int(getattr(w, "lbfgs_max_iters", 0) or 0)
+        pb.lbfgs_tol = float(getattr(w, "lbfgs_tol", 0.0) or 0.0)
         return pb
 
     def alloc_result(self, B: int, S: int, max_iters: int = 0, history: bool = False, device="cuda"):
@@ -272,6 +275,25 @@ class Solver:
         if rc != TOP_OK:
             raise TopError(rc, "top_solve", top_last_cuda_error(self.handle))
         return out
+
+    def grad(self, w, dJ=None, max_iters=None, tensors=None, stream=None):
+        """d(sum_b dJ[b] J_b)/d(waypoints, durations) through max_iters unrolled iterations
+        (top_grad); returns device tensors (dwaypoints [S+B,3], ddurations [S])."""
+        torch = self.torch
+        tensors = tensors if tensors is not None else self.device_inputs(w)
+        B = int(np.asarray(w.seg_offset).shape[0] - 1)
+        S = int(np.asarray(w.seg_offset)[-1])
+        if dJ is None:
+            dJ = torch.ones(B, dtype=torch.float64, device="cuda")
+        dJ = torch.as_tensor(dJ, dtype=torch.float64, device="cuda").contiguous()
+        dw = torch.empty((S + B, 3), dtype=torch.float64, device="cuda")
+        dT = torch.empty(S, dtype=torch.float64, device="cuda")
+        pb = self.make_problem(w, tensors, TOP_MEM_DEVICE, max_iters=max_iters, eps=0.0)
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        rc = top_grad(self.handle, pb, dJ.data_ptr(), dw.data_ptr(), dT.data_ptr(), s)
+        if rc != TOP_OK:
+            raise TopError(rc, "top_grad", top_last_cuda_error(self.handle))
+        return dw, dT
 
     def solve_host(self, w, history: bool = False, max_iters=None, eps=None, check_every: int = 1,
                    arrays=None, out=None, stream=None):

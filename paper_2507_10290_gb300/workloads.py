@@ -67,6 +67,9 @@ class Workload:
     M_gen: int = 0
     gen_vmax: Optional[np.ndarray] = None  # [B]
     gen_amax: Optional[np.ndarray] = None  # [B]
+    lbfgs_mem: int = 0          # numerical step settings (0 = the solver's default)
+    lbfgs_max_iters: int = 0
+    lbfgs_tol: float = 0.0
     notes: dict = field(default_factory=dict)
 
     @property

@@ -188,3 +188,25 @@ def test_full_size_batch_sampled(T):
     gs["coeffs"] = g["coeffs"][segs]
     compare(gs, o, sub, TOL["fp32"])
     assert np.all(np.isfinite(g["coeffs"])) and np.all(g["iters"] == 300)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-4)])
+def test_numerical_step_with_active_bounds(T, precision, tol):
+    """General norm bounds through the L-BFGS local step (Sec. III-C.3), with
+    bounds active on several segments; both sides solve every local problem
+    to a tight tolerance, so they agree at the inner optimum."""
+    w = W.general(N=100, v_nom=3.0).with_(max_iters=100, rho=100.0, lbfgs_max_iters=2000,
+                                          lbfgs_tol=1e-12 if precision == "fp64" else 1e-6)
+    o = oracle.solve(w, state=True, lbfgs_tol=1e-12, lbfgs_max_iters=2000)
+    assert (o["inner_iters"] > 0).sum() >= 3, "the bounds must be active somewhere"
+    g = to_np(solver(T, precision).solve(w))
+    compare(g, o, w, tol)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_numerical_step_inactive_equals_closed_form(T, precision):
+    w = W.tiny(seed=8, N=[6, 40, 3], mode="pin").with_(max_iters=60)
+    wn = w.with_(inner="numeric", M_gen=8, gen_vmax=np.full(3, 1e6), gen_amax=np.full(3, 1e6))
+    o = oracle.solve(w)
+    g = to_np(solver(T, precision).solve(wn))
+    compare(g, o, w, TOL[precision])
