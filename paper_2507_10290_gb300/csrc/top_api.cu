@@ -32,6 +32,13 @@ struct top_handle {
   int32_t *h_off = nullptr;   // [max_batch + 1]
   Pack *h_packs = nullptr;    // [max_segments]
   int *h_lt = nullptr;        // [2 * max_batch + 1] streaming trajectory list and prefix
+  // resident plan (packs + trajectory list), reused while the batch layout repeats
+  int *h_tlist = nullptr;     // [max_batch]
+  int *d_tlist = nullptr;     // [max_batch]
+  int32_t *plan_off = nullptr;  // [max_batch + 1] layout the plan was made for
+  bool plan_valid = false;
+  int plan_B = -1, plan_cap = -1, plan_npack = 0, plan_max_nseg = 0, plan_max_ntraj = 0;
+  bool plan_has_long = false;
   int *h_err = nullptr;
   // streaming-form workspace (allocated on first use)
   unsigned char *d_stream = nullptr;
@@ -82,6 +89,87 @@ int resident_capacity(const top_handle *h, const top_problem *pb) {
     if (L.total <= (size_t)h->smem_optin) return C;
   }
   return 0;
+}
+
+// Best-fit-decreasing packing of the trajectories that fit one resident CTA
+// (N_b <= cap) into packs of at most `cap` segments and `ntp_cap`
+// trajectories.  Trajectories longer than `cap` are left for the streaming
+// form (has_long).  Writes packs[] and the trajectory list grouped by pack.
+void plan_packs(const int32_t *off, int B, int cap, int ntp_cap, Pack *packs, int *tlist, int &npack,
+                int &max_nseg, int &max_ntraj, bool &has_long) {
+  npack = max_nseg = max_ntraj = 0;
+  has_long = false;
+  if (cap <= 0) {
+    for (int b = 0; b < B; ++b)
+      if (off[b + 1] > off[b]) has_long = true;
+    // empty trajectories need no kernel: their outputs are zeroed by the caller
+    return;
+  }
+  // counting sort by length, longest first
+  std::vector<int> cnt(cap + 2, 0), order;
+  order.reserve(B);
+  for (int b = 0; b < B; ++b) {
+    const int nb = off[b + 1] - off[b];
+    if (nb > cap) { has_long = true; continue; }
+    ++cnt[nb];
+  }
+  std::vector<int> start(cap + 2, 0);
+  for (int n = cap; n >= 0; --n) start[n] = (n == cap ? 0 : start[n + 1] + cnt[n + 1]);
+  int packable = 0;
+  for (int n = 0; n <= cap; ++n) packable += cnt[n];
+  order.assign(packable, 0);
+  for (int b = 0; b < B; ++b) {
+    const int nb = off[b + 1] - off[b];
+    if (nb <= cap) order[start[nb]++] = b;
+  }
+  // bins indexed by remaining room; a bitset of non-empty room buckets
+  std::vector<int> room, ntraj, nseg, bin_of(B, -1);
+  std::vector<std::vector<int>> bucket(cap + 1);
+  const int words = cap / 64 + 1;
+  std::vector<uint64_t> live(words, 0);
+  auto push = [&](int r, int bin) {
+    bucket[r].push_back(bin);
+    live[r >> 6] |= (1ull << (r & 63));
+  };
+  auto find_at_least = [&](int n) -> int {
+    for (int w = n >> 6; w < words; ++w) {
+      uint64_t m = live[w];
+      if (w == (n >> 6)) m &= ~0ull << (n & 63);
+      if (m) return (w << 6) + __builtin_ctzll(m);
+    }
+    return -1;
+  };
+  for (int b : order) {
+    const int nb = off[b + 1] - off[b];
+    int r = find_at_least(nb);
+    int bin;
+    if (r >= 0 && r <= cap) {
+      bin = bucket[r].back();
+      bucket[r].pop_back();
+      if (bucket[r].empty()) live[r >> 6] &= ~(1ull << (r & 63));
+    } else {
+      bin = (int)room.size();
+      room.push_back(cap);
+      ntraj.push_back(0);
+      nseg.push_back(0);
+    }
+    room[bin] -= nb;
+    nseg[bin] += nb;
+    ntraj[bin] += 1;
+    bin_of[b] = bin;
+    if (ntraj[bin] < ntp_cap) push(room[bin], bin);
+  }
+  npack = (int)room.size();
+  // trajectory list grouped by pack (ascending trajectory id inside a pack)
+  std::vector<int> pos(npack + 1, 0);
+  for (int q = 0; q < npack; ++q) pos[q + 1] = pos[q] + ntraj[q];
+  for (int q = 0; q < npack; ++q) {
+    packs[q] = Pack{pos[q], nseg[q], ntraj[q], 0};
+    max_nseg = std::max(max_nseg, nseg[q]);
+    max_ntraj = std::max(max_ntraj, ntraj[q]);
+  }
+  for (int b = 0; b < B; ++b)
+    if (bin_of[b] >= 0) tlist[pos[bin_of[b]]++] = b;
 }
 
 struct StagePlan {
@@ -197,6 +285,9 @@ void top_destroy(top_handle *h) {
   cudaFreeHost(h->h_off);
   cudaFreeHost(h->h_packs);
   cudaFreeHost(h->h_lt);
+  cudaFreeHost(h->h_tlist);
+  cudaFree(h->d_tlist);
+  std::free(h->plan_off);
   cudaFreeHost(h->h_err);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
@@ -222,15 +313,21 @@ int top_create(const top_config *cfg, top_handle **out) {
     e = cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   const size_t S = (size_t)cfg->max_segments, B = (size_t)cfg->max_batch;
   if (e == cudaSuccess) e = cudaMalloc(&h->G, (size_t)NG * S * rbytes(h));
-  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_packs, sizeof(Pack) * S);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_packs, sizeof(Pack) * std::max(S, B));
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_err, sizeof(int));
   if (e == cudaSuccess) {
     h->stage_bytes = stage_plan((int)B, (int)S).total;
     e = cudaMalloc((void **)&h->d_stage, h->stage_bytes);
   }
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_off, sizeof(int32_t) * (B + 1));
-  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_packs, sizeof(Pack) * S);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_packs, sizeof(Pack) * std::max(S, B));
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_lt, sizeof(int) * (2 * B + 1));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_tlist, sizeof(int) * B);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_tlist, sizeof(int) * B);
+  if (e == cudaSuccess) {
+    h->plan_off = (int32_t *)std::malloc(sizeof(int32_t) * (B + 1));
+    if (!h->plan_off) e = cudaErrorMemoryAllocation;
+  }
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_err, sizeof(int));
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? TOP_E_NOMEM : TOP_E_CUDA;
@@ -340,40 +437,39 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   // ---- plan: resident packs of whole trajectories ----
   const int fam = families(&pb);
   const int cap = (h->cfg.schedule == TOP_SCHED_STREAM || pb.inner == TOP_NUMERIC) ? 0 : resident_capacity(h, &pb);
-  int npack = 0, max_nseg = 0, max_ntraj = 0;
-  bool has_long = false;
-  {
-    const int ntp_cap = std::max(1, cap / 4);
-    int b = 0;
-    while (b < B) {
-      const int nb = off[b + 1] - off[b];
-      if (cap == 0 || nb > cap) { has_long = true; ++b; continue; }
-      Pack pk{off[b], 0, b, 0};
-      while (b < B) {
-        const int n2 = off[b + 1] - off[b];
-        if (n2 > cap || pk.nseg + n2 > cap || pk.ntraj + 1 > ntp_cap) break;
-        pk.nseg += n2;
-        pk.ntraj += 1;
-        ++b;
-      }
-      h->h_packs[npack++] = pk;
-      max_nseg = std::max(max_nseg, pk.nseg);
-      max_ntraj = std::max(max_ntraj, pk.ntraj);
-    }
+  const int ntp_cap = std::max(1, cap / 4);
+  // the plan is reused while the batch layout and the capacity repeat
+  const bool same_plan = h->plan_valid && h->plan_B == B && h->plan_cap == cap &&
+                         std::memcmp(h->plan_off, off, sizeof(int32_t) * (B + 1)) == 0;
+  if (!same_plan) {
+    plan_packs(off, B, cap, ntp_cap, h->h_packs, h->h_tlist, h->plan_npack, h->plan_max_nseg,
+               h->plan_max_ntraj, h->plan_has_long);
+    std::memcpy(h->plan_off, off, sizeof(int32_t) * (B + 1));
+    h->plan_B = B;
+    h->plan_cap = cap;
+    h->plan_valid = false;  // set once the device copies are enqueued
   }
+  const int npack = h->plan_npack, max_nseg = h->plan_max_nseg, max_ntraj = h->plan_max_ntraj;
+  const bool has_long = h->plan_has_long;
   if (has_long && h->cfg.schedule == TOP_SCHED_RESIDENT) {
     if (d_hist) cudaFree(d_hist);
     return TOP_E_NOTSUP;
   }
   if (npack > 0) {
-    TOP_CUDA(h, cudaMemcpyAsync(h->d_packs, h->h_packs, sizeof(Pack) * npack, cudaMemcpyHostToDevice, st));
+    if (!same_plan) {
+      TOP_CUDA(h, cudaMemcpyAsync(h->d_packs, h->h_packs, sizeof(Pack) * npack, cudaMemcpyHostToDevice, st));
+      int ntl = 0;
+      for (int q = 0; q < npack; ++q) ntl += h->h_packs[q].ntraj;
+      TOP_CUDA(h, cudaMemcpyAsync(h->d_tlist, h->h_tlist, sizeof(int) * ntl, cudaMemcpyHostToDevice, st));
+      h->plan_valid = true;
+    }
     const int C = std::max(32, (max_nseg + 31) / 32 * 32);
     const int ntp = std::max(1, max_ntraj);
     const int Mb = (fam & FAM_BOX) ? pb.M_box : 0, Mq = (fam & FAM_BALL) ? pb.M_ball : 0,
               Mv = (fam & FAM_VN) ? pb.M_vn : 0;
     const ResLayout L = res_layout(C, ntp, Mb, Mq, Mv, (int)rbytes(h));
     ResidentArgs ra{};
-    ra.p = dp; ra.r = dr; ra.G = h->G; ra.packs = h->d_packs; ra.ntp = ntp;
+    ra.p = dp; ra.r = dr; ra.G = h->G; ra.packs = h->d_packs; ra.traj_list = h->d_tlist; ra.ntp = ntp;
     if (h->profiling) cudaEventRecord(h->ev[2], st);
     int e = fp64 ? launch_resident_f64(ra, npack, C, L.total, fam, st)
                  : launch_resident_f32(ra, npack, C, L.total, fam, st);

@@ -8,14 +8,14 @@ namespace top {
 
 enum Family : int { FAM_BOX = 1, FAM_BALL = 2, FAM_VN = 4, FAM_GEN = 8 };
 
-// A pack is a run of consecutive whole trajectories processed by one CTA of
-// the resident kernel (all of its state stays in shared memory for every
-// iteration).
+// A pack is a set of whole trajectories processed by one CTA of the
+// resident kernel (all of its state stays in shared memory for every
+// iteration); its trajectories are traj_list[tlist .. tlist+ntraj-1].
 struct Pack {
-  int seg0;   // first global segment
+  int tlist;  // first entry in the trajectory list
   int nseg;   // segments in the pack (<= CTA capacity)
-  int traj0;  // first global trajectory
   int ntraj;  // trajectories in the pack
+  int pad;
 };
 
 // Problem data, all device pointers (FP64, the ABI layout).
@@ -45,6 +45,7 @@ struct ResidentArgs {
   DevResult r;
   const void *G;        // [36][S] packed (D K D)^{-1}, element type = iteration type
   const Pack *packs;
+  const int *traj_list; // trajectory ids, grouped by pack
   int ntp;              // trajectory slots per pack (shared-memory sizing)
 };
 
@@ -52,8 +53,8 @@ struct ResidentArgs {
 // launch on the host and carves the buffer on the device.
 struct ResLayout {
   size_t red_rp, red_rd, tr_rp, tr_rd;           // double arrays
-  size_t z, uL, uRp, eS, dz, ybox, qball, qvn, uR0, tabB, tabQ, tabV;  // element arrays
-  size_t off, done;                              // int arrays
+  size_t p, m, zP, eS, dz, ybox, qball, qvn, tabB, tabQ, tabV;  // element arrays
+  size_t off, done, tid;                         // int arrays
   size_t total;
 };
 
@@ -68,21 +69,21 @@ __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, 
   L.tr_rp = o;  o += sizeof(double) * ntp;
   L.tr_rd = o;  o += sizeof(double) * ntp;
   o = align_up(o, 16);
-  L.z = o;      o += size_t(rb) * 21 * J;
-  L.uL = o;     o += size_t(rb) * 21 * J;
-  L.uRp = o;    o += size_t(rb) * 3 * J;
-  L.eS = o;     o += size_t(rb) * 21 * C;
-  L.dz = o;     o += size_t(rb) * 21 * J;
+  L.p = o;      o += size_t(rb) * 21 * J;  // [slot][21] start-side targets
+  L.m = o;      o += size_t(rb) * 21 * J;  // [slot][21] end-side targets
+  L.zP = o;     o += size_t(rb) * 3 * J;   // [slot][3] pinned positions
+  L.eS = o;     o += size_t(rb) * 21 * C;  // [segment][21] published start derivatives
+  L.dz = o;     o += size_t(rb) * 21 * J;  // [slot][21] consensus change (check iterations)
   L.ybox = o;   o += size_t(rb) * 6 * Mb * C;
   L.qball = o;  o += size_t(rb) * 3 * Mq * C;
   L.qvn = o;    o += size_t(rb) * 3 * Mv * C;
-  L.uR0 = o;    o += size_t(rb) * 12 * ntp;
   L.tabB = o;   o += size_t(rb) * 8 * Mb;
   L.tabQ = o;   o += size_t(rb) * 8 * Mq;
   L.tabV = o;   o += size_t(rb) * 8 * Mv;
   o = align_up(o, 16);
   L.off = o;    o += sizeof(int) * (ntp + 1);
   L.done = o;   o += sizeof(int) * ntp;
+  L.tid = o;    o += sizeof(int) * ntp;
   L.total = align_up(o, 16);
   return L;
 }

@@ -45,7 +45,9 @@ constexpr size_t kMaxBatch = TOP_NOALLOC_MAX_BATCH;
 constexpr size_t kGBytes = (size_t)NG * kMaxSeg * sizeof(double);      // FP64 worst case
 constexpr size_t kPackOff = round256(kGBytes);
 constexpr size_t kPackBytes = sizeof(Pack) * kMaxBatch;                 // at most one pack per trajectory
-constexpr size_t kErrOff = round256(kPackOff + kPackBytes);
+constexpr size_t kListOff = round256(kPackOff + kPackBytes);
+constexpr size_t kListBytes = sizeof(int) * kMaxBatch;                  // trajectory list of the packs
+constexpr size_t kErrOff = round256(kListOff + kListBytes);
 constexpr size_t kScratchBytes = kErrOff + 256;
 
 constexpr int kMaxDevices = 64;
@@ -133,7 +135,7 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
   const int ntp_cap = std::max(1, cap / 4);
   for (int b = 0; b < B;) {
     if (off[b + 1] - off[b] > cap) return TOP_E_LIMIT;
-    Pack pk{off[b], 0, b, 0};
+    Pack pk{b, 0, 0, 0};  // consecutive trajectories: the list is the identity
     while (b < B) {
       const int n2 = off[b + 1] - off[b];
       if (n2 > cap || pk.nseg + n2 > cap || pk.ntraj + 1 > ntp_cap) break;
@@ -149,6 +151,7 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
   unsigned char *base = slot->ptr;
   void *G = base;
   Pack *d_packs = (Pack *)(base + kPackOff);
+  int *d_list = (int *)(base + kListOff);
   int *d_err = (int *)(base + kErrOff);
   DevProblem dp{};
   dp.B = B; dp.S = S;
@@ -174,12 +177,16 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
   if (launch_kinv(dp, pb->rho, fp64 ? nullptr : G, fp64 ? G : nullptr, d_err, st) != 0) return TOP_E_CUDA;
   if (cudaMemcpyAsync(d_packs, packs, sizeof(Pack) * npack, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return TOP_E_CUDA;
+  int ident[kMaxBatch];
+  for (int b = 0; b < B; ++b) ident[b] = b;
+  if (cudaMemcpyAsync(d_list, ident, sizeof(int) * B, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return TOP_E_CUDA;
   const int C = std::max(32, (max_nseg + 31) / 32 * 32);
   const int ntp = std::max(1, max_ntraj);
   const ResLayout L = res_layout(C, ntp, (fam & FAM_BOX) ? pb->M_box : 0, (fam & FAM_BALL) ? pb->M_ball : 0,
                                  (fam & FAM_VN) ? pb->M_vn : 0, rb);
   ResidentArgs ra{};
-  ra.p = dp; ra.r = dr; ra.G = G; ra.packs = d_packs; ra.ntp = ntp;
+  ra.p = dp; ra.r = dr; ra.G = G; ra.packs = d_packs; ra.traj_list = d_list; ra.ntp = ntp;
   const int e = fp64 ? launch_resident_f64(ra, npack, C, L.total, fam, st)
                      : launch_resident_f32(ra, npack, C, L.total, fam, st);
   if (e != 0) return TOP_E_CUDA;

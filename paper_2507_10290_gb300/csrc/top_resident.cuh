@@ -2,20 +2,33 @@
 // trajectories, one thread per segment, all iteration state in shared memory
 // for the whole run (Algorithm 1 of the paper, Eq. 18a-g, 19-21).
 //
+// Junction state.  For every junction slot and row (axis a, order r) the
+// kernel keeps the two consensus targets the adjacent segments read in the
+// local step of Eq. 18a, instead of z and u themselves:
+//   p = z - u(start side of the right segment),  m = z - u(end side of the left segment).
+// On free interior rows the two scaled duals sum to zero (the average of
+// Eq. 18b makes the increments opposite), so with uL = u(end side):
+//   p = z + uL,  m = z - uL,   z = (p + m)/2,  uL = (p - m)/2,
+// and the updates of Eq. 18b-c become  p' = eE + uL,  m' = eS_next - uL.
+// Rows whose z is fixed keep the fixed value in the slot no neighbour reads:
+//   pinned interior positions (PIN mode): zP[slot][a] = waypoint;
+//     m' = m + P - eE,  p' = p + P - eS_next
+//   trajectory end (orders < p):   p = z_N (fixed),  m' = m + z_N - eE
+//   trajectory start (orders < p): m = z_0 (fixed),  p' = p + z_0 - eS
+//   orders >= p at the two ends: p = m = 0 (dropped rows, reading R2).
+// The local step then reads p at its start slot and m at its end slot,
+// 42 values, with every special case already encoded.
+//
 // Per iteration and segment i (thread i of its pack):
-//   1. local step (Eq. 18a, 18d-g): targets w = E (z - u) at both ends, the
-//      shared local_step() solves with G and advances the constraint state
-//   2. publish the start-end derivatives; barrier
-//   3. junction i+1 (owned by thread i): consensus average (Eq. 18b, pinned
-//      position rows kept at the waypoint), scaled duals (Eq. 18c), primal
-//      residual contribution (Eq. 19); barrier
-//   4. on check iterations: dual residual contribution (Eq. 20), per-
-//      trajectory FP64 reductions in a fixed order, stopping test (Eq. 21)
-// Junction state per slot: z[21], uL[21] (u of the left segment's end side),
-// uRp[3] (u of the right segment's start side on pinned position rows); on
-// free rows the right side's u equals -uL (the averaging keeps the pair
-// summing to zero), and each trajectory's start junction keeps its own
-// start-side u for orders 0..3 (uR0).
+//   1. local step (Eq. 18a, 18d-g) from s_r p[start], s_r m[end]
+//   2. publish the start derivatives; barrier
+//   3. junction i+1 (owned by thread i): consensus update, primal-residual
+//      share (Eq. 19) on check iterations; barrier
+//   4. on check iterations: dual residual (Eq. 20), per-trajectory FP64
+//      reductions in a fixed order, stopping test (Eq. 21)
+// Shared arrays are slot-major (21 values per slot): every access of a
+// thread is a constant offset from one base, and consecutive threads are 21
+// words apart (no bank conflicts).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,31 +58,39 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
   double *red_rd = (double *)(smem + L.red_rd);
   double *tr_rp = (double *)(smem + L.tr_rp);
   double *tr_rd = (double *)(smem + L.tr_rd);
-  R *sz = (R *)(smem + L.z);
-  R *suL = (R *)(smem + L.uL);
-  R *suRp = (R *)(smem + L.uRp);
+  R *sp = (R *)(smem + L.p);
+  R *sm = (R *)(smem + L.m);
+  R *szP = (R *)(smem + L.zP);
   R *seS = (R *)(smem + L.eS);
   R *sdz = (R *)(smem + L.dz);
   R *sybox = (R *)(smem + L.ybox);
   R *sqball = (R *)(smem + L.qball);
   R *sqvn = (R *)(smem + L.qvn);
-  R *suR0 = (R *)(smem + L.uR0);
   R *tabB = (R *)(smem + L.tabB);
   R *tabQ = (R *)(smem + L.tabQ);
   R *tabV = (R *)(smem + L.tabV);
   int *soff = (int *)(smem + L.off);
   int *sdone = (int *)(smem + L.done);
+  int *stid = (int *)(smem + L.tid);
 
   const R rho = R(p.rho);
   const int K = p.max_iters;
   const bool pin = (p.mode == 0);
 
-  // ---- set-up: pack offsets, sample tables, zeroed state ----
-  for (int t = l; t <= pk.ntraj; t += C) soff[t] = p.seg_offset[pk.traj0 + t] - pk.seg0;
+  // ---- set-up: the pack's trajectories, local offsets, tables, zeroed state ----
+  for (int t = l; t < pk.ntraj; t += C) stid[t] = A.traj_list[pk.tlist + t];
+  __syncthreads();
+  if (l == 0) {
+    int acc = 0;
+    for (int t = 0; t < pk.ntraj; ++t) {
+      soff[t] = acc;
+      acc += p.seg_offset[stid[t] + 1] - p.seg_offset[stid[t]];
+    }
+    soff[pk.ntraj] = acc;
+  }
   for (int t = l; t < ntp; t += C) { tr_rp[t] = 0.0; tr_rd[t] = 0.0; }
-  for (int q = l; q < 12 * ntp; q += C) suR0[q] = R(0);
-  for (int q = l; q < 21 * J; q += C) { sdz[q] = R(0); sz[q] = R(0); suL[q] = R(0); }
-  for (int q = l; q < 3 * J; q += C) suRp[q] = R(0);
+  for (int q = l; q < NJ * J; q += C) { sdz[q] = R(0); sp[q] = R(0); sm[q] = R(0); }
+  for (int q = l; q < 3 * J; q += C) szP[q] = R(0);
   if (BOX) for (int q = l; q < 6 * Mb * C; q += C) sybox[q] = R(0);
   if (BALL) for (int q = l; q < 3 * Mq * C; q += C) sqball[q] = R(0);
   if (VN) for (int q = l; q < 3 * Mv * C; q += C) sqvn[q] = R(0);
@@ -93,10 +114,12 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
   const int Nb = soff[tb + 1] - soff[tb];
   const bool first = valid && i == 0;
   const bool last = valid && i == Nb - 1;
-  const int b = pk.traj0 + tb;
-  const int g = pk.seg0 + l;
-  const int jS = l + tb, jE = l + tb + 1;
-  const int wrow0 = pk.seg0 + pk.traj0;
+  const int b = stid[tb];
+  const int g = p.seg_offset[b] + i;        // global segment
+  const int jS = l + tb, jE = l + tb + 1;   // junction slots in shared memory
+  R *pS = sp + jS * NJ, *mS = sm + jS * NJ;  // start slot
+  R *pE = sp + jE * NJ, *mE = sm + jE * NJ;  // end slot (owned by this thread)
+  const R *eSnext = seS + (l + 1) * NJ;
 
   SegConst<R> sc;
   R Tq = R(1);
@@ -114,18 +137,26 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
       sc.brad = R(p.ball_r[g]);
       for (int a = 0; a < 3; ++a) sc.bo[a] = R(p.ball_c[(size_t)g * 3 + a]);
     }
-    // junction state (Init of Algorithm 1): positions from the path, other
-    // orders zero, the trajectory's ends from the boundary states
+    // Init of Algorithm 1: z position rows from the path, other orders zero,
+    // the trajectory's two ends from the boundary states, every u zero
     for (int a = 0; a < AX; ++a)
       for (int r = 0; r < ND; ++r) {
-        R zv = R(0);
+        const int row = a * ND + r;
         if (!last) {
-          if (r == 0) zv = R(p.waypoints[(size_t)(wrow0 + jE) * 3 + a]);
+          const R P = (r == 0) ? R(p.waypoints[(size_t)(g + b + 1) * 3 + a]) : R(0);
+          pE[row] = P;
+          mE[row] = P;
+          if (r == 0) szP[jE * 3 + a] = P;
         } else if (r < PO) {
-          zv = R(p.end_state[((size_t)b * PO + r) * 3 + a]);
+          const R zN = R(p.end_state[((size_t)b * PO + r) * 3 + a]);
+          pE[row] = zN;
+          mE[row] = zN;
         }
-        sz[(a * ND + r) * J + jE] = zv;
-        if (first) sz[(a * ND + r) * J + jS] = r < PO ? R(p.start_state[((size_t)b * PO + r) * 3 + a]) : R(0);
+        if (first && r < PO) {
+          const R z0 = R(p.start_state[((size_t)b * PO + r) * 3 + a]);
+          pS[row] = z0;
+          mS[row] = z0;
+        }
       }
   } else {
 #pragma unroll
@@ -152,18 +183,12 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
       // ---- 1. local step (Eq. 18a, 18d-g) ----
       R wS[AX][ND], wE[AX][ND];
 #pragma unroll
-      for (int a = 0; a < AX; ++a) {
+      for (int a = 0; a < AX; ++a)
 #pragma unroll
         for (int r = 0; r < ND; ++r) {
-          const int row = (a * ND + r) * J;
-          R us;
-          if (first) us = (r < PO) ? suR0[(a * PO + r) * ntp + tb] : R(0);
-          else if (pin && r == 0) us = suRp[a * J + jS];
-          else us = -suL[row + jS];
-          wS[a][r] = (first && r >= PO) ? R(0) : sc.s[r] * (sz[row + jS] - us);
-          wE[a][r] = (last && r >= PO) ? R(0) : sc.s[r] * (sz[row + jE] - suL[row + jE]);
+          wS[a][r] = sc.s[r] * pS[a * ND + r];
+          wE[a][r] = sc.s[r] * mE[a * ND + r];
         }
-      }
       local_step<R, F>(sc, wS, wE, rho, k == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq,
                        Mv, ch);
       // ---- 2. publish start derivatives ----
@@ -171,41 +196,55 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
       for (int a = 0; a < AX; ++a) {
         end_derivs(ch[a], sc.s, eSv[a], eE[a]);
 #pragma unroll
-        for (int r = 0; r < ND; ++r) seS[(a * ND + r) * C + l] = eSv[a][r];
+        for (int r = 0; r < ND; ++r) seS[l * NJ + a * ND + r] = eSv[a][r];
       }
     }
     __syncthreads();
     // ---- 3. junction update (Eq. 18b, 18c) and primal residual (Eq. 19) ----
-    R rp2 = R(0);  // this segment's share of ||r_p||^2, only formed on check iterations
+    R rp2 = R(0);  // this segment's share of ||r_p||^2, formed on check iterations only
     if (act) {
+      if (!last) {
 #pragma unroll
-      for (int a = 0; a < AX; ++a) {
+        for (int a = 0; a < AX; ++a) {
 #pragma unroll
-        for (int r = 0; r < ND; ++r) {
-          const int idx = (a * ND + r) * J + jE;
-          if (!last) {
-            const R en = seS[(a * ND + r) * C + l + 1];
+          for (int r = 0; r < ND; ++r) {
+            const int row = a * ND + r;
+            const R ee = eE[a][r], en = eSnext[row];
+            const R pv = pE[row], mv = mE[row];
             if (check) {
-              const R gap = eE[a][r] - en;
+              const R gap = ee - en;
               rp2 += gap * gap;
             }
             if (pin && r == 0) {
-              const R P = sz[idx];
-              suL[idx] += eE[a][r] - P;
-              suRp[a * J + jE] += en - P;
-              if (check) sdz[idx] = R(0);
+              const R P = szP[jE * 3 + a];
+              mE[row] = mv + (P - ee);
+              pE[row] = pv + (P - en);
+              if (check) sdz[jE * NJ + row] = R(0);
             } else {
-              const R zo = sz[idx];
-              const R zn = R(0.5) * (eE[a][r] + en);
-              suL[idx] += eE[a][r] - zn;
-              sz[idx] = zn;
-              if (check) sdz[idx] = zn - zo;
+              const R uL = R(0.5) * (pv - mv);
+              pE[row] = ee + uL;
+              mE[row] = en - uL;
+              if (check) sdz[jE * NJ + row] = R(0.5) * ((ee + en) - (pv + mv));
             }
-          } else if (r < PO) {
-            suL[idx] += eE[a][r] - sz[idx];
           }
-          if (first && r < PO) suR0[(a * PO + r) * ntp + tb] += eSv[a][r] - sz[(a * ND + r) * J + jS];
         }
+      } else {
+#pragma unroll
+        for (int a = 0; a < AX; ++a)
+#pragma unroll
+          for (int r = 0; r < PO; ++r) {
+            const int row = a * ND + r;
+            mE[row] += pE[row] - eE[a][r];
+          }
+      }
+      if (first) {
+#pragma unroll
+        for (int a = 0; a < AX; ++a)
+#pragma unroll
+          for (int r = 0; r < PO; ++r) {
+            const int row = a * ND + r;
+            pS[row] += mS[row] - eSv[a][r];
+          }
       }
     }
     __syncthreads();
@@ -222,8 +261,8 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
           R dS[ND], dE[ND];
 #pragma unroll
           for (int r = 0; r < ND; ++r) {
-            dS[r] = first ? R(0) : sc.s[r] * sdz[(a * ND + r) * J + jS];
-            dE[r] = last ? R(0) : sc.s[r] * sdz[(a * ND + r) * J + jE];
+            dS[r] = first ? R(0) : sc.s[r] * sdz[jS * NJ + a * ND + r];
+            dE[r] = last ? R(0) : sc.s[r] * sdz[jE * NJ + a * ND + r];
           }
           rd2 += dual_residual_sq(dS, dE, rho, Tk);
         }
@@ -245,7 +284,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
           const double rp = sqrt(a1), rd = sqrt(a2);
           tr_rp[t] = rp;
           tr_rd[t] = rd;
-          const int bb = pk.traj0 + t;
+          const int bb = stid[t];
           if (res.history) {
             res.history[((size_t)k * p.B + bb) * 2 + 0] = rp;
             res.history[((size_t)k * p.B + bb) * 2 + 1] = rd;
@@ -288,7 +327,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) a1 += __shfl_xor_sync(0xffffffffu, a1, o);
       if (lane == 0) {
-        const int bb = pk.traj0 + t;
+        const int bb = stid[t];
         res.cost[bb] = a1;
         res.r_primal[bb] = tr_rp[t];
         res.r_dual[bb] = tr_rd[t];
