@@ -292,7 +292,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "trajectories_per_s": world * B / (ms_step / 1000.0),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+                     "frac": achieved / fp32_peak, "traffic": resident_traffic(S),
                      "kernel": "resident_kernel<float,0>", "kernel_ms": res_ms,
                      "peak_source": f"FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x {sm_max:.0f} MHz (max SM clock)",
                      "flop_per_segment_iteration": FLOP_PER_SEG_IT},
@@ -306,6 +306,33 @@ def run_ours(args):
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
+
+
+KERNEL_SOURCES = ["top_resident.cuh", "top_step.cuh", "top_math.cuh", "top_internal.h"]
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "resident_kernel_batch512_fp32.md")
+
+
+def resident_traffic(S: int):
+    """DRAM bytes of one resident-kernel launch at S segments, scaled from the
+    committed ncu capture of a smaller batch (traffic is per segment: inputs,
+    G and outputs; the iteration loop reads none).  None when the kernel
+    sources differ from the profiled ones."""
+    import hashlib
+    try:
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            with open(os.path.join(ROOT, "paper_2507_10290_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        vals = {}
+        for line in open(TRAFFIC_PROFILE):
+            if ":" in line and line.split(":")[0].strip() in ("traffic_bytes_per_segment", "kernel_source_sha256_16"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_sha256_16") != h.hexdigest()[:16]:
+            return None
+        return float(vals["traffic_bytes_per_segment"]) * S
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def main():

@@ -63,6 +63,19 @@ __device__ __forceinline__ void consensus_rhs(const R (&wS)[ND], const R (&wE)[N
   }
 }
 
+// as consensus_rhs, with the start-side targets already multiplied by k!
+template <class R>
+__device__ __forceinline__ void consensus_rhs_f(const R (&wSf)[ND], const R (&wE)[ND], R rho, R (&rhs)[NC]) {
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    R acc = (k < ND) ? wSf[k] : R(0);
+#pragma unroll
+    for (int r = 0; r < ND; ++r)
+      if (r <= k) acc += R(falling(k, r)) * wE[r];
+    rhs[k] += rho * acc;
+  }
+}
+
 // derivatives 0..6 at both ends of one axis: eS_r = r! s_r ch_r,
 // eE_r = s_r sum_{k>=r} F(k,r) ch_k  (the rows of M(T) c, Sec. III-D.1)
 template <class R>
@@ -71,6 +84,20 @@ __device__ __forceinline__ void end_derivs(const R (&ch)[NC], const R (&s)[NC], 
 #pragma unroll
   for (int r = 0; r < ND; ++r) {
     eS[r] = R(fact(r)) * s[r] * ch[r];
+    R acc = R(0);
+#pragma unroll
+    for (int k = r; k < NC; ++k) acc += R(falling(k, r)) * ch[k];
+    eE[r] = s[r] * acc;
+  }
+}
+
+// as end_derivs, with fs_r = r! s_r precomputed
+template <class R>
+__device__ __forceinline__ void end_derivs_f(const R (&ch)[NC], const R (&s)[NC], const R (&fs)[ND], R (&eS)[ND],
+                                             R (&eE)[ND]) {
+#pragma unroll
+  for (int r = 0; r < ND; ++r) {
+    eS[r] = fs[r] * ch[r];
     R acc = R(0);
 #pragma unroll
     for (int k = r; k < NC; ++k) acc += R(falling(k, r)) * ch[k];

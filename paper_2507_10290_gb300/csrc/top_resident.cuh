@@ -165,6 +165,9 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
     for (int r = 0; r < NC; ++r) sc.s[r] = R(0);
   }
   __syncthreads();
+  R fs[ND];  // r! T^-r
+#pragma unroll
+  for (int r = 0; r < ND; ++r) fs[r] = R(fact(r)) * sc.s[r];
 
   R ch[AX][NC];
 #pragma unroll
@@ -186,15 +189,15 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
       for (int a = 0; a < AX; ++a)
 #pragma unroll
         for (int r = 0; r < ND; ++r) {
-          wS[a][r] = sc.s[r] * pS[a * ND + r];
+          wS[a][r] = fs[r] * pS[a * ND + r];
           wE[a][r] = sc.s[r] * mE[a * ND + r];
         }
-      local_step<R, F>(sc, wS, wE, rho, k == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq,
+      local_step<R, F, true>(sc, wS, wE, rho, k == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq,
                        Mv, ch);
       // ---- 2. publish start derivatives ----
 #pragma unroll
       for (int a = 0; a < AX; ++a) {
-        end_derivs(ch[a], sc.s, eSv[a], eE[a]);
+        end_derivs_f(ch[a], sc.s, fs, eSv[a], eE[a]);
 #pragma unroll
         for (int r = 0; r < ND; ++r) seS[l * NJ + a * ND + r] = eSv[a][r];
       }

@@ -43,7 +43,8 @@ __device__ __forceinline__ void fill_sample_table(R *tab, int M, int order, int 
   }
 }
 
-template <class R, int F>
+// FS: the start-side targets wS already carry the factor k! (see consensus_rhs_f)
+template <class R, int F, bool FS = false>
 __device__ __forceinline__ void local_step(const SegConst<R> &sc, const R (&wS)[AX][ND], const R (&wE)[AX][ND],
                                            R rho, bool first_iter, R *ybox, R *qball, R *qvn, int stride,
                                            const R *tabB, const R *tabQ, const R *tabV, int Mb, int Mq, int Mv,
@@ -56,7 +57,8 @@ __device__ __forceinline__ void local_step(const SegConst<R> &sc, const R (&wS)[
   for (int a = 0; a < AX; ++a) {
 #pragma unroll
     for (int q = 0; q < NC; ++q) rhs[a][q] = R(0);
-    consensus_rhs(wS[a], wE[a], rho, rhs[a]);
+    if (FS) consensus_rhs_f(wS[a], wE[a], rho, rhs[a]);
+    else consensus_rhs(wS[a], wE[a], rho, rhs[a]);
   }
   if (BOX) {
     for (int j = 0; j < Mb; ++j) {
