@@ -303,9 +303,156 @@ def run_ours(args):
         "e2e": {"value": world * S * iters / e2e_step, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": 1000 * e2e_step},
     }
+    if not args.no_tolerance:
+        line["to_tolerance"] = time_to_tolerance(top, B, rank, world)
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
+
+
+def _timed_solve(solver, w, tensors, out, **kw):
+    """One solve timed with CUDA events on the current stream; returns ms."""
+    import torch
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    solver.solve(w, tensors=tensors, out=out, stream=st.cuda_stream, **kw)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def time_to_tolerance(top, B, rank, world, eps=1e-4, cap=30000, fp64_B=256):
+    """Trajectories per second that meet the stopping rule of Eq. 21 at eps.
+
+    PIN waypoints with the fixed rho = 1 do not reach even the paper's loose
+    eps = 0.05 in 2e5 iterations (oracle), so the batch is solved with FREE
+    waypoints (otherwise the same recipe), which converges.  FP32 on the
+    whole batch; FP32 and FP64 side by side on its first `fp64_B` trajectories.
+    """
+    res = {"workload": f"batch recipe with FREE waypoints, eps={eps} (E = N_b eps), cap {cap} iterations, "
+                       "residuals every iteration", "eps": eps, "cap": cap}
+    for tag, BB, precs in (("full", B, ("fp32",)), ("subset", min(fp64_B, B), ("fp32", "fp64"))):
+        w = W.batch(seed=rank, B=BB).with_(mode="free", eps=eps, max_iters=cap)
+        Nb = np.diff(w.seg_offset)
+        for prec in precs:
+            s = top.Solver(max_batch=BB, max_segments=w.S, precision=prec, max_samples=0)
+            tensors = s.device_inputs(w)
+            out = s.alloc_result(BB, w.S, cap)
+            s.solve(w, tensors=tensors, out=out, max_iters=5, eps=eps)  # warm-up
+            ms = _timed_solve(s, w, tensors, out)
+            it = out["iters"].cpu().numpy()
+            st = out["status"].cpu().numpy()
+            conv = int((st == 0).sum())
+            res[f"{tag}_{prec}"] = {
+                "trajectories": BB, "segments": int(w.S), "ms": ms, "converged": conv,
+                "trajectories_per_s": world * conv / (ms / 1000.0),
+                "mean_iterations": float(it.mean()), "max_iterations": int(it.max()),
+                "segment_iterations_per_s": world * float(np.sum(Nb * it)) / (ms / 1000.0),
+            }
+            s.close()
+    return res
+
+
+def run_suite(args):
+    """One JSON line per benchmark workload: GPU time per iteration (FP32 and
+    FP64), parity against the oracle, the oracle's own time beside it."""
+    import torch
+    torch.cuda.set_device(0)
+    import oracle
+    from paper_2507_10290_gb300 import top
+
+    def scaled_err(g, o, T):
+        sc = np.asarray(T)[:, None, None] ** np.arange(8)[None, None, :]
+        return float(np.linalg.norm((g - o) * sc) / np.linalg.norm(o * sc))
+
+    def oracle_rate(w, max_iters=None):
+        t0 = time.perf_counter()
+        r = oracle.solve(w, max_iters=max_iters)
+        dt = time.perf_counter() - t0
+        return r, dt
+
+    def gpu_case(name, w, precs=("fp32", "fp64"), extra=None, tol_eps=None, tol_cap=20000):
+        line = {"suite": name, "workload": w.name, "segments": int(w.S), "trajectories": int(w.B),
+                "iterations": int(w.max_iters)}
+        o, odt = oracle_rate(w)
+        line["oracle"] = {"seconds": odt, "cores": 1, "segment_iterations_per_s": w.S * w.max_iters / odt}
+        for prec in precs:
+            s = top.Solver(max_batch=w.B, max_segments=w.S, precision=prec, max_samples=16)
+            tensors = s.device_inputs(w)
+            out = s.alloc_result(w.B, w.S, w.max_iters)
+            s.solve(w, tensors=tensors, out=out)
+            top.top_set_profiling(s.handle, True)
+            ms = [_timed_solve(s, w, tensors, out) for _ in range(3)]
+            kt = top.top_kernel_times(s.handle)[1]
+            top.top_set_profiling(s.handle, False)
+            g = {k: v.cpu().numpy() for k, v in out.items()}
+            entry = {"ms": float(np.median(ms)), "us_per_iteration": 1000 * float(np.median(ms)) / w.max_iters,
+                     "kernel_ms": {"precompute": kt[0], "resident": kt[1], "streaming": kt[2]},
+                     "segment_iterations_per_s": w.S * w.max_iters / (float(np.median(ms)) / 1000),
+                     "coeff_rel_err_vs_oracle": scaled_err(g["coeffs"], o["coeffs"], w.durations),
+                     "cost_rel_err_vs_oracle": float(np.max(np.abs(g["cost"] - o["cost"]) / np.abs(o["cost"])))}
+            if tol_eps:
+                wt = w.with_(eps=tol_eps, max_iters=tol_cap)
+                out2 = s.alloc_result(w.B, w.S, tol_cap)
+                mt = _timed_solve(s, wt, tensors, out2)
+                entry["to_tolerance"] = {"eps": tol_eps, "cap": tol_cap, "ms": mt,
+                                         "iterations": out2["iters"].cpu().numpy().tolist(),
+                                         "status": out2["status"].cpu().numpy().tolist()}
+            line[prec] = entry
+            s.close()
+        if extra:
+            line.update(extra(o))
+        print(json.dumps(line), flush=True)
+
+    gpu_case("single_box", W.single_box(), tol_eps=1e-4)
+    gpu_case("corridor", W.corridor(), tol_eps=1e-4)
+    sub = W.batch().subset(list(range(64)))
+    gpu_case("batch (64-trajectory subset for the oracle)", sub, precs=("fp32", "fp64"))
+    gpu_case("general (N=1000, numerical step)", W.general(N=1000), tol_eps=1e-4)
+
+    # adjoint through 100 iterations on the 256 x 256 batch
+    w = W.grad_batch()
+    s = top.Solver(max_batch=w.B, max_segments=w.S, precision="fp32")
+    tensors = s.device_inputs(w)
+    s.grad(w, tensors=tensors)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        s.grad(w, tensors=tensors)
+    torch.cuda.synchronize()
+    gms = (time.perf_counter() - t0) / 3 * 1000
+    s.close()
+    one = w.subset([0])
+    h = 1e-3
+    t0 = time.perf_counter()
+    oracle.solve(one.with_(durations=one.durations + h))
+    oracle.solve(one.with_(durations=one.durations - h))
+    fd_s = time.perf_counter() - t0
+    print(json.dumps({"suite": "grad_batch", "workload": w.name, "segments": int(w.S), "iterations": 100,
+                      "fp32": {"ms": gms, "segment_iterations_per_s_forward_and_reverse": w.S * 100 / (gms / 1000)},
+                      "oracle_one_directional_fd_seconds_per_trajectory": fd_s}), flush=True)
+
+    # the full 1e5-segment general-bounds trajectory on the GPU only (oracle: the N=1000 line above)
+    w = W.general()
+    for prec in ("fp32",):
+        s = top.Solver(max_batch=1, max_segments=w.S, precision=prec, max_samples=16)
+        tensors = s.device_inputs(w)
+        out = s.alloc_result(1, w.S, w.max_iters)
+        s.solve(w, tensors=tensors, out=out, max_iters=5)
+        ms = _timed_solve(s, w, tensors, out)
+        wt = w.with_(eps=1e-4, max_iters=20000)
+        out2 = s.alloc_result(1, w.S, 20000)
+        mt = _timed_solve(s, wt, tensors, out2)
+        print(json.dumps({"suite": "general (N=100000, numerical step)", "segments": int(w.S),
+                          prec: {"ms_200_iterations": ms, "us_per_iteration": 1000 * ms / 200,
+                                 "to_tolerance": {"eps": 1e-4, "cap": 20000, "ms": mt,
+                                                  "iterations": int(out2["iters"][0]),
+                                                  "status": int(out2["status"][0]),
+                                                  "r_primal": float(out2["r_primal"][0]),
+                                                  "r_dual": float(out2["r_dual"][0])}}}), flush=True)
+        s.close()
 
 
 KERNEL_SOURCES = ["top_resident.cuh", "top_step.cuh", "top_math.cuh", "top_internal.h"]
@@ -344,11 +491,16 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tolerance", action="store_true", help="skip the time-to-tolerance measurement")
+    ap.add_argument("--suite", action="store_true",
+                    help="one JSON line per benchmark workload (single_box, corridor, batch, grad_batch, general)")
     ap.add_argument("--trajectories", type=int, default=4096,
                     help="batch size (4096 = the benchmark workload; smaller only for profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.suite:
+        run_suite(args)
     else:
         run_ours(args)
 

@@ -300,6 +300,30 @@ __device__ int numeric_step(const SegConst<R> &sc, const R (&w)[AX][2][ND], R rh
     consensus_rhs(oS, oE, rho, rhs[a]);
     apply_g(sc.G, rhs[a], ch[a]);
   }
+  // If no bound is violated at the minimiser of the quadratic part, every
+  // penalty term and its gradient vanish there and F >= quadratic part >=
+  // its minimum = F(start): the start is the exact minimiser (and y stays).
+  {
+    bool violated = false;
+    for (int j = 0; j < Mg && !violated; ++j) {
+#pragma unroll
+      for (int kind = 0; kind < 2; ++kind) {
+        const R *tab = kind ? tabA + j * 8 : tabV + j * 8;
+        const R sc_t = kind ? sc.s[2] : sc.s[1];
+        const R gmax = kind ? amax : vmax;
+        R n2 = R(0);
+#pragma unroll
+        for (int a = 0; a < AX; ++a) {
+          R acc = R(0);
+#pragma unroll
+          for (int k = 0; k < NC; ++k) acc += tab[k] * ch[a][k];
+          n2 += (sc_t * acc) * (sc_t * acc);
+        }
+        if (n2 > gmax * gmax) violated = true;
+      }
+    }
+    if (!violated) return 0;
+  }
   R scale = dot24(rhs, ch);  // rhs^T G rhs: size of the linear term in the G metric
   if (!(scale > R(0))) scale = R(1);
   R g[AX][NC], gn[AX][NC], d[AX][NC], xn[AX][NC];
@@ -355,7 +379,7 @@ __device__ int numeric_step(const SegConst<R> &sc, const R (&w)[AX][2][ND], R rh
     // Armijo backtracking (c1 = 1e-4, halving)
     R step = R(1), Fn = Fv;
     bool ok = false;
-    for (int bt = 0; bt < 40; ++bt) {
+    for (int bt = 0; bt < 30; ++bt) {
 #pragma unroll
       for (int a = 0; a < AX; ++a)
 #pragma unroll

