@@ -43,6 +43,19 @@ FLOP_PER_SEG_IT = 1190        # algorithmic FP32 FLOPs of one segment-iteration 
 L2_BYTES = 129 * 1024 * 1024
 
 
+def aggregate_ranks(ms_step: float, units_per_rank: float, world: int, device: str = "cuda"):
+    """Step time = maximum over ranks (every rank solves its own batch, no
+    data-path collective); value = units of all ranks / that time.  Uses the
+    process group already initialised (NCCL on GPUs, gloo in the CPU tests)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    return ms_step, world * units_per_rank / (ms_step / 1000.0)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -232,12 +245,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms_step = float(np.mean(ms))
-    if world > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * S * iters / (ms_step / 1000.0)
+    ms_step, value = aggregate_ranks(float(np.mean(ms)), S * iters, world, device="cuda")
     kern = {"kinv_ms": float(np.mean(kinv_ms)), "resident_ms": float(np.mean(res_ms))}
 
     # e2e through the C ABI with host buffers (H2D + D2H inside the timed region)

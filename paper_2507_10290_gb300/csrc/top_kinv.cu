@@ -14,8 +14,10 @@
 //      +   rho s_1^2 sum_j a_j a_j^T          (velocity-norm samples)
 // with a_j[k] = k tau_j^{k-1}, b_j[k] = tau_j^k, tau_j = j / M, and the
 // consensus rows of order >= p dropped at the trajectory's two ends.  Kh is
-// Jacobi-equilibrated, factorised by Cholesky and inverted in FP64; the
-// packed inverse is written in FP64 and rounded to FP32 for the FP32 path.
+// Jacobi-equilibrated, factorised by Cholesky and inverted in FP64, all in
+// one packed lower triangle held in registers (the factor and its inverse
+// overwrite the matrix); the packed inverse is written in FP64 or rounded to
+// FP32 for the FP32 path.
 #include <cuda_runtime.h>
 
 #include "top_internal.h"
@@ -32,8 +34,55 @@ __device__ __forceinline__ int find_traj(const int32_t *off, int B, int g) {
   return lo;
 }
 
-__global__ void kinv_kernel(const DevProblem p, double rho, float *__restrict__ G32,
-                            double *__restrict__ G64, int *__restrict__ err) {
+// packed lower triangle, i >= j
+__host__ __device__ constexpr int lidx(int i, int j) { return i * (i + 1) / 2 + j; }
+
+__device__ __forceinline__ void add_sample_rows(double (&A)[NG], int M, int order, double weight) {
+  for (int j = 1; j <= M; ++j) {
+    const double tau = double(j) / double(M);
+    double a[NC];
+    double t = 1.0;  // tau^(k - order) built incrementally
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      if (order == 0) {
+        a[k] = t;
+        t *= tau;
+      } else {
+        a[k] = (k == 0) ? 0.0 : double(k) * t;
+        if (k >= 1) t *= tau;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NC; ++r)
+#pragma unroll
+      for (int c = 0; c <= r; ++c) A[lidx(r, c)] += weight * a[r] * a[c];
+  }
+}
+
+// column J of the in-place Cholesky factorisation (recursion keeps every
+// index a compile-time constant, so the packed matrix stays in registers)
+template <int J>
+__device__ __forceinline__ void chol_col(double (&A)[NG], double (&inv)[NC], bool &ok) {
+  double dd = A[lidx(J, J)];
+#pragma unroll
+  for (int k = 0; k < J; ++k) dd -= A[lidx(J, k)] * A[lidx(J, k)];
+  ok = ok && (dd > 0.0);
+  const double ddp = dd > 0.0 ? dd : 1.0;
+  inv[J] = rsqrt(ddp);          // 1 / L_JJ
+  A[lidx(J, J)] = ddp * inv[J];  // L_JJ = sqrt(dd)
+#pragma unroll
+  for (int r = J + 1; r < NC; ++r) {
+    double a = A[lidx(r, J)];
+#pragma unroll
+    for (int k = 0; k < J; ++k) a -= A[lidx(r, k)] * A[lidx(J, k)];
+    A[lidx(r, J)] = a * inv[J];
+  }
+  if constexpr (J + 1 < NC) chol_col<J + 1>(A, inv, ok);
+}
+
+template <bool SAMPLES>
+__global__ void __launch_bounds__(128) kinv_kernel(const DevProblem p, double rho, float *__restrict__ G32,
+                                                   double *__restrict__ G64, int *__restrict__ err) {
   const int S = p.S;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < S; g += gridDim.x * blockDim.x) {
     const int b = find_traj(p.seg_offset, p.B, g);
@@ -46,94 +95,80 @@ __global__ void kinv_kernel(const DevProblem p, double rho, float *__restrict__ 
       continue;
     }
     double s[NC];
+    const double it = 1.0 / T;
     s[0] = 1.0;
-    for (int r = 1; r < NC; ++r) s[r] = s[r - 1] / T;
-    double K[NC][NC];
-    const double t7 = s[7];
 #pragma unroll
-    for (int k = 0; k < NC; ++k)
+    for (int r = 1; r < NC; ++r) s[r] = s[r - 1] * it;
+    double A[NG];
 #pragma unroll
-      for (int l = 0; l < NC; ++l) K[k][l] = 2.0 * t7 * qhat(k, l);
+    for (int r = 0; r < NC; ++r)
+#pragma unroll
+      for (int c = 0; c <= r; ++c) A[lidx(r, c)] = 2.0 * s[7] * qhat(r, c);
     // consensus rows (Mt^T E Mt)
 #pragma unroll
-    for (int r = 0; r < ND; ++r) {
-      if (!(first && r >= PO)) {
-        const double v = double(fact(r)) * s[r];
-        K[r][r] += rho * v * v;
+    for (int q = 0; q < ND; ++q) {
+      if (!(first && q >= PO)) {
+        const double v = double(fact(q)) * s[q];
+        A[lidx(q, q)] += rho * v * v;
       }
-      if (!(last && r >= PO)) {
-        const double w = rho * s[r] * s[r];
+      if (!(last && q >= PO)) {
+        const double w = rho * s[q] * s[q];
 #pragma unroll
-        for (int k = r; k < NC; ++k)
+        for (int r = q; r < NC; ++r)
 #pragma unroll
-          for (int l = r; l < NC; ++l) K[k][l] += w * double(falling(k, r)) * double(falling(l, r));
+          for (int c = q; c <= r; ++c) A[lidx(r, c)] += w * double(falling(r, q)) * double(falling(c, q));
       }
     }
-    auto add_samples = [&](int M, int order, double weight) {
-      for (int j = 1; j <= M; ++j) {
-        const double tau = double(j) / double(M);
-        double a[NC];
-        for (int k = 0; k < NC; ++k) {
-          if (order == 0) {
-            double t = 1.0;
-            for (int q = 0; q < k; ++q) t *= tau;
-            a[k] = t;
-          } else {
-            double t = 1.0;
-            for (int q = 0; q < k - 1; ++q) t *= tau;
-            a[k] = (k == 0) ? 0.0 : double(k) * t;
-          }
-        }
-        for (int k = 0; k < NC; ++k)
-          for (int l = 0; l < NC; ++l) K[k][l] += weight * a[k] * a[l];
-      }
-    };
-    if (p.inner == 0) {
-      if (p.M_box > 0) add_samples(p.M_box, 1, 2.0 * rho * s[1] * s[1]);
-      if (p.M_ball > 0) add_samples(p.M_ball, 0, rho);
-      if (p.M_vn > 0) add_samples(p.M_vn, 1, rho * s[1] * s[1]);
+    if (SAMPLES && p.inner == 0) {
+      if (p.M_box > 0) add_sample_rows(A, p.M_box, 1, 2.0 * rho * s[1] * s[1]);
+      if (p.M_ball > 0) add_sample_rows(A, p.M_ball, 0, rho);
+      if (p.M_vn > 0) add_sample_rows(A, p.M_vn, 1, rho * s[1] * s[1]);
     }
-    // Jacobi equilibration + Cholesky + inverse, all FP64
+    // Jacobi equilibration: A <- D A D, D = diag(A)^-1/2
     double d[NC];
     bool ok = true;
+#pragma unroll
     for (int k = 0; k < NC; ++k) {
-      ok = ok && (K[k][k] > 0.0);
-      d[k] = ok ? 1.0 / sqrt(K[k][k]) : 0.0;
-    }
-    double L[NC][NC];
-    for (int k = 0; k < NC; ++k)
-      for (int l = 0; l < NC; ++l) L[k][l] = 0.0;
-    for (int j = 0; j < NC && ok; ++j) {
-      double dd = d[j] * K[j][j] * d[j];
-      for (int q = 0; q < j; ++q) dd -= L[j][q] * L[j][q];
-      if (!(dd > 0.0)) { ok = false; break; }
-      const double ljj = sqrt(dd);
-      L[j][j] = ljj;
-      for (int r = j + 1; r < NC; ++r) {
-        const double kk = (r > j) ? K[j][r] : K[r][j];  // K upper part is complete (symmetric fill)
-        double a = d[r] * kk * d[j];
-        for (int q = 0; q < j; ++q) a -= L[r][q] * L[j][q];
-        L[r][j] = a / ljj;
-      }
+      const double akk = A[lidx(k, k)];
+      ok = ok && (akk > 0.0);
+      d[k] = ok ? rsqrt(akk) : 0.0;
     }
     if (!ok) {
       atomicOr(err, 2);
       continue;
     }
-    // inverse of L (lower), then (L L^T)^-1 = L^-T L^-1
-    double Li[NC][NC];
-    for (int c = 0; c < NC; ++c) {
-      for (int r = 0; r < NC; ++r) {
-        if (r < c) { Li[r][c] = 0.0; continue; }
-        double a = (r == c) ? 1.0 : 0.0;
-        for (int q = c; q < r; ++q) a -= L[r][q] * Li[q][c];
-        Li[r][c] = a / L[r][r];
+#pragma unroll
+    for (int r = 0; r < NC; ++r)
+#pragma unroll
+      for (int c = 0; c <= r; ++c) A[lidx(r, c)] *= d[r] * d[c];
+    // Cholesky in place: A <- L (lower), inv[j] = 1 / L_jj
+    double inv[NC];
+    chol_col<0>(A, inv, ok);
+    if (!ok) {
+      atomicOr(err, 2);
+      continue;
+    }
+    // invert L in place, column by column: X_jj = 1/L_jj,
+    // X_rj = -(1/L_rr) (L_rj X_jj + sum_{j<k<r} L_rk X_kj)
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      A[lidx(j, j)] = inv[j];
+#pragma unroll
+      for (int r = j + 1; r < NC; ++r) {
+        double a = A[lidx(r, j)] * A[lidx(j, j)];
+#pragma unroll
+        for (int k = j + 1; k < r; ++k) a += A[lidx(r, k)] * A[lidx(k, j)];
+        A[lidx(r, j)] = -inv[r] * a;
       }
     }
+    // (D K D)^-1 = L^-T L^-1, so K^-1 = D L^-T L^-1 D
+#pragma unroll
     for (int k = 0; k < NC; ++k)
+#pragma unroll
       for (int l = k; l < NC; ++l) {
         double a = 0.0;
-        for (int q = l; q < NC; ++q) a += Li[q][k] * Li[q][l];
+#pragma unroll
+        for (int q = l; q < NC; ++q) a += A[lidx(q, k)] * A[lidx(q, l)];
         const double v = d[k] * a * d[l];
         const int idx = gidx(k, l);
         if (G64) G64[size_t(idx) * S + g] = v;
@@ -146,8 +181,12 @@ int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_
   if (p.S == 0) return 0;
   const int threads = 128;
   int blocks = (p.S + threads - 1) / threads;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  kinv_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(p, rho, (float *)G32, (double *)G64, err_flag);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  const bool samples = p.inner == 0 && (p.M_box > 0 || p.M_ball > 0 || p.M_vn > 0);
+  if (samples)
+    kinv_kernel<true><<<blocks, threads, 0, (cudaStream_t)stream>>>(p, rho, (float *)G32, (double *)G64, err_flag);
+  else
+    kinv_kernel<false><<<blocks, threads, 0, (cudaStream_t)stream>>>(p, rho, (float *)G32, (double *)G64, err_flag);
   return (int)cudaGetLastError();
 }
 
