@@ -51,6 +51,8 @@ class _Problem(C.Structure):
         ("M_vn", C.c_int32), ("vnorm", C.c_void_p),
         ("M_gen", C.c_int32), ("gen_vmax", C.c_void_p), ("gen_amax", C.c_void_p),
         ("lbfgs_tol", C.c_double), ("lbfgs_max_iters", C.c_int32), ("lbfgs_mem", C.c_int32),
+        ("adaptive_rho", C.c_int32), ("rho_mu", C.c_double), ("rho_tau_incr", C.c_double),
+        ("rho_tau_decr", C.c_double),
     ]
 
 
@@ -61,7 +63,7 @@ class _Result(C.Structure):
         ("history", C.c_void_p), ("z", C.c_void_p), ("u", C.c_void_p),
         ("s", C.c_void_p), ("v", C.c_void_p), ("phi_b", C.c_void_p), ("w_b", C.c_void_p),
         ("phi_v", C.c_void_p), ("w_v", C.c_void_p), ("y_gen", C.c_void_p),
-        ("inner_iters", C.c_void_p),
+        ("inner_iters", C.c_void_p), ("rho_hist", C.c_void_p), ("rho_final", C.c_void_p),
     ]
 
 
@@ -157,6 +159,10 @@ def _make_problem(w, keep, lbfgs_tol, lbfgs_max_iters, lbfgs_mem, max_iters=None
     pb.lbfgs_tol = float(lbfgs_tol)
     pb.lbfgs_max_iters = int(lbfgs_max_iters)
     pb.lbfgs_mem = int(lbfgs_mem)
+    pb.adaptive_rho = int(bool(getattr(w, "adaptive_rho", False)))
+    pb.rho_mu = float(getattr(w, "rho_mu", 10.0))
+    pb.rho_tau_incr = float(getattr(w, "rho_tau_incr", 1.1))
+    pb.rho_tau_decr = float(getattr(w, "rho_tau_decr", 1.1))
     return pb, B, S
 
 
@@ -184,6 +190,10 @@ def solve(w, *, real: str = "double", state: bool = False, history: bool = False
     if history:
         out["history"] = np.zeros((max(K, 1), B, 2))
         res.history = _ptr(out["history"])
+        out["rho_hist"] = np.zeros((max(K, 1), B))
+        res.rho_hist = _ptr(out["rho_hist"])
+    out["rho_final"] = np.zeros(B)
+    res.rho_final = _ptr(out["rho_final"])
     if state:
         Mb, Mq, Mv, Mg = pb.M_box, pb.M_ball, pb.M_vn, pb.M_gen
         out.update({
@@ -199,7 +209,9 @@ def solve(w, *, real: str = "double", state: bool = False, history: bool = False
     if rc != 0:
         raise RuntimeError(f"oracle_solve failed with code {rc}")
     if history:
-        out["history"] = out["history"][: int(out["iters"].max()) if B else 0]
+        kmax = int(out["iters"].max()) if B else 0
+        out["history"] = out["history"][:kmax]
+        out["rho_hist"] = out["rho_hist"][:kmax]
     return out
 
 

@@ -14,6 +14,7 @@
  *   - the consensus average (Eq. 18b) and the scaled dual update (Eq. 18c),
  *   - the numerical local step of Sec. III-C.3 (Eq. 15-17) solved with L-BFGS,
  *   - primal / dual residuals (Eq. 19-20) and the stopping rule (Eq. 21),
+ *   - optionally the residual-balancing update of rho (UpdateRho, Eq. 22),
  * all with dense matrices built entry by entry (the 24x24 local matrix of
  * Eq. 18a, the 42x24 consensus map, the 2*3*M x 24 linear-constraint matrix,
  * the 3x24 sample matrices), solved with a Cholesky factorisation of the
@@ -45,6 +46,10 @@
  *       backtracking (c1 = 1e-4, halving), started from the minimiser of the
  *       quadratic part, stopped when g^T K^-1 g <= tol^2 rhs^T K^-1 rhs.
  *   R10 dual residual stacked per segment: rho * Mt_i^T E_i (zt_i^{k+1} - zt_i^k).
+ *   R13 UpdateRho runs after the stopping test of each iteration; when rho
+ *       changes, the unscaled duals rho*u, rho*v, rho*w are kept (every
+ *       scaled dual is multiplied by rho_old / rho_new) and each segment's
+ *       local matrix is assembled and factorised again for the new rho.
  *
  * Compile-time type: OR_REAL (default double; the oracle's own rounding is
  * bounded by re-running it with OR_REAL = long double).
@@ -91,6 +96,9 @@ typedef struct or_problem {
   double lbfgs_tol;          /* relative infinity-norm gradient tolerance */
   int32_t lbfgs_max_iters;
   int32_t lbfgs_mem;
+  /* adaptive penalty (Sec. III-D.4, Eq. 22); 0 keeps rho fixed */
+  int32_t adaptive_rho;
+  double rho_mu, rho_tau_incr, rho_tau_decr;
 } or_problem;
 
 typedef struct or_result {
@@ -109,6 +117,8 @@ typedef struct or_result {
   double *phi_v, *w_v;/* [S][M_vn][3] */
   double *y_gen;      /* [S][M_gen][2] (velocity, acceleration) */
   int32_t *inner_iters; /* [S] L-BFGS iterations summed over the run */
+  double *rho_hist;   /* optional [max_iters][B]: rho used in each iteration */
+  double *rho_final;  /* optional [B]: rho after the last update */
 } or_result;
 
 /* ------------------------------------------------------------------ */
@@ -309,6 +319,22 @@ static void free_segment(seg_data *sd) {
   free(sd->Ao); free(sd->b); free(sd->Ab); free(sd->Av); free(sd->Agv); free(sd->Aga);
 }
 
+/* the matrix of Eq. 18a for another penalty rho (adaptive rho, Eq. 22),
+ * assembled from the stored matrices and factored again */
+static int refactor_segment(seg_data *sd, const or_problem *pb, real rho) {
+  for (int i = 0; i < NL * NL; ++i) sd->K[i] = 2 * sd->Qt[i];
+  for (int i = 0; i < NL; ++i)
+    for (int j = 0; j < NL; ++j) {
+      real acc = 0;
+      for (int q = 0; q < NR; ++q) acc += sd->Mt[q * NL + i] * sd->E[q] * sd->Mt[q * NL + j];
+      sd->K[i * NL + j] += rho * acc;
+    }
+  if (sd->Ao) add_AtA(sd->K, sd->Ao, sd->nbox, rho);
+  for (int j = 0; j < pb->M_ball; ++j) add_AtA(sd->K, sd->Ab + (size_t)j * 3 * NL, 3, rho);
+  for (int j = 0; j < pb->M_vn; ++j) add_AtA(sd->K, sd->Av + (size_t)j * 3 * NL, 3, rho);
+  return chol_equil(NL, sd->K, sd->L, sd->S);
+}
+
 /* y = A x  (rows x NL) */
 static void matvec(const real *A, int rows, const real *x, real *y) {
   for (int q = 0; q < rows; ++q) {
@@ -464,7 +490,7 @@ static int solve_one(const or_problem *pb, or_result *res, int b) {
   const int s0 = pb->seg_offset[b];
   const int N = pb->seg_offset[b + 1] - s0;
   const double *P = pb->waypoints + (size_t)(s0 + b) * 3;
-  const real rho = pb->rho;
+  real rho = pb->rho;
   const int Mb = pb->M_box, Mq = pb->M_ball, Mv = pb->M_vn, Mg = pb->M_gen;
   const int nbox = 6 * Mb;
   if (N <= 0) {
@@ -646,9 +672,29 @@ static int solve_one(const or_problem *pb, or_result *res, int b) {
       res->history[((size_t)k * pb->B + b) * 2 + 0] = (double)rp;
       res->history[((size_t)k * pb->B + b) * 2 + 1] = (double)rd;
     }
+    if (res->rho_hist) res->rho_hist[(size_t)k * pb->B + b] = (double)rho;
     if (!isfin(rp) || !isfin(rd)) { status = OR_NONFINITE; ++k; break; }
     if (pb->eps > 0 && rp < eps_tol && rd < eps_tol) { status = OR_CONVERGED; ++k; break; }
+    if (pb->adaptive_rho) {
+      /* UpdateRho (Eq. 22): keep the two residuals within a factor mu */
+      real rn = rho;
+      if (rp > (real)pb->rho_mu * rd) rn = rho * (real)pb->rho_tau_incr;
+      else if (rd > (real)pb->rho_mu * rp) rn = rho / (real)pb->rho_tau_decr;
+      if (rn != rho) {
+        /* the scaled duals hold y / rho: keep the unscaled y fixed across
+           the change, so every scaled dual is multiplied by rho_old / rho_new */
+        const real f = rho / rn;
+        for (size_t q = 0; q < (size_t)N * NR; ++q) u[q] *= f;
+        for (size_t q = 0; q < (size_t)N * nbox; ++q) v[q] *= f;
+        for (size_t q = 0; q < (size_t)N * Mq * 3; ++q) wb[q] *= f;
+        for (size_t q = 0; q < (size_t)N * Mv * 3; ++q) wv[q] *= f;
+        rho = rn;
+        for (int i = 0; i < N; ++i)
+          if (refactor_segment(&sd[i], pb, rho) != 0) { status = OR_NONFINITE; break; }
+      }
+    }
   }
+  if (res->rho_final) res->rho_final[b] = (double)rho;
   /* outputs */
   real J = 0;
   for (int i = 0; i < N; ++i) {

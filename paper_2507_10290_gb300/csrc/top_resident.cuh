@@ -15,7 +15,7 @@
 //     m' = m + P - eE,  p' = p + P - eS_next
 //   trajectory end (orders < p):   p = z_N (fixed),  m' = m + z_N - eE
 //   trajectory start (orders < p): m = z_0 (fixed),  p' = p + z_0 - eS
-//   orders >= p at the two ends: p = m = 0 (dropped rows, reading R2).
+//   orders >= p at the two ends: p = m = 0 (those consensus rows are dropped).
 // The local step then reads p at its start slot and m at its end slot,
 // 42 values, with every special case already encoded.
 //

@@ -67,6 +67,10 @@ class Workload:
     M_gen: int = 0
     gen_vmax: Optional[np.ndarray] = None  # [B]
     gen_amax: Optional[np.ndarray] = None  # [B]
+    adaptive_rho: bool = False  # UpdateRho of Eq. 22 (mu, tau_incr, tau_decr as the paper: 10, 1.1, 1.1)
+    rho_mu: float = 10.0
+    rho_tau_incr: float = 1.1
+    rho_tau_decr: float = 1.1
     lbfgs_mem: int = 0          # numerical step settings (0 = the solver's default)
     lbfgs_max_iters: int = 0
     lbfgs_tol: float = 0.0

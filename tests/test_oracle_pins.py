@@ -392,3 +392,126 @@ def test_batch_is_per_trajectory_and_handles_empty():
         s0, s1 = a.seg_offset[b], a.seg_offset[b + 1]
         assert np.array_equal(rb["coeffs"], r["coeffs"][s0:s1])
         assert rb["cost"][0] == r["cost"][b]
+
+
+# ------------------------------------------------- adaptive rho (Eq. 22) --
+
+def _consensus_rows(T, first, last):
+    """M~ (42 x 24) and the end mask E of one segment, rows (a, side, r)."""
+    Mt = np.zeros((42, 24))
+    E = np.ones(42)
+    for a in range(3):
+        for side in range(2):
+            for rr in range(7):
+                row = a * 14 + side * 7 + rr
+                Mt[row, a * 8:(a + 1) * 8] = CZ.deriv_row(rr, T if side else 0.0)
+                if ((side == 0 and first) or (side == 1 and last)) and rr >= 4:
+                    E[row] = 0
+    return Mt, E
+
+
+def test_adaptive_rho_never_triggered_equals_fixed_rho():
+    w = W.tiny(seed=2, N=[5, 9], mode="pin").with_(max_iters=80)
+    r0 = oracle.solve(w)
+    r1 = oracle.solve(w.with_(adaptive_rho=True, rho_mu=1e300))
+    assert np.array_equal(r0["coeffs"], r1["coeffs"]) and np.array_equal(r0["cost"], r1["cost"])
+
+
+def adaptive_rule_violations(lib=None):
+    """Count of iterations whose next rho breaks Eq. 22 (mu = 10, tau = 1.1),
+    and the numbers of increases and decreases of rho seen, over a run that
+    starts at rho = 1 (r_d dominates) and one at rho = 1e-3 (r_p dominates)."""
+    bad, up, down = 0, 0, 0
+    for rho0 in (1.0, 1e-3):
+        w = W.tiny(seed=3, N=[12], mode="pin").with_(max_iters=400, adaptive_rho=True, rho=rho0)
+        r = oracle.solve(w, history=True, **({} if lib is None else {"real": lib}))
+        rho, h = r["rho_hist"][:, 0], r["history"][:, 0]
+        bad += rho[0] != rho0
+        for k in range(len(rho) - 1):
+            rp, rd = h[k]
+            expect = rho[k] * 1.1 if rp > 10 * rd else (rho[k] / 1.1 if rd > 10 * rp else rho[k])
+            bad += abs(rho[k + 1] - expect) > 1e-14 * expect
+            up += rho[k + 1] > rho[k]
+            down += rho[k + 1] < rho[k]
+    return bad, up, down
+
+
+def test_adaptive_rho_follows_the_update_rule():
+    """rho_{k+1} = 1.1 rho_k if r_p > 10 r_d, rho_k / 1.1 if r_d > 10 r_p, else rho_k (Eq. 22)."""
+    bad, up, down = adaptive_rule_violations()
+    assert bad == 0 and up > 10 and down > 10
+
+
+def test_adaptive_rho_reaches_the_same_fixed_point():
+    """The schedule of rho changes the path, not the limit: FREE mode still ends
+    at the single polynomial (P3).  On small PIN instances the rule settles at
+    rho ~ 0.027, where plain ADMM is slow, so PIN-like behaviour is pinned by the
+    box-KKT certificate below instead."""
+    w = W.tiny(seed=1, N=8, mode="free", T_range=(0.8, 1.6)).with_(max_iters=30000, adaptive_rho=True)
+    r = oracle.solve(w)
+    assert r["rho_final"][0] != 1.0
+    ref = CZ.free_polynomial(w.durations, w.start_state[0], w.end_state[0])
+    assert scaled_relerr(r["coeffs"], ref, w.durations) < 1e-8
+
+
+def adaptive_kkt_error(lib=None):
+    """Stationarity of the converged box problem with the final rho and the
+    final scaled duals (y = rho u, mu = rho v), relative to |2 Qt c|."""
+    w = _box_instance().with_(adaptive_rho=True, max_iters=100000, rho=10.0)
+    r = oracle.solve(w, state=True, **({} if lib is None else {"real": lib}))
+    rho = r["rho_final"][0]
+    T, M = w.durations, w.M_box
+    N = len(T)
+    worst = 0.0
+    for i in range(N):
+        Mt, E = _consensus_rows(T[i], i == 0, i == N - 1)
+        Ao = []
+        for j in range(1, M + 1):
+            for a in range(3):
+                for sg in (1.0, -1.0):
+                    row = np.zeros(24)
+                    row[a * 8:(a + 1) * 8] = sg * CZ.deriv_row(1, j * T[i] / M)
+                    Ao.append(row)
+        Ao = np.array(Ao)
+        Qt = np.zeros((24, 24))
+        for a in range(3):
+            Qt[a * 8:(a + 1) * 8, a * 8:(a + 1) * 8] = CZ.snap_gram(T[i])
+        ci = r["coeffs"][i].reshape(24)
+        stat = 2 * Qt @ ci + rho * Mt.T @ (E * r["u"][i]) + Ao.T @ (rho * r["v"][i])
+        worst = max(worst, np.abs(stat).max() / np.abs(2 * Qt @ ci).max())
+    return worst, rho
+
+
+def test_adaptive_rho_keeps_box_kkt_certificate():
+    err, rho = adaptive_kkt_error()
+    assert rho != 10.0 and err < 1e-5
+
+
+def adaptive_dual_continuity_error(lib=None):
+    """Across a change of rho the unscaled consensus dual y = rho u follows
+    y+ = y + rho_k E (M~ c+ - z+) exactly (Eq. 18c in unscaled form), however the
+    scaled copy is stored.  Returns the largest relative violation over the
+    first few changes of rho in a box-constrained FREE run."""
+    w = _box_instance().with_(adaptive_rho=True)
+    kw = {} if lib is None else {"real": lib}
+    hist = oracle.solve(w.with_(max_iters=200), history=True, **kw)["rho_hist"][:, 0]
+    changes = [k for k in range(1, len(hist)) if hist[k] != hist[k - 1]][:4]
+    if not changes:
+        return np.inf
+    worst = 0.0
+    N = len(w.durations)
+    for m1 in changes:           # rho changed after iteration m1 - 1 (0-based)
+        a = oracle.solve(w.with_(max_iters=m1 - 1), state=True, **kw)
+        b = oracle.solve(w.with_(max_iters=m1), state=True, **kw)
+        rho_a, rho_b = a["rho_final"][0], b["rho_final"][0]
+        for i in range(N):
+            Mt, E = _consensus_rows(w.durations[i], i == 0, i == N - 1)
+            zt = np.concatenate([b["z"][i][ax].tolist() + b["z"][i + 1][ax].tolist() for ax in range(3)])
+            y_next = rho_a * (a["u"][i] + E * (Mt @ b["coeffs"][i].reshape(24) - zt))
+            err = np.abs(rho_b * b["u"][i] - y_next).max() / max(np.abs(y_next).max(), 1e-30)
+            worst = max(worst, err)
+    return worst
+
+
+def test_adaptive_rho_unscaled_dual_is_continuous():
+    assert adaptive_dual_continuity_error() < 1e-12

@@ -15,7 +15,8 @@ from oracle import capi
 from oracle import centralized as CZ
 from paper_2507_10290_gb300 import workloads as W
 
-from test_oracle_pins import _box_instance, _numpy_F, read_golden, scaled_relerr
+from test_oracle_pins import (_box_instance, _numpy_F, adaptive_dual_continuity_error, adaptive_kkt_error,
+                              adaptive_rule_violations, read_golden, scaled_relerr)
 
 
 def pin_closed_form(lib):
@@ -106,8 +107,22 @@ def pin_numeric_stationary(lib):
     return True
 
 
+def pin_adaptive_rule(lib):
+    bad, up, down = adaptive_rule_violations(lib)
+    return bad == 0 and up > 10 and down > 10
+
+
+def pin_adaptive_kkt(lib):
+    err, rho = adaptive_kkt_error(lib)
+    return rho != 10.0 and err < 1e-5
+
+
+def pin_adaptive_dual(lib):
+    return adaptive_dual_continuity_error(lib) < 1e-12
+
+
 ALL_PINS = [pin_projection, pin_closed_form, pin_numeric_stationary, pin_free_fixed_point,
-            pin_active_set, pin_pin_fixed_point]
+            pin_active_set, pin_pin_fixed_point, pin_adaptive_rule, pin_adaptive_dual, pin_adaptive_kkt]
 
 PLANTS = {
     "rhs without rho": ("for (int l = 0; l < NL; ++l) rhs[l] *= rho;\n        chol_solve",
@@ -127,6 +142,10 @@ PLANTS = {
     "penalty gradient": ("real coef = (rho * g + y) * 4 * h;", "real coef = (rho * g + y) * 2 * h;"),
     "velocity sample row": ("sample_matrix(1, t, sd->Agv + (size_t)j * 3 * NL);",
                             "sample_matrix(2, t, sd->Agv + (size_t)j * 3 * NL);"),
+    "scaled duals kept on rho change": ("const real f = rho / rn;", "const real f = 1;"),
+    "rho rule inverted": ("rn = rho * (real)pb->rho_tau_incr;", "rn = rho / (real)pb->rho_tau_incr;"),
+    "K kept at old rho": ("if (refactor_segment(&sd[i], pb, rho) != 0)",
+                          "if (0 && refactor_segment(&sd[i], pb, rho) != 0)"),
 }
 
 
