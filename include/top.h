@@ -118,6 +118,18 @@ typedef struct top_problem {
   int32_t lbfgs_mem;          /* numerical step: L-BFGS memory (0 = 8) */
   int32_t lbfgs_max_iters;    /* numerical step: iteration cap per local solve (0 = 50) */
   double lbfgs_tol;           /* numerical step: relative gradient tolerance (0 = 1e-6 FP32 / 1e-12 FP64) */
+  /* Residual balancing of rho (UpdateRho of Algorithm 1, Eq. 22), per
+   * trajectory.  0 keeps rho fixed.  1: after the stopping test of every
+   * iteration, rho <- rho * rho_tau_incr when ||r_p|| > rho_mu ||r_d||, and
+   * rho <- rho / rho_tau_decr when ||r_d|| > rho_mu ||r_p||; the unscaled
+   * duals are kept across a change (every scaled dual is multiplied by
+   * rho_old / rho_new) and the local matrix inverse follows the new rho.
+   * Residuals are then evaluated at every iteration (check_every is ignored).
+   * Not available in top_grad and top_solve_noalloc (TOP_E_NOTSUP). */
+  int32_t adaptive_rho;
+  double rho_mu;              /* >= 1 (0 = 10) */
+  double rho_tau_incr;        /* >= 1 (0 = 1.1) */
+  double rho_tau_decr;        /* >= 1 (0 = 1.1) */
 } top_problem;
 
 /* Outputs (same memory kind as the problem).  history may be NULL. */
@@ -130,6 +142,7 @@ typedef struct top_result {
   int32_t *status;   /* [B] TOP_CONVERGED | TOP_NOT_CONVERGED | TOP_NONFINITE */
   double *history;   /* optional [max_iters][B][2]: (||r_p||, ||r_d||) at every evaluated iteration
                         (entries of iterations that were not evaluated are left untouched) */
+  double *rho;       /* optional [B]: rho after the last update (adaptive_rho), else the fixed rho */
 } top_result;
 
 /* Allocate a handle and its device workspace on the current CUDA device.

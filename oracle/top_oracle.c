@@ -496,6 +496,7 @@ static int solve_one(const or_problem *pb, or_result *res, int b) {
   if (N <= 0) {
     res->cost[b] = 0; res->r_primal[b] = 0; res->r_dual[b] = 0;
     res->iters[b] = 0; res->status[b] = OR_CONVERGED;
+    if (res->rho_final) res->rho_final[b] = (double)rho;  /* no iteration, no update */
     return 0;
   }
   seg_data *sd = (seg_data *)calloc((size_t)N, sizeof(seg_data));

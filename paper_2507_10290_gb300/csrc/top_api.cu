@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -23,6 +24,8 @@ struct top_handle {
   int last_cuda = 0;
   // device workspace
   void *G = nullptr;          // [36][max_segments] of the iteration type
+  void *E = nullptr;          // [NE][S] adaptive-rho data (allocated on first use)
+  size_t E_bytes = 0;
   Pack *d_packs = nullptr;    // [max_segments]
   int *d_err = nullptr;       // error flag of the precompute kernel
   // staging for TOP_MEM_HOST problems
@@ -174,7 +177,7 @@ void plan_packs(const int32_t *off, int B, int cap, int ntp_cap, Pack *packs, in
 
 struct StagePlan {
   size_t off_seg, off_wp, off_T, off_s0, off_s1, off_vbox, off_bc, off_br, off_vn, off_gv, off_ga;
-  size_t off_coef, off_cost, off_rp, off_rd, off_it, off_st, total;
+  size_t off_coef, off_cost, off_rp, off_rd, off_it, off_st, off_rho, total;
 };
 
 StagePlan stage_plan(int Bmax, int Smax) {
@@ -198,6 +201,7 @@ StagePlan stage_plan(int Bmax, int Smax) {
   P.off_rd = take(sizeof(double) * Bmax);
   P.off_it = take(sizeof(int32_t) * Bmax);
   P.off_st = take(sizeof(int32_t) * Bmax);
+  P.off_rho = take(sizeof(double) * Bmax);
   P.total = o;
   return P;
 }
@@ -220,6 +224,11 @@ int validate(const top_handle *h, const top_problem *pb, const top_result *res) 
   if (pb->M_gen > 0 && (!pb->gen_vmax || !pb->gen_amax)) return TOP_E_INVAL;
   if (pb->inner == TOP_NUMERIC && (pb->M_box || pb->M_ball || pb->M_vn)) return TOP_E_NOTSUP;
   if (pb->inner == TOP_CLOSED_FORM && pb->M_gen) return TOP_E_NOTSUP;
+  if (pb->adaptive_rho != 0 && pb->adaptive_rho != 1) return TOP_E_INVAL;
+  if (pb->adaptive_rho) {
+    for (double v : {pb->rho_mu, pb->rho_tau_incr, pb->rho_tau_decr})
+      if (v != 0.0 && !(v >= 1.0 && std::isfinite(v))) return TOP_E_INVAL;
+  }
   if (pb->B > 0 && (!pb->seg_offset || !pb->waypoints || !pb->start_state || !pb->end_state))
     return TOP_E_INVAL;
   if (pb->B > 0 && (!res->coeffs || !res->cost || !res->r_primal || !res->r_dual || !res->iters ||
@@ -278,6 +287,7 @@ void top_destroy(top_handle *h) {
   cudaGetDevice(&prev);
   cudaSetDevice(h->device);
   cudaFree(h->G);
+  cudaFree(h->E);
   cudaFree(h->d_packs);
   cudaFree(h->d_err);
   cudaFree(h->d_stage);
@@ -393,6 +403,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     res.r_dual = (double *)(base + SP.off_rd);
     res.iters = (int32_t *)(base + SP.off_it);
     res.status = (int32_t *)(base + SP.off_st);
+    res.rho = res_in->rho ? (double *)(base + SP.off_rho) : nullptr;
     res.history = nullptr;
     if (res_in->history && pb.max_iters > 0) {
       TOP_CUDA(h, cudaMalloc((void **)&d_hist, sizeof(double) * 2 * (size_t)pb.max_iters * B));
@@ -414,9 +425,13 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   dp.lbfgs_mem = pb.lbfgs_mem > 0 ? pb.lbfgs_mem : 8;
   dp.lbfgs_max_iters = pb.lbfgs_max_iters > 0 ? pb.lbfgs_max_iters : 50;
   dp.lbfgs_tol = pb.lbfgs_tol > 0 ? pb.lbfgs_tol : (h->cfg.precision == TOP_FP64 ? 1e-12 : 1e-6);
+  dp.adaptive = pb.adaptive_rho;
+  dp.rho_mu = pb.rho_mu > 0 ? pb.rho_mu : 10.0;
+  dp.rho_incr = pb.rho_tau_incr > 0 ? pb.rho_tau_incr : 1.1;
+  dp.rho_decr = pb.rho_tau_decr > 0 ? pb.rho_tau_decr : 1.1;
   DevResult dr{};
   dr.coeffs = res.coeffs; dr.cost = res.cost; dr.r_primal = res.r_primal; dr.r_dual = res.r_dual;
-  dr.history = res.history; dr.iters = res.iters; dr.status = res.status;
+  dr.history = res.history; dr.iters = res.iters; dr.status = res.status; dr.rho = res.rho;
 
   // ---- per-trajectory outputs start at zero (covers empty trajectories) ----
   TOP_CUDA(h, cudaMemsetAsync(dr.cost, 0, sizeof(double) * B, st));
@@ -424,6 +439,25 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   TOP_CUDA(h, cudaMemsetAsync(dr.r_dual, 0, sizeof(double) * B, st));
   TOP_CUDA(h, cudaMemsetAsync(dr.iters, 0, sizeof(int32_t) * B, st));
   TOP_CUDA(h, cudaMemsetAsync(dr.status, 0, sizeof(int32_t) * B, st));
+  if (dr.rho) {
+    int e = launch_fill(dr.rho, B, pb.rho, st);
+    if (e) return cuda_fail(h, (cudaError_t)e);
+  }
+  // ---- adaptive-rho data: grow-only workspace ----
+  const bool adapt = pb.adaptive_rho != 0;
+  if (adapt && (size_t)NE * S * rbytes(h) > h->E_bytes) {
+    cudaFree(h->E);
+    h->E = nullptr;
+    h->E_bytes = 0;
+    const size_t want = (size_t)NE * h->cfg.max_segments * rbytes(h);
+    cudaError_t e = cudaMalloc(&h->E, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (d_hist) cudaFree(d_hist);
+      return e == cudaErrorMemoryAllocation ? TOP_E_NOMEM : cuda_fail(h, e);
+    }
+    h->E_bytes = want;
+  }
   // ---- FP64 local-matrix inverses (Eq. 18a) ----
   TOP_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
   const bool fp64 = h->cfg.precision == TOP_FP64;
@@ -432,6 +466,10 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     if (h->profiling) cudaEventRecord(h->ev[0], st);
     int e = launch_kinv(dp, pb.rho, fp64 ? nullptr : h->G, fp64 ? h->G : nullptr, h->d_err, st);
     if (e) return cuda_fail(h, (cudaError_t)e);
+    if (adapt) {
+      e = launch_keig(dp, fp64 ? nullptr : h->E, fp64 ? h->E : nullptr, h->d_err, st);
+      if (e) return cuda_fail(h, (cudaError_t)e);
+    }
     if (h->profiling) { cudaEventRecord(h->ev[1], st); h->ran[0] = true; }
   }
   // ---- plan: resident packs of whole trajectories ----
@@ -470,6 +508,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     const ResLayout L = res_layout(C, ntp, Mb, Mq, Mv, (int)rbytes(h));
     ResidentArgs ra{};
     ra.p = dp; ra.r = dr; ra.G = h->G; ra.packs = h->d_packs; ra.traj_list = h->d_tlist; ra.ntp = ntp;
+    ra.E = adapt ? h->E : nullptr;
     if (h->profiling) cudaEventRecord(h->ev[2], st);
     int e = fp64 ? launch_resident_f64(ra, npack, C, L.total, fam, st)
                  : launch_resident_f32(ra, npack, C, L.total, fam, st);
@@ -505,6 +544,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     const size_t o_yg = take(rb * 2 * Mg * (size_t)S);
     const size_t o_rp = take(sizeof(double) * total), o_rd = take(sizeof(double) * total);
     const size_t o_done = take(sizeof(int) * nl), o_trp = take(sizeof(double) * nl), o_trd = take(sizeof(double) * nl);
+    const size_t o_rho = take(sizeof(double) * nl), o_fac = take(sizeof(double) * nl);
     const size_t o_lt = take(sizeof(int) * (2 * (size_t)nl + 1));
     if (o > h->stream_bytes) {
       cudaFree(h->d_stream);
@@ -533,6 +573,8 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     sa.ygen = base + o_yg; sa.inner_iters = nullptr;
     sa.rp2 = (double *)(base + o_rp); sa.rd2 = (double *)(base + o_rd);
     sa.done = (int *)(base + o_done); sa.tr_rp = (double *)(base + o_trp); sa.tr_rd = (double *)(base + o_trd);
+    sa.rho_t = (double *)(base + o_rho); sa.fac_t = (double *)(base + o_fac);
+    sa.E = adapt ? h->E : nullptr;
     if (h->profiling) cudaEventRecord(h->ev[4], st);
     int e = fp64 ? launch_stream_f64(sa, fam, st) : launch_stream_f32(sa, fam, st);
     if (e) return cuda_fail(h, (cudaError_t)e);
@@ -546,6 +588,8 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     TOP_CUDA(h, cudaMemcpyAsync(res_in->r_dual, res.r_dual, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
     TOP_CUDA(h, cudaMemcpyAsync(res_in->iters, res.iters, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
     TOP_CUDA(h, cudaMemcpyAsync(res_in->status, res.status, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
+    if (res.rho)
+      TOP_CUDA(h, cudaMemcpyAsync(res_in->rho, res.rho, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
     if (d_hist)
       TOP_CUDA(h, cudaMemcpyAsync(res_in->history, d_hist, sizeof(double) * 2 * (size_t)pb.max_iters * B,
                                   cudaMemcpyDeviceToHost, st));
@@ -567,6 +611,7 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
   int rc = validate(h, pb_in, &fake);
   if (rc != TOP_OK) return rc;
   if (pb_in->M_box || pb_in->M_ball || pb_in->M_vn || pb_in->M_gen) return TOP_E_NOTSUP;
+  if (pb_in->adaptive_rho) return TOP_E_NOTSUP;
   cudaStream_t st = (cudaStream_t)stream;
   TOP_CUDA(h, cudaSetDevice(h->device));
   const int B = pb_in->B;
@@ -607,6 +652,7 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
   const size_t o_eS = take(rb * 21 * (size_t)S), o_eE = take(rb * 21 * (size_t)S), o_ch = take(rb * 24 * (size_t)S);
   const size_t o_rp = take(sizeof(double) * total), o_rd = take(sizeof(double) * total);
   const size_t o_done = take(sizeof(int) * nl), o_trp = take(sizeof(double) * nl), o_trd = take(sizeof(double) * nl);
+  const size_t o_rho = take(sizeof(double) * nl), o_fac = take(sizeof(double) * nl);
   const size_t o_lt = take(sizeof(int) * (2 * (size_t)nl + 1));
   const size_t o_ck = take((bz * 2 + buRp + buR0 + 4 * 256) * (size_t)nblk);
   const size_t o_tape = take((bz * 2 + buRp + buR0 + 4 * 256) * (size_t)ckpt);
@@ -679,6 +725,8 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
     sa.inner_iters = nullptr;
     sa.rp2 = (double *)(base + o_rp); sa.rd2 = (double *)(base + o_rd);
     sa.done = (int *)(base + o_done); sa.tr_rp = (double *)(base + o_trp); sa.tr_rd = (double *)(base + o_trd);
+    sa.rho_t = (double *)(base + o_rho); sa.fac_t = (double *)(base + o_fac);
+    sa.E = nullptr;
     AdjArgs aa{};
     aa.f = sa;
     aa.zb = base + o_zb; aa.uLb = base + o_uLb; aa.uRb = base + o_uRb; aa.uR0b = base + o_uR0b;

@@ -33,17 +33,28 @@ struct DevProblem {
   int M_gen;  const double *gen_vmax, *gen_amax;
   int lbfgs_mem, lbfgs_max_iters;
   double lbfgs_tol;
+  int adaptive;   // residual balancing of rho (Eq. 22)
+  double rho_mu, rho_incr, rho_decr;
 };
 
 struct DevResult {
   double *coeffs, *cost, *r_primal, *r_dual, *history;
   int32_t *iters, *status;
+  double *rho;          // [B] final rho, or null
 };
+
+// Per-segment data that rebuilds the local-matrix inverse for any rho
+// (adaptive rho): K(rho) = 2 T^-7 Qh + rho H in the normalised basis, and
+//   G(rho) = K(rho)^{-1} = A0 / rho + sum_{k<4} y_k y_k^T / (lambda_k + rho)
+// with A0 supported on the top-left 4x4 block (packed lower, 10 values),
+// Y = [y_0 .. y_3] (8 x 4, row-major) and lambda_k >= 0.  Layout [NE][S].
+constexpr int NE_A0 = 0, NE_Y = 10, NE_L = 42, NE = 46;
 
 struct ResidentArgs {
   DevProblem p;
   DevResult r;
   const void *G;        // [36][S] packed (D K D)^{-1}, element type = iteration type
+  const void *E;        // [NE][S] adaptive-rho data (same type), or null
   const Pack *packs;
   const int *traj_list; // trajectory ids, grouped by pack
   int ntp;              // trajectory slots per pack (shared-memory sizing)
@@ -54,7 +65,8 @@ struct ResidentArgs {
 struct ResLayout {
   size_t red_rp, red_rd, tr_rp, tr_rd;           // double arrays
   size_t p, m, zP, eS, dz, ybox, qball, qvn, tabB, tabQ, tabV;  // element arrays
-  size_t off, done, tid;                         // int arrays
+  size_t off, done, tid, flag;                   // int arrays
+  size_t rho, fac;                               // double arrays (per trajectory)
   size_t total;
 };
 
@@ -84,6 +96,10 @@ __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, 
   L.off = o;    o += sizeof(int) * (ntp + 1);
   L.done = o;   o += sizeof(int) * ntp;
   L.tid = o;    o += sizeof(int) * ntp;
+  L.flag = o;   o += sizeof(int);
+  o = align_up(o, 8);
+  L.rho = o;    o += sizeof(double) * ntp;
+  L.fac = o;    o += sizeof(double) * ntp;
   L.total = align_up(o, 16);
   return L;
 }
@@ -94,7 +110,8 @@ __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, 
 struct StreamArgs {
   DevProblem p;
   DevResult r;
-  const void *G;           // [36][S]
+  const void *G;           // [36][S] (rewritten on a change of rho)
+  const void *E;           // [NE][S] adaptive-rho data, or null
   const int *lt_b;         // [nl]
   const int *lt_prefix;    // [nl+1]
   int nl, total;           // trajectories, segments in the streaming set
@@ -111,10 +128,13 @@ struct StreamArgs {
   double *rp2, *rd2;       // [total]
   int *done;               // [nl]
   double *tr_rp, *tr_rd;   // [nl]
+  double *rho_t, *fac_t;   // [nl] current rho, rescale factor of the last update
 };
 
 // launchers (defined in the .cu files)
 int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_flag, void *stream);
+int launch_keig(const DevProblem &p, void *E32, void *E64, int *err_flag, void *stream);
+int launch_fill(double *x, int n, double v, void *stream);
 int launch_resident_f32(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
 int launch_resident_f64(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
 int launch_stream_f32(const StreamArgs &a, int fam, void *stream);

@@ -80,86 +80,107 @@ __device__ __forceinline__ void chol_col(double (&A)[NG], double (&inv)[NC], boo
   if constexpr (J + 1 < NC) chol_col<J + 1>(A, inv, ok);
 }
 
+// the rho-weighted terms of the local matrix: consensus rows (Mt^T E Mt) and
+// the sample rows of the closed-form constraint families, each times `rho`
+template <bool SAMPLES>
+__device__ __forceinline__ void add_rho_terms(const DevProblem &p, const double (&s)[NC], bool first, bool last,
+                                              double rho, double (&A)[NG]) {
+#pragma unroll
+  for (int q = 0; q < ND; ++q) {
+    if (!(first && q >= PO)) {
+      const double v = double(fact(q)) * s[q];
+      A[lidx(q, q)] += rho * v * v;
+    }
+    if (!(last && q >= PO)) {
+      const double w = rho * s[q] * s[q];
+#pragma unroll
+      for (int r = q; r < NC; ++r)
+#pragma unroll
+        for (int c = q; c <= r; ++c) A[lidx(r, c)] += w * double(falling(r, q)) * double(falling(c, q));
+    }
+  }
+  if (SAMPLES && p.inner == 0) {
+    if (p.M_box > 0) add_sample_rows(A, p.M_box, 1, 2.0 * rho * s[1] * s[1]);
+    if (p.M_ball > 0) add_sample_rows(A, p.M_ball, 0, rho);
+    if (p.M_vn > 0) add_sample_rows(A, p.M_vn, 1, rho * s[1] * s[1]);
+  }
+}
+
+// segment g's place in its trajectory and its powers s_r = T^-r; false for a
+// duration that is not positive and finite
+__device__ __forceinline__ bool segment_setup(const DevProblem &p, int g, bool &first, bool &last,
+                                              double (&s)[NC]) {
+  const int b = find_traj(p.seg_offset, p.B, g);
+  const int i = g - p.seg_offset[b];
+  const int N = p.seg_offset[b + 1] - p.seg_offset[b];
+  first = (i == 0);
+  last = (i == N - 1);
+  const double T = p.durations[g];
+  if (!(T > 0.0) || !(T < 1e30)) return false;
+  const double it = 1.0 / T;
+  s[0] = 1.0;
+#pragma unroll
+  for (int r = 1; r < NC; ++r) s[r] = s[r - 1] * it;
+  return true;
+}
+
+// Jacobi equilibration (A <- D A D, D = diag(A)^-1/2), Cholesky and inversion
+// of the factor, all in place: A ends as L^-1 of D A D (packed lower).
+// Returns false if A is not positive definite.
+__device__ __forceinline__ bool equil_chol_inv(double (&A)[NG], double (&d)[NC]) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const double akk = A[lidx(k, k)];
+    ok = ok && (akk > 0.0);
+    d[k] = ok ? rsqrt(akk) : 0.0;
+  }
+  if (!ok) return false;
+#pragma unroll
+  for (int r = 0; r < NC; ++r)
+#pragma unroll
+    for (int c = 0; c <= r; ++c) A[lidx(r, c)] *= d[r] * d[c];
+  // Cholesky in place: A <- L (lower), inv[j] = 1 / L_jj
+  double inv[NC];
+  chol_col<0>(A, inv, ok);
+  if (!ok) return false;
+  // invert L in place, column by column: X_jj = 1/L_jj,
+  // X_rj = -(1/L_rr) (L_rj X_jj + sum_{j<k<r} L_rk X_kj)
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    A[lidx(j, j)] = inv[j];
+#pragma unroll
+    for (int r = j + 1; r < NC; ++r) {
+      double a = A[lidx(r, j)] * A[lidx(j, j)];
+#pragma unroll
+      for (int k = j + 1; k < r; ++k) a += A[lidx(r, k)] * A[lidx(k, j)];
+      A[lidx(r, j)] = -inv[r] * a;
+    }
+  }
+  return true;
+}
+
 template <bool SAMPLES>
 __global__ void __launch_bounds__(128) kinv_kernel(const DevProblem p, double rho, float *__restrict__ G32,
                                                    double *__restrict__ G64, int *__restrict__ err) {
   const int S = p.S;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < S; g += gridDim.x * blockDim.x) {
-    const int b = find_traj(p.seg_offset, p.B, g);
-    const int i = g - p.seg_offset[b];
-    const int N = p.seg_offset[b + 1] - p.seg_offset[b];
-    const bool first = (i == 0), last = (i == N - 1);
-    const double T = p.durations[g];
-    if (!(T > 0.0) || !(T < 1e30)) {
+    bool first, last;
+    double s[NC];
+    if (!segment_setup(p, g, first, last, s)) {
       atomicOr(err, 1);
       continue;
     }
-    double s[NC];
-    const double it = 1.0 / T;
-    s[0] = 1.0;
-#pragma unroll
-    for (int r = 1; r < NC; ++r) s[r] = s[r - 1] * it;
     double A[NG];
 #pragma unroll
     for (int r = 0; r < NC; ++r)
 #pragma unroll
       for (int c = 0; c <= r; ++c) A[lidx(r, c)] = 2.0 * s[7] * qhat(r, c);
-    // consensus rows (Mt^T E Mt)
-#pragma unroll
-    for (int q = 0; q < ND; ++q) {
-      if (!(first && q >= PO)) {
-        const double v = double(fact(q)) * s[q];
-        A[lidx(q, q)] += rho * v * v;
-      }
-      if (!(last && q >= PO)) {
-        const double w = rho * s[q] * s[q];
-#pragma unroll
-        for (int r = q; r < NC; ++r)
-#pragma unroll
-          for (int c = q; c <= r; ++c) A[lidx(r, c)] += w * double(falling(r, q)) * double(falling(c, q));
-      }
-    }
-    if (SAMPLES && p.inner == 0) {
-      if (p.M_box > 0) add_sample_rows(A, p.M_box, 1, 2.0 * rho * s[1] * s[1]);
-      if (p.M_ball > 0) add_sample_rows(A, p.M_ball, 0, rho);
-      if (p.M_vn > 0) add_sample_rows(A, p.M_vn, 1, rho * s[1] * s[1]);
-    }
-    // Jacobi equilibration: A <- D A D, D = diag(A)^-1/2
+    add_rho_terms<SAMPLES>(p, s, first, last, rho, A);
     double d[NC];
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      const double akk = A[lidx(k, k)];
-      ok = ok && (akk > 0.0);
-      d[k] = ok ? rsqrt(akk) : 0.0;
-    }
-    if (!ok) {
+    if (!equil_chol_inv(A, d)) {
       atomicOr(err, 2);
       continue;
-    }
-#pragma unroll
-    for (int r = 0; r < NC; ++r)
-#pragma unroll
-      for (int c = 0; c <= r; ++c) A[lidx(r, c)] *= d[r] * d[c];
-    // Cholesky in place: A <- L (lower), inv[j] = 1 / L_jj
-    double inv[NC];
-    chol_col<0>(A, inv, ok);
-    if (!ok) {
-      atomicOr(err, 2);
-      continue;
-    }
-    // invert L in place, column by column: X_jj = 1/L_jj,
-    // X_rj = -(1/L_rr) (L_rj X_jj + sum_{j<k<r} L_rk X_kj)
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-      A[lidx(j, j)] = inv[j];
-#pragma unroll
-      for (int r = j + 1; r < NC; ++r) {
-        double a = A[lidx(r, j)] * A[lidx(j, j)];
-#pragma unroll
-        for (int k = j + 1; k < r; ++k) a += A[lidx(r, k)] * A[lidx(k, j)];
-        A[lidx(r, j)] = -inv[r] * a;
-      }
     }
     // (D K D)^-1 = L^-T L^-1, so K^-1 = D L^-T L^-1 D
 #pragma unroll
@@ -175,6 +196,165 @@ __global__ void __launch_bounds__(128) kinv_kernel(const DevProblem p, double rh
         if (G32) G32[size_t(idx) * S + g] = float(v);
       }
   }
+}
+
+// one cyclic-Jacobi rotation of the symmetric 4x4 matrix C zeroing C[P][Q]
+// (textbook symmetric Schur decomposition, e.g. Golub & Van Loan, Sec. 8.5),
+// accumulated into the eigenvector columns of V
+template <int P, int Q>
+__device__ __forceinline__ void jacobi_rot(double (&C)[4][4], double (&V)[4][4]) {
+  const double apq = C[P][Q];
+  if (apq == 0.0) return;
+  const double theta = (C[Q][Q] - C[P][P]) / (2.0 * apq);
+  const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
+  const double c = rsqrt(1.0 + t * t), sn = t * c;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {  // columns P, Q of C J
+    const double ckp = C[k][P], ckq = C[k][Q];
+    C[k][P] = c * ckp - sn * ckq;
+    C[k][Q] = sn * ckp + c * ckq;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {  // rows P, Q of J^T (C J)
+    const double cpk = C[P][k], cqk = C[Q][k];
+    C[P][k] = c * cpk - sn * cqk;
+    C[Q][k] = sn * cpk + c * cqk;
+  }
+  C[P][Q] = C[Q][P] = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double vkp = V[k][P], vkq = V[k][Q];
+    V[k][P] = c * vkp - sn * vkq;
+    V[k][Q] = sn * vkp + c * vkq;
+  }
+}
+
+// Adaptive-rho data of every segment (FP64).  With H the rho-weighted part of
+// the local matrix and D its Jacobi scaling, D H D = L L^T and M = L^-1 D
+// (lower triangular).  The cost block 2 T^-7 Qh lives on coefficients 4..7
+// only, so  M K(rho) M^T = rho I + blockdiag(0, C4),  C4 = M44 Q4 M44^T, and
+// with C4 = V diag(lambda) V^T:
+//   K(rho)^-1 = M^T blockdiag(I / rho, V diag(1 / (lambda + rho)) V^T) M
+//             = A0 / rho + Y diag(1 / (lambda + rho)) Y^T,
+//   A0 = M_top^T M_top (rows 0..3 of M, columns 0..3 only),  Y = M_bot^T V.
+template <bool SAMPLES>
+__global__ void __launch_bounds__(128) keig_kernel(const DevProblem p, float *__restrict__ E32,
+                                                   double *__restrict__ E64, int *__restrict__ err) {
+  const int S = p.S;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < S; g += gridDim.x * blockDim.x) {
+    bool first, last;
+    double s[NC];
+    if (!segment_setup(p, g, first, last, s)) {
+      atomicOr(err, 1);
+      continue;
+    }
+    double A[NG];
+#pragma unroll
+    for (int q = 0; q < NG; ++q) A[q] = 0.0;
+    add_rho_terms<SAMPLES>(p, s, first, last, 1.0, A);
+    double d[NC];
+    if (!equil_chol_inv(A, d)) {
+      atomicOr(err, 2);
+      continue;
+    }
+    // M = L^-1 D in place (lower triangular)
+#pragma unroll
+    for (int r = 0; r < NC; ++r)
+#pragma unroll
+      for (int c = 0; c <= r; ++c) A[lidx(r, c)] *= d[c];
+    // C4 = M44 Q4 M44^T with Q4 = 2 s_7 Qh[4..7][4..7]
+    double W[4][4];  // W = M44 Q4
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        double a = 0.0;
+#pragma unroll
+        for (int k = 0; k <= i; ++k) a += A[lidx(PO + i, PO + k)] * (2.0 * s[7] * qhat(PO + k, PO + j));
+        W[i][j] = a;
+      }
+    double Cm[4][4], V[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        double a = 0.0;
+#pragma unroll
+        for (int k = 0; k <= j; ++k) a += W[i][k] * A[lidx(PO + j, PO + k)];
+        Cm[i][j] = a;
+        V[i][j] = (i == j) ? 1.0 : 0.0;
+      }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < i; ++j) Cm[i][j] = Cm[j][i] = 0.5 * (Cm[i][j] + Cm[j][i]);
+    // cyclic Jacobi sweeps (quadratic convergence; a 4x4 needs a handful)
+    for (int sweep = 0; sweep < 16; ++sweep) {
+      double off = 0.0, dia = 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        dia += Cm[i][i] * Cm[i][i];
+#pragma unroll
+        for (int j = i + 1; j < 4; ++j) off += Cm[i][j] * Cm[i][j];
+      }
+      if (!(off > 1e-34 * dia)) break;
+      jacobi_rot<0, 1>(Cm, V); jacobi_rot<0, 2>(Cm, V); jacobi_rot<0, 3>(Cm, V);
+      jacobi_rot<1, 2>(Cm, V); jacobi_rot<1, 3>(Cm, V); jacobi_rot<2, 3>(Cm, V);
+    }
+    double out[NE];
+    // A0 = M_top^T M_top on the top-left 4x4 block (packed lower)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) {
+        double a = 0.0;
+#pragma unroll
+        for (int r = i; r < 4; ++r) a += A[lidx(r, i)] * A[lidx(r, j)];
+        out[NE_A0 + lidx(i, j)] = a;
+      }
+    // Y = M_bot^T V
+#pragma unroll
+    for (int i = 0; i < NC; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        double a = 0.0;
+#pragma unroll
+        for (int r = (i > PO ? i : PO); r < NC; ++r) a += A[lidx(r, i)] * V[r - PO][k];
+        out[NE_Y + i * 4 + k] = a;
+      }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[NE_L + k] = Cm[k][k] > 0.0 ? Cm[k][k] : 0.0;
+#pragma unroll
+    for (int q = 0; q < NE; ++q) {
+      if (E64) E64[size_t(q) * S + g] = out[q];
+      if (E32) E32[size_t(q) * S + g] = float(out[q]);
+    }
+  }
+}
+
+int launch_keig(const DevProblem &p, void *E32, void *E64, int *err_flag, void *stream) {
+  if (p.S == 0) return 0;
+  const int threads = 128;
+  int blocks = (p.S + threads - 1) / threads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  const bool samples = p.inner == 0 && (p.M_box > 0 || p.M_ball > 0 || p.M_vn > 0);
+  if (samples)
+    keig_kernel<true><<<blocks, threads, 0, (cudaStream_t)stream>>>(p, (float *)E32, (double *)E64, err_flag);
+  else
+    keig_kernel<false><<<blocks, threads, 0, (cudaStream_t)stream>>>(p, (float *)E32, (double *)E64, err_flag);
+  return (int)cudaGetLastError();
+}
+
+__global__ void fill_kernel(double *x, int n, double v) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) x[q] = v;
+}
+
+int launch_fill(double *x, int n, double v, void *stream) {
+  if (n <= 0) return 0;
+  int blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  fill_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(x, n, v);
+  return (int)cudaGetLastError();
 }
 
 int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_flag, void *stream) {

@@ -94,6 +94,7 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
     return TOP_E_INVAL;
   if (pb->mode != TOP_PIN && pb->mode != TOP_FREE) return TOP_E_INVAL;
   if (pb->inner != TOP_CLOSED_FORM || pb->M_gen != 0) return TOP_E_NOTSUP;
+  if (pb->adaptive_rho != 0) return TOP_E_NOTSUP;  // the fixed scratch has no room for the adaptive-rho data
   if (pb->M_box < 0 || pb->M_ball < 0 || pb->M_vn < 0) return TOP_E_INVAL;
   if ((pb->M_box && !pb->vbox) || (pb->M_ball && (!pb->ball_c || !pb->ball_r)) || (pb->M_vn && !pb->vnorm))
     return TOP_E_INVAL;
@@ -164,7 +165,7 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
   dp.M_vn = pb->M_vn; dp.vnorm = pb->vnorm;
   DevResult dr{};
   dr.coeffs = res->coeffs; dr.cost = res->cost; dr.r_primal = res->r_primal; dr.r_dual = res->r_dual;
-  dr.history = res->history; dr.iters = res->iters; dr.status = res->status;
+  dr.history = res->history; dr.iters = res->iters; dr.status = res->status; dr.rho = res->rho;
 
   if (cudaMemsetAsync(d_err, 0, sizeof(int), st) != cudaSuccess) return TOP_E_CUDA;
   if (cudaMemsetAsync(dr.cost, 0, sizeof(double) * B, st) != cudaSuccess ||

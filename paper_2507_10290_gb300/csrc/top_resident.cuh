@@ -39,7 +39,7 @@
 
 namespace top {
 
-template <class R, int F>
+template <class R, int F, bool ADAPT>
 __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) {
   constexpr bool BOX = (F & FAM_BOX) != 0;
   constexpr bool BALL = (F & FAM_BALL) != 0;
@@ -72,8 +72,12 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
   int *soff = (int *)(smem + L.off);
   int *sdone = (int *)(smem + L.done);
   int *stid = (int *)(smem + L.tid);
+  int *sflag = (int *)(smem + L.flag);
+  double *srho = (double *)(smem + L.rho);  // per-trajectory rho (Eq. 22)
+  double *sfac = (double *)(smem + L.fac);  // rho_old / rho_new of the last update
 
-  const R rho = R(p.rho);
+  const R rho0 = R(p.rho);
+  constexpr bool adapt = ADAPT;  // residual balancing of rho (Eq. 22); A.E is non-null
   const int K = p.max_iters;
   const bool pin = (p.mode == 0);
 
@@ -88,7 +92,8 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
     }
     soff[pk.ntraj] = acc;
   }
-  for (int t = l; t < ntp; t += C) { tr_rp[t] = 0.0; tr_rd[t] = 0.0; }
+  for (int t = l; t < ntp; t += C) { tr_rp[t] = 0.0; tr_rd[t] = 0.0; srho[t] = p.rho; sfac[t] = 1.0; }
+  if (l == 0) *sflag = 0;
   for (int q = l; q < NJ * J; q += C) { sdz[q] = R(0); sp[q] = R(0); sm[q] = R(0); }
   for (int q = l; q < 3 * J; q += C) szP[q] = R(0);
   if (BOX) for (int q = l; q < 6 * Mb * C; q += C) sybox[q] = R(0);
@@ -178,8 +183,9 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
   const int cev = p.check_every > 0 ? p.check_every : 1;
   const bool periodic = p.eps > 0.0 || res.history != nullptr;
   for (int k = 0; k < K; ++k) {
-    const bool check = (k == K - 1) || (periodic && ((k + 1) % cev == 0));
+    const bool check = adapt || (k == K - 1) || (periodic && ((k + 1) % cev == 0));
     const bool act = valid && !sdone[tb];
+    const R rho = adapt ? R(srho[tb]) : rho0;
     R eE[AX][ND];
     R eSv[AX][ND];
     if (act) {
@@ -252,7 +258,8 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
     }
     __syncthreads();
     if (check) {
-      // ---- 4. dual residual (Eq. 20), reductions, stopping rule (Eq. 21) ----
+      // ---- 4. dual residual (Eq. 20), reductions, stopping rule (Eq. 21), rho update (Eq. 22) ----
+      if (adapt && l == 0) *sflag = 0;  // every reader of the last flag has passed a barrier since
       double rd2 = 0.0;
       if (act) {
         R Tk[NC];
@@ -300,10 +307,50 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
             sdone[t] = 1;
             res.iters[bb] = k + 1;
             res.status[bb] = st;
+          } else if (adapt) {
+            const double ro = srho[t], rn = next_rho(p, ro, rp, rd);
+            sfac[t] = ro / rn;
+            if (rn != ro) {
+              srho[t] = rn;
+              *sflag = 1;
+            }
           }
         }
       }
       __syncthreads();
+      // ---- 5. after a change of rho: keep the unscaled duals, new local inverse ----
+      if (adapt && *sflag && k + 1 < K) {
+        if (valid && !sdone[tb] && sfac[tb] != 1.0) {
+          const R f = R(sfac[tb]);
+#pragma unroll
+          for (int a = 0; a < AX; ++a)
+#pragma unroll
+            for (int r = 0; r < ND; ++r) {
+              const int row = a * ND + r;
+              if (!last) {  // p = z + u_start-side, m = z - u_end-side, z fixed for pinned rows
+                const R zc = (pin && r == 0) ? szP[jE * 3 + a] : R(0.5) * (pE[row] + mE[row]);
+                pE[row] = zc + f * (pE[row] - zc);
+                mE[row] = zc + f * (mE[row] - zc);
+              } else if (r < PO) {  // p holds the fixed end value
+                mE[row] = pE[row] + f * (mE[row] - pE[row]);
+              }
+              if (first && r < PO) pS[row] = mS[row] + f * (pS[row] - mS[row]);  // m holds the start value
+            }
+          if (BOX)
+            for (int q = 0; q < 6 * Mb; ++q) {
+              const R y = sybox[q * C + l];
+              if (y > R(0)) sybox[q * C + l] = f * y;  // v = max(0, y) scales, s = max(0, -y) stays
+            }
+          if (BALL)
+            for (int j = 0; j < Mq; ++j) rescale_projected(sqball + j * 3 * C + l, C, sc.bo, sc.brad, f);
+          if (VN) {
+            const R zero3[3] = {R(0), R(0), R(0)};
+            for (int j = 0; j < Mv; ++j) rescale_projected(sqvn + j * 3 * C + l, C, zero3, sc.vnorm, f);
+          }
+          g_from_eig((const R *)A.E, (size_t)p.S, (size_t)g, srho[tb], sc.G);
+        }
+        __syncthreads();
+      }
     }
   }
 
@@ -334,6 +381,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
         res.cost[bb] = a1;
         res.r_primal[bb] = tr_rp[t];
         res.r_dual[bb] = tr_rd[t];
+        if (res.rho) res.rho[bb] = srho[t];
         const bool empty = soff[t + 1] == soff[t];
         if (empty) {
           res.iters[bb] = 0;
@@ -350,9 +398,10 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
 template <class R>
 int launch_resident_t(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
+  const bool adapt = a.p.adaptive != 0 && a.E != nullptr;
 #define TOP_RES_CASE(FV)                                                                               \
   case FV: {                                                                                           \
-    auto kern = resident_kernel<R, FV>;                                                                \
+    auto kern = adapt ? resident_kernel<R, FV, true> : resident_kernel<R, FV, false>;                  \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return (int)e;                                                               \
     kern<<<nblocks, C, smem, st>>>(a);                                                                 \

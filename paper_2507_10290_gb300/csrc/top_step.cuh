@@ -195,6 +195,53 @@ __device__ __forceinline__ double segment_cost(const R (&ch)[AX][NC], double t7)
 
 __device__ __forceinline__ bool finite_d(double x) { return x == x && x - x == 0.0; }
 
+// The next rho of residual balancing (Eq. 22), in FP64 on the FP64 residual norms.
+__device__ __forceinline__ double next_rho(const DevProblem &p, double rho, double rp, double rd) {
+  if (rp > p.rho_mu * rd) return rho * p.rho_incr;
+  if (rd > p.rho_mu * rp) return rho / p.rho_decr;
+  return rho;
+}
+
+// The local-matrix inverse for a new rho from the segment's adaptive-rho data
+// (layout NE_* of top_internal.h): G = A0 / rho + sum_k y_k y_k^T / (lambda_k + rho).
+// Every term is a positive multiple of a rank-one square, so the sum has no
+// cancellation whatever rho is.
+template <class R>
+__device__ __forceinline__ void g_from_eig(const R *E, size_t S, size_t g, double rho, R (&G)[NG]) {
+  const R ir = R(1.0 / rho);
+#pragma unroll
+  for (int r = 0; r < NC; ++r)
+#pragma unroll
+    for (int c = r; c < NC; ++c)
+      G[gidx(r, c)] = (c < PO) ? E[(size_t)(NE_A0 + c * (c + 1) / 2 + r) * S + g] * ir : R(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const R wk = R(1.0 / (double(E[(size_t)(NE_L + k) * S + g]) + rho));
+    R y[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) y[i] = E[(size_t)(NE_Y + i * 4 + k) * S + g];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) {
+      const R wy = wk * y[r];
+#pragma unroll
+      for (int c = r; c < NC; ++c) G[gidx(r, c)] += wy * y[c];
+    }
+  }
+}
+
+// q' = phi + f (q - phi), phi = the projection of q: the compressed ball /
+// velocity-norm state with its scaled dual w = q - phi multiplied by f and
+// the projection unchanged (the ray from phi through q keeps its projection).
+template <class R>
+__device__ __forceinline__ void rescale_projected(R *q, int stride, const R (&o)[3], R rad, R f) {
+  R qv[3], ph[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) qv[a] = q[a * stride];
+  project_ball(qv, o, rad, ph);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) q[a * stride] = ph[a] + f * (qv[a] - ph[a]);
+}
+
 // ---------------------------------------------------------------------------
 // Numerical local step for general convex constraints (Sec. III-C.3, Eq.
 // 15-17): per segment, minimise

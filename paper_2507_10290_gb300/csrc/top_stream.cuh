@@ -79,7 +79,13 @@ __global__ void stream_init(const StreamArgs A) {
       for (int q = 0; q < 2 * p.M_gen; ++q) ((R *)A.ygen)[(size_t)q * A.S + g] = R(0);
       if (A.inner_iters) A.inner_iters[g] = 0;
     }
-    if (first) { A.done[t] = 0; A.tr_rp[t] = 0.0; A.tr_rd[t] = 0.0; }
+    if (first) {
+      A.done[t] = 0;
+      A.tr_rp[t] = 0.0;
+      A.tr_rd[t] = 0.0;
+      A.rho_t[t] = p.rho;
+      A.fac_t[t] = 1.0;
+    }
   }
 }
 
@@ -104,12 +110,12 @@ __global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
   const R *z = (const R *)A.z, *uL = (const R *)A.uL, *uRp = (const R *)A.uRp, *uR0 = (const R *)A.uR0;
   const R *Gp = (const R *)A.G;
   R *eS = (R *)A.eS, *eE = (R *)A.eE, *chg = (R *)A.ch;
-  const R rho = R(p.rho);
   const bool pin = p.mode == 0;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
     int t, b, i, N, g;
     stream_locate(A, x, t, b, i, N, g);
     if (A.done[t]) continue;
+    const R rho = R(A.rho_t[t]);
     const bool first = i == 0, last = i == N - 1;
     const int jS = g + b, jE = g + b + 1;
     SegConst<R> sc;
@@ -219,11 +225,11 @@ template <class R>
 __global__ void __launch_bounds__(256) stream_dual(const StreamArgs A) {
   const DevProblem &p = A.p;
   const R *dz = (const R *)A.dz;
-  const R rho = R(p.rho);
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
     int t, b, i, N, g;
     stream_locate(A, x, t, b, i, N, g);
     if (A.done[t]) continue;
+    const R rho = R(A.rho_t[t]);
     const bool first = i == 0, last = i == N - 1;
     const int jS = g + b, jE = g + b + 1;
     R s[NC], Tk[NC];
@@ -281,7 +287,60 @@ __global__ void __launch_bounds__(256) stream_reduce(const StreamArgs A, int k) 
       A.done[t] = 1;
       A.r.iters[b] = k + 1;
       A.r.status[b] = st;
+    } else if (A.p.adaptive && A.E) {  // UpdateRho (Eq. 22)
+      const double ro = A.rho_t[t], rn = next_rho(A.p, ro, rp, rd);
+      A.fac_t[t] = ro / rn;
+      A.rho_t[t] = rn;
     }
+  }
+}
+
+// after a change of rho (adaptive rho): every scaled dual times rho_old / rho_new
+// (the unscaled duals are kept) and the segment's local inverse for the new rho
+template <class R, int F>
+__global__ void __launch_bounds__(256) stream_rescale(const StreamArgs A) {
+  constexpr bool BOX = (F & FAM_BOX) != 0, BALL = (F & FAM_BALL) != 0, VN = (F & FAM_VN) != 0;
+  const DevProblem &p = A.p;
+  R *uL = (R *)A.uL, *uRp = (R *)A.uRp, *uR0 = (R *)A.uR0, *Gw = (R *)A.G;
+  const bool pin = p.mode == 0;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
+    int t, b, i, N, g;
+    stream_locate(A, x, t, b, i, N, g);
+    if (A.done[t] || A.fac_t[t] == 1.0) continue;
+    const R f = R(A.fac_t[t]);
+    const bool first = i == 0, last = i == N - 1;
+    const int jS = g + b, jE = g + b + 1;
+    (void)jS;
+#pragma unroll
+    for (int a = 0; a < AX; ++a)
+#pragma unroll
+      for (int r = 0; r < ND; ++r) {
+        const size_t row = (size_t)(a * ND + r) * A.Jn;
+        if (!last || r < PO) uL[row + jE] *= f;
+        if (!last && pin && r == 0) uRp[(size_t)a * A.Jn + jE] *= f;
+        if (first && r < PO) uR0[(size_t)(a * PO + r) * p.B + b] *= f;
+      }
+    if (BOX) {
+      R *yb = (R *)A.ybox;
+      for (int q = 0; q < 6 * p.M_box; ++q) {
+        const R y = yb[(size_t)q * A.S + g];
+        if (y > R(0)) yb[(size_t)q * A.S + g] = f * y;
+      }
+    }
+    if (BALL) {
+      const R o[3] = {R(p.ball_c[(size_t)g * 3]), R(p.ball_c[(size_t)g * 3 + 1]), R(p.ball_c[(size_t)g * 3 + 2])};
+      for (int j = 0; j < p.M_ball; ++j)
+        rescale_projected((R *)A.qball + (size_t)j * 3 * A.S + g, A.S, o, R(p.ball_r[g]), f);
+    }
+    if (VN) {
+      const R zero3[3] = {R(0), R(0), R(0)};
+      for (int j = 0; j < p.M_vn; ++j)
+        rescale_projected((R *)A.qvn + (size_t)j * 3 * A.S + g, A.S, zero3, R(p.vnorm[b]), f);
+    }
+    R G[NG];
+    g_from_eig((const R *)A.E, (size_t)A.S, (size_t)g, A.rho_t[t], G);
+#pragma unroll
+    for (int q = 0; q < NG; ++q) Gw[(size_t)q * A.S + g] = G[q];
   }
 }
 
@@ -327,6 +386,7 @@ __global__ void __launch_bounds__(256) stream_finish(const StreamArgs A, int K) 
     A.r.cost[b] = s1[0];
     A.r.r_primal[b] = A.tr_rp[t];
     A.r.r_dual[b] = A.tr_rd[t];
+    if (A.r.rho) A.r.rho[b] = A.rho_t[t];
     if (!A.done[t]) {
       A.r.iters[b] = K;
       A.r.status[b] = 1;
@@ -348,8 +408,10 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
   const size_t tab_bytes = sizeof(R) * 8 * (size_t)(Mb + Mq + Mv + 2 * Mg);
   void (*init)(const StreamArgs) = nullptr;
   void (*local)(const StreamArgs, int) = nullptr;
+  void (*rescale)(const StreamArgs) = nullptr;
   switch (fam) {
-#define TOP_ST_CASE(FV) case FV: init = stream_init<R, FV>; local = stream_local<R, FV>; break;
+#define TOP_ST_CASE(FV) \
+  case FV: init = stream_init<R, FV>; local = stream_local<R, FV>; rescale = stream_rescale<R, FV>; break;
     TOP_ST_CASE(0) TOP_ST_CASE(1) TOP_ST_CASE(2) TOP_ST_CASE(3)
     TOP_ST_CASE(4) TOP_ST_CASE(5) TOP_ST_CASE(6) TOP_ST_CASE(7) TOP_ST_CASE(8)
 #undef TOP_ST_CASE
@@ -358,14 +420,16 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
   init<<<blocks, threads, 0, st>>>(A);
   const int K = p.max_iters;
   const int cev = p.check_every > 0 ? p.check_every : 1;
+  const bool adapt = p.adaptive && A.E;
   for (int k = 0; k < K; ++k) {
-    const bool check = (k == K - 1) || ((p.eps > 0.0 || A.r.history) && ((k + 1) % cev == 0));
+    const bool check = adapt || (k == K - 1) || ((p.eps > 0.0 || A.r.history) && ((k + 1) % cev == 0));
     local<<<blocks, threads, tab_bytes, st>>>(A, k);
     stream_junction<R><<<blocks, threads, 0, st>>>(A, check ? 1 : 0);
     if (check) {
       stream_dual<R><<<blocks, threads, 0, st>>>(A);
       stream_reduce<R><<<A.nl, 256, 0, st>>>(A, k);
     }
+    if (adapt && k + 1 < K) rescale<<<blocks, threads, 0, st>>>(A);
   }
   stream_output<R><<<blocks, threads, 0, st>>>(A);
   stream_finish<R><<<A.nl, 256, 0, st>>>(A, K);

@@ -70,13 +70,15 @@ class top_problem(C.Structure):
                 ("M_ball", C.c_int32), ("ball_c", C.c_void_p), ("ball_r", C.c_void_p),
                 ("M_vn", C.c_int32), ("vnorm", C.c_void_p),
                 ("M_gen", C.c_int32), ("gen_vmax", C.c_void_p), ("gen_amax", C.c_void_p),
-                ("lbfgs_mem", C.c_int32), ("lbfgs_max_iters", C.c_int32), ("lbfgs_tol", C.c_double)]
+                ("lbfgs_mem", C.c_int32), ("lbfgs_max_iters", C.c_int32), ("lbfgs_tol", C.c_double),
+                ("adaptive_rho", C.c_int32), ("rho_mu", C.c_double), ("rho_tau_incr", C.c_double),
+                ("rho_tau_decr", C.c_double)]
 
 
 class top_result(C.Structure):
     _fields_ = [("coeffs", C.c_void_p), ("cost", C.c_void_p), ("r_primal", C.c_void_p),
                 ("r_dual", C.c_void_p), ("iters", C.c_void_p), ("status", C.c_void_p),
-                ("history", C.c_void_p)]
+                ("history", C.c_void_p), ("rho", C.c_void_p)]
 
 
 _lib.top_create.argtypes = [C.POINTER(top_config), C.POINTER(C.c_void_p)]
@@ -235,6 +237,10 @@ class Solver:
         pb.lbfgs_mem = int(getattr(w, "lbfgs_mem", 0) or 0)
         pb.lbfgs_max_iters = int(getattr(w, "lbfgs_max_iters", 0) or 0)
         pb.lbfgs_tol = float(getattr(w, "lbfgs_tol", 0.0) or 0.0)
+        pb.adaptive_rho = int(bool(getattr(w, "adaptive_rho", False)))
+        pb.rho_mu = float(getattr(w, "rho_mu", 0.0) or 0.0)
+        pb.rho_tau_incr = float(getattr(w, "rho_tau_incr", 0.0) or 0.0)
+        pb.rho_tau_decr = float(getattr(w, "rho_tau_decr", 0.0) or 0.0)
         return pb
 
     def alloc_result(self, B: int, S: int, max_iters: int = 0, history: bool = False, device="cuda"):
@@ -246,6 +252,7 @@ class Solver:
             "r_dual": torch.empty(B, dtype=torch.float64, device=device),
             "iters": torch.empty(B, dtype=torch.int32, device=device),
             "status": torch.empty(B, dtype=torch.int32, device=device),
+            "rho": torch.empty(B, dtype=torch.float64, device=device),
         }
         if history:
             out["history"] = torch.full((max(1, max_iters), B, 2), float("nan"), dtype=torch.float64, device=device)
@@ -254,7 +261,7 @@ class Solver:
     @staticmethod
     def result_struct(out):
         r = top_result()
-        for k in ("coeffs", "cost", "r_primal", "r_dual", "iters", "status", "history"):
+        for k in ("coeffs", "cost", "r_primal", "r_dual", "iters", "status", "history", "rho"):
             x = out.get(k)
             setattr(r, k, None if x is None else (x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()))
         return r
@@ -314,7 +321,8 @@ class Solver:
                 arrays[k] = None if x is None else np.ascontiguousarray(x, dtype=np.float64)
         if out is None:
             out = {"coeffs": np.empty((S, 3, 8)), "cost": np.empty(B), "r_primal": np.empty(B),
-                   "r_dual": np.empty(B), "iters": np.empty(B, np.int32), "status": np.empty(B, np.int32)}
+                   "r_dual": np.empty(B), "iters": np.empty(B, np.int32), "status": np.empty(B, np.int32),
+                   "rho": np.empty(B)}
             if history:
                 out["history"] = np.full((max(1, K), B, 2), np.nan)
         pb = self.make_problem(w, arrays, TOP_MEM_HOST, max_iters=K, eps=eps, check_every=check_every)
