@@ -212,6 +212,7 @@ def run_ours(args):
     solver = top.Solver(max_batch=B, max_segments=S, precision=args.precision, max_samples=0)
     tensors = solver.device_inputs(w)
     out = solver.alloc_result(B, S, iters)
+    out.pop("rho")  # fixed rho: the step does not ask for the final rho (no fill launch)
     stream = torch.cuda.current_stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -331,34 +332,45 @@ def _timed_solve(solver, w, tensors, out, **kw):
     return e0.elapsed_time(e1)
 
 
-def time_to_tolerance(top, B, rank, world, eps=1e-4, cap=30000, fp64_B=256):
-    """Trajectories per second that meet the stopping rule of Eq. 21 at eps.
+def time_to_tolerance(top, B, rank, world, eps=1e-4, cap=30000, fp64_B=256, pin_eps=0.05):
+    """Trajectories per second that meet the stopping rule of Eq. 21.
 
     PIN waypoints with the fixed rho = 1 do not reach even the paper's loose
     eps = 0.05 in 2e5 iterations (oracle), so the batch is solved with FREE
-    waypoints (otherwise the same recipe), which converges.  FP32 on the
-    whole batch; FP32 and FP64 side by side on its first `fp64_B` trajectories.
+    waypoints (otherwise the same recipe) at `eps`: FP32 on the whole batch,
+    FP32 and FP64 side by side on its first `fp64_B` trajectories, and FP32
+    with residual balancing of rho (Eq. 22).  The PIN batch is then solved at
+    `pin_eps` with fixed and with balanced rho (FP32, whole batch).
     """
-    res = {"workload": f"batch recipe with FREE waypoints, eps={eps} (E = N_b eps), cap {cap} iterations, "
-                       "residuals every iteration", "eps": eps, "cap": cap}
-    for tag, BB, precs in (("full", B, ("fp32",)), ("subset", min(fp64_B, B), ("fp32", "fp64"))):
-        w = W.batch(seed=rank, B=BB).with_(mode="free", eps=eps, max_iters=cap)
+    res = {"workload": f"batch recipe, FREE waypoints at eps={eps} and PIN at eps={pin_eps} "
+                       f"(E = N_b eps), cap {cap} iterations, residuals every iteration",
+           "eps": eps, "pin_eps": pin_eps, "cap": cap}
+    runs = (("full", B, ("fp32",), "free", eps, False), ("subset", min(fp64_B, B), ("fp32", "fp64"), "free", eps, False),
+            ("full_adaptive", B, ("fp32",), "free", eps, True), ("pin_full", B, ("fp32",), "pin", pin_eps, False),
+            ("pin_full_adaptive", B, ("fp32",), "pin", pin_eps, True))
+    for tag, BB, precs, mode, e, adapt in runs:
+        w = W.batch(seed=rank, B=BB).with_(mode=mode, eps=e, max_iters=cap, adaptive_rho=adapt)
         Nb = np.diff(w.seg_offset)
         for prec in precs:
             s = top.Solver(max_batch=BB, max_segments=w.S, precision=prec, max_samples=0)
             tensors = s.device_inputs(w)
             out = s.alloc_result(BB, w.S, cap)
-            s.solve(w, tensors=tensors, out=out, max_iters=5, eps=eps)  # warm-up
+            s.solve(w, tensors=tensors, out=out, max_iters=5, eps=e)  # warm-up
             ms = _timed_solve(s, w, tensors, out)
             it = out["iters"].cpu().numpy()
             st = out["status"].cpu().numpy()
             conv = int((st == 0).sum())
-            res[f"{tag}_{prec}"] = {
+            entry = {
                 "trajectories": BB, "segments": int(w.S), "ms": ms, "converged": conv,
                 "trajectories_per_s": world * conv / (ms / 1000.0),
                 "mean_iterations": float(it.mean()), "max_iterations": int(it.max()),
                 "segment_iterations_per_s": world * float(np.sum(Nb * it)) / (ms / 1000.0),
             }
+            if adapt:
+                rho = out["rho"].cpu().numpy()
+                entry["rho_final"] = {"min": float(rho.min()), "median": float(np.median(rho)),
+                                      "max": float(rho.max())}
+            res[f"{tag}_{prec}"] = entry
             s.close()
     return res
 
@@ -401,6 +413,8 @@ def run_suite(args):
                      "segment_iterations_per_s": w.S * w.max_iters / (float(np.median(ms)) / 1000),
                      "coeff_rel_err_vs_oracle": scaled_err(g["coeffs"], o["coeffs"], w.durations),
                      "cost_rel_err_vs_oracle": float(np.max(np.abs(g["cost"] - o["cost"]) / np.abs(o["cost"])))}
+            if getattr(w, "adaptive_rho", False):
+                entry["final_rho_equal_to_oracle"] = float(np.mean(g["rho"] == o["rho_final"]))
             if tol_eps:
                 wt = w.with_(eps=tol_eps, max_iters=tol_cap)
                 out2 = s.alloc_result(w.B, w.S, tol_cap)
@@ -418,6 +432,8 @@ def run_suite(args):
     gpu_case("corridor", W.corridor(), tol_eps=1e-4)
     sub = W.batch().subset(list(range(64)))
     gpu_case("batch (64-trajectory subset for the oracle)", sub, precs=("fp32", "fp64"))
+    gpu_case("batch, residual balancing of rho (Eq. 22), 64-trajectory subset", sub.with_(adaptive_rho=True),
+             precs=("fp32", "fp64"))
     gpu_case("general (N=1000, numerical step)", W.general(N=1000), tol_eps=1e-4)
 
     # adjoint through 100 iterations on the 256 x 256 batch

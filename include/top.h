@@ -75,7 +75,7 @@ typedef struct top_handle top_handle;
 
 /* Fixed at creation: capacities of the device workspace and the precision. */
 typedef struct top_config {
-  int32_t precision;      /* TOP_FP32: FP32 iteration with FP64 KKT inverse and FP64 reductions;
+  int32_t precision;      /* TOP_FP32: FP32 iteration with FP64 KKT inverse and FP64 cost;
                              TOP_FP64: everything in FP64 */
   int32_t max_batch;      /* largest B a call may pass */
   int32_t max_segments;   /* largest total segment count S a call may pass */

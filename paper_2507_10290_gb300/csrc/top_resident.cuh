@@ -24,8 +24,12 @@
 //   2. publish the start derivatives; barrier
 //   3. junction i+1 (owned by thread i): consensus update, primal-residual
 //      share (Eq. 19) on check iterations; barrier
-//   4. on check iterations: dual residual (Eq. 20), per-trajectory FP64
-//      reductions in a fixed order, stopping test (Eq. 21)
+//   4. on check iterations: dual residual (Eq. 20), per-trajectory
+//      reductions in a fixed order, stopping test (Eq. 21), and with adaptive
+//      rho the update of Eq. 22; barrier
+//   5. after a change of rho (adaptive rho only): the thread's own junction
+//      targets, slack duals and projection states rescaled, its local inverse
+//      rebuilt for the new rho; barrier
 // Shared arrays are slot-major (21 values per slot): every access of a
 // thread is a constant offset from one base, and consecutive threads are 21
 // words apart (no bank conflicts).
@@ -54,8 +58,9 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
   const int J = C + ntp;
   const int Mb = BOX ? p.M_box : 0, Mq = BALL ? p.M_ball : 0, Mv = VN ? p.M_vn : 0;
   const ResLayout L = res_layout(C, ntp, Mb, Mq, Mv, (int)sizeof(R));
-  double *red_rp = (double *)(smem + L.red_rp);
-  double *red_rd = (double *)(smem + L.red_rd);
+  double *red_rp = (double *)(smem + L.red_rp);  // FP64 cost shares (epilogue)
+  R *sh_rp = (R *)(smem + L.red_rp);              // residual shares (check iterations)
+  R *sh_rd = (R *)(smem + L.red_rd);
   double *tr_rp = (double *)(smem + L.tr_rp);
   double *tr_rd = (double *)(smem + L.tr_rd);
   R *sp = (R *)(smem + L.p);
@@ -182,10 +187,10 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
 
   const int cev = p.check_every > 0 ? p.check_every : 1;
   const bool periodic = p.eps > 0.0 || res.history != nullptr;
+  R rho = rho0;  // this trajectory's rho (changes only with adaptive rho, step 5)
   for (int k = 0; k < K; ++k) {
     const bool check = adapt || (k == K - 1) || (periodic && ((k + 1) % cev == 0));
     const bool act = valid && !sdone[tb];
-    const R rho = adapt ? R(srho[tb]) : rho0;
     R eE[AX][ND];
     R eSv[AX][ND];
     if (act) {
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
     if (check) {
       // ---- 4. dual residual (Eq. 20), reductions, stopping rule (Eq. 21), rho update (Eq. 22) ----
       if (adapt && l == 0) *sflag = 0;  // every reader of the last flag has passed a barrier since
-      double rd2 = 0.0;
+      R rd2 = R(0);
       if (act) {
         R Tk[NC];
         Tk[0] = R(1);
@@ -277,21 +282,21 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
           rd2 += dual_residual_sq(dS, dE, rho, Tk);
         }
       }
-      red_rp[l] = double(rp2);
-      red_rd[l] = rd2;
+      sh_rp[l] = rp2;
+      sh_rd[l] = rd2;
       __syncthreads();
       const int warp = l >> 5, lane = l & 31, nw = C >> 5;
       for (int t = warp; t < pk.ntraj; t += nw) {
         if (sdone[t]) continue;
-        double a1 = 0.0, a2 = 0.0;
-        for (int x = soff[t] + lane; x < soff[t + 1]; x += 32) { a1 += red_rp[x]; a2 += red_rd[x]; }
+        R a1 = R(0), a2 = R(0);  // fixed order: lane-strided, then a butterfly
+        for (int x = soff[t] + lane; x < soff[t + 1]; x += 32) { a1 += sh_rp[x]; a2 += sh_rd[x]; }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           a1 += __shfl_xor_sync(0xffffffffu, a1, o);
           a2 += __shfl_xor_sync(0xffffffffu, a2, o);
         }
         if (lane == 0) {
-          const double rp = sqrt(a1), rd = sqrt(a2);
+          const double rp = sqrt(double(a1)), rd = sqrt(double(a2));
           tr_rp[t] = rp;
           tr_rd[t] = rd;
           const int bb = stid[t];
@@ -347,7 +352,11 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) 
             const R zero3[3] = {R(0), R(0), R(0)};
             for (int j = 0; j < Mv; ++j) rescale_projected(sqvn + j * 3 * C + l, C, zero3, sc.vnorm, f);
           }
-          g_from_eig((const R *)A.E, (size_t)p.S, (size_t)g, srho[tb], sc.G);
+          R *Gw = (R *)A.G;  // this segment's column of the precomputed inverses
+          g_from_eig_store((const R *)A.E, (size_t)p.S, (size_t)g, srho[tb], Gw);
+#pragma unroll
+          for (int q = 0; q < NG; ++q) sc.G[q] = Gw[(size_t)q * p.S + g];
+          rho = R(srho[tb]);
         }
         __syncthreads();
       }

@@ -163,17 +163,19 @@ __device__ __forceinline__ void local_step(const SegConst<R> &sc, const R (&wS)[
 }
 
 // rho M^T (s .* dz) for one axis, mapped back to the paper's coefficients
-// (multiplied by T^k), squared and summed: one segment's share of ||r_d||^2 (Eq. 20)
+// (multiplied by T^k), squared and summed: one segment's share of ||r_d||^2
+// (Eq. 20), in the iteration's precision (FP64 arithmetic runs at 1/64 of the
+// FP32 rate on this GPU, and the residual norms only steer the stopping test)
 template <class R>
-__device__ __forceinline__ double dual_residual_sq(const R (&dS)[ND], const R (&dE)[ND], R rho, const R (&Tk)[NC]) {
+__device__ __forceinline__ R dual_residual_sq(const R (&dS)[ND], const R (&dE)[ND], R rho, const R (&Tk)[NC]) {
   R x[NC];
 #pragma unroll
   for (int q = 0; q < NC; ++q) x[q] = R(0);
   consensus_rhs(dS, dE, rho, x);
-  double acc = 0.0;
+  R acc = R(0);
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
-    const double v = double(x[q]) * double(Tk[q]);
+    const R v = x[q] * Tk[q];
     acc += v * v;
   }
   return acc;
@@ -205,26 +207,27 @@ __device__ __forceinline__ double next_rho(const DevProblem &p, double rho, doub
 // The local-matrix inverse for a new rho from the segment's adaptive-rho data
 // (layout NE_* of top_internal.h): G = A0 / rho + sum_k y_k y_k^T / (lambda_k + rho).
 // Every term is a positive multiple of a rank-one square, so the sum has no
-// cancellation whatever rho is.
+// cancellation whatever rho is.  Written one entry at a time to global memory
+// (Gw[q * S + g], the packed layout of the precompute): a dozen registers
+// instead of 36 accumulators, for kernels that keep G in registers and
+// reload it afterwards.
 template <class R>
-__device__ __forceinline__ void g_from_eig(const R *E, size_t S, size_t g, double rho, R (&G)[NG]) {
+__device__ __forceinline__ void g_from_eig_store(const R *E, size_t S, size_t g, double rho, R *Gw) {
   const R ir = R(1.0 / rho);
+  R w[4];
 #pragma unroll
-  for (int r = 0; r < NC; ++r)
+  for (int k = 0; k < 4; ++k) w[k] = R(1.0 / (double(E[(size_t)(NE_L + k) * S + g]) + rho));
+#pragma unroll 1
+  for (int r = 0; r < NC; ++r) {
+    R yr[4];
 #pragma unroll
-    for (int c = r; c < NC; ++c)
-      G[gidx(r, c)] = (c < PO) ? E[(size_t)(NE_A0 + c * (c + 1) / 2 + r) * S + g] * ir : R(0);
+    for (int k = 0; k < 4; ++k) yr[k] = w[k] * E[(size_t)(NE_Y + r * 4 + k) * S + g];
+#pragma unroll 1
+    for (int c = r; c < NC; ++c) {
+      R v = (c < PO) ? E[(size_t)(NE_A0 + c * (c + 1) / 2 + r) * S + g] * ir : R(0);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const R wk = R(1.0 / (double(E[(size_t)(NE_L + k) * S + g]) + rho));
-    R y[NC];
-#pragma unroll
-    for (int i = 0; i < NC; ++i) y[i] = E[(size_t)(NE_Y + i * 4 + k) * S + g];
-#pragma unroll
-    for (int r = 0; r < NC; ++r) {
-      const R wy = wk * y[r];
-#pragma unroll
-      for (int c = r; c < NC; ++c) G[gidx(r, c)] += wy * y[c];
+      for (int k = 0; k < 4; ++k) v += yr[k] * E[(size_t)(NE_Y + c * 4 + k) * S + g];
+      Gw[(size_t)(r * NC - (r * (r - 1)) / 2 + (c - r)) * S + g] = v;
     }
   }
 }

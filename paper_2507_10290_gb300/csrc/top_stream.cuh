@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(256) stream_dual(const StreamArgs A) {
     Tk[0] = R(1);
 #pragma unroll
     for (int q = 1; q < NC; ++q) Tk[q] = Tk[q - 1] * T;
-    double rd2 = 0.0;
+    R rd2 = R(0);
 #pragma unroll
     for (int a = 0; a < AX; ++a) {
       R dS[ND], dE[ND];
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(256) stream_dual(const StreamArgs A) {
       }
       rd2 += dual_residual_sq(dS, dE, rho, Tk);
     }
-    A.rd2[x] = rd2;
+    A.rd2[x] = double(rd2);
   }
 }
 
@@ -337,10 +337,7 @@ __global__ void __launch_bounds__(256) stream_rescale(const StreamArgs A) {
       for (int j = 0; j < p.M_vn; ++j)
         rescale_projected((R *)A.qvn + (size_t)j * 3 * A.S + g, A.S, zero3, R(p.vnorm[b]), f);
     }
-    R G[NG];
-    g_from_eig((const R *)A.E, (size_t)A.S, (size_t)g, A.rho_t[t], G);
-#pragma unroll
-    for (int q = 0; q < NG; ++q) Gw[(size_t)q * A.S + g] = G[q];
+    g_from_eig_store((const R *)A.E, (size_t)A.S, (size_t)g, A.rho_t[t], Gw);
   }
 }
 

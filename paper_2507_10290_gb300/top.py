@@ -163,7 +163,7 @@ def _ptr(t):
 class Solver:
     """One handle of the library, sized for a batch capacity.
 
-    precision: "fp32" (FP32 iteration, FP64 KKT inverses and reductions) or "fp64".
+    precision: "fp32" (FP32 iteration, FP64 KKT inverses and cost) or "fp64".
     """
 
     def __init__(self, max_batch: int, max_segments: int, precision: str = "fp32", max_samples: int = 16,

@@ -4,7 +4,7 @@ Both sides get the same seeded inputs and run the same number of CADMM
 iterations; coefficients are compared on the time-normalised scale
 c_k T^k (relative 2-norm over the batch), costs relative, iteration counts
 and statuses exactly.  Tolerances: 1e-9 for the FP64 path, 1e-4 for the
-FP32 path (FP32 state with FP64 KKT inverses and FP64 reductions).
+FP32 path (FP32 state with FP64 KKT inverses and FP64 cost).
 """
 import numpy as np
 import pytest
