@@ -428,15 +428,86 @@ def run_suite(args):
             line.update(extra(o))
         print(json.dumps(line), flush=True)
 
-    gpu_case("single_box", W.single_box(), tol_eps=1e-4)
-    gpu_case("corridor", W.corridor(), tol_eps=1e-4)
-    sub = W.batch().subset(list(range(64)))
-    gpu_case("batch (64-trajectory subset for the oracle)", sub, precs=("fp32", "fp64"))
-    gpu_case("batch, residual balancing of rho (Eq. 22), 64-trajectory subset", sub.with_(adaptive_rho=True),
-             precs=("fp32", "fp64"))
-    gpu_case("general (N=1000, numerical step)", W.general(N=1000), tol_eps=1e-4)
+    only = set(args.only.split(",")) if args.only else None
 
-    # adjoint through 100 iterations on the 256 x 256 batch
+    def want(name):
+        return only is None or name in only
+
+    if want("single_box"):
+        gpu_case("single_box", W.single_box(), tol_eps=1e-4)
+    if want("corridor"):
+        gpu_case("corridor", W.corridor(), tol_eps=1e-4)
+    sub = W.batch().subset(list(range(64)))
+    if want("batch"):
+        gpu_case("batch (64-trajectory subset for the oracle)", sub, precs=("fp32", "fp64"))
+    if want("adaptive"):
+        gpu_case("batch, residual balancing of rho (Eq. 22), 64-trajectory subset", sub.with_(adaptive_rho=True),
+                 precs=("fp32", "fp64"))
+    if want("general"):
+        gpu_case("general (N=1000, numerical step)", W.general(N=1000), tol_eps=1e-4)
+    if want("speed"):
+        speed_bound_comparison(top, oracle)
+    if want("grad"):
+        grad_line(top, oracle)
+    if want("general_full"):
+        general_full_line(top)
+
+
+def speed_bound_comparison(top, oracle):
+    """One speed bound through both constraint paths (the paper's Table III
+    comparison, on a synthetic instance): time per iteration, iterations and
+    time to eps, the cost and the largest sampled speed excess."""
+    def max_speed_excess(coeffs, durations, M, vmax):
+        k = np.arange(8)
+        worst = -np.inf
+        for i, Ti in enumerate(durations):
+            t = np.arange(1, M + 1)[:, None] * Ti / M
+            rows = np.where(k >= 1, k * t ** np.maximum(k - 1, 0), 0.0)  # [M][8]
+            v = rows @ coeffs[i].T                                         # [M][3]
+            worst = max(worst, float(np.linalg.norm(v, axis=1).max()) - vmax)
+        return worst
+
+    N, eps, cap = 256, 1e-4, 20000
+    line = {"suite": "speed bound: projection (Eq. 14, 18f-g) vs numerical step (Eq. 15-17)",
+            "workload": f"speed_limit N={N}, M=16, FREE, v_max = 1.6 x end-to-end mean speed; numerical "
+                        "step with the library's L-BFGS defaults (50 iterations, tol 1e-6 FP32 / 1e-12 FP64)",
+            "segments": N, "to_tolerance": {"eps": eps, "cap": cap}}
+    sols = {}
+    for inner in ("closed", "numeric"):
+        w = W.speed_limit(N=N, inner=inner)
+        vmax = float((w.vnorm if inner == "closed" else w.gen_vmax)[0])
+        t0 = time.perf_counter()
+        oracle.solve(w.with_(max_iters=20), lbfgs_tol=1e-12, lbfgs_max_iters=50)
+        entry = {"oracle_ms_per_iteration_1_core": 1000 * (time.perf_counter() - t0) / 20}
+        for prec in ("fp32", "fp64"):
+            s = top.Solver(max_batch=1, max_segments=N, precision=prec, max_samples=16)
+            tensors = s.device_inputs(w)
+            out = s.alloc_result(1, N, w.max_iters)
+            s.solve(w, tensors=tensors, out=out, max_iters=5)
+            ms = _timed_solve(s, w, tensors, out)
+            # the run to eps gets at most about a minute of GPU time
+            cap_here = int(min(cap, max(w.max_iters, 60e3 / (ms / w.max_iters))))
+            wt = w.with_(eps=eps, max_iters=cap_here)
+            out2 = s.alloc_result(1, N, cap_here)
+            mt = _timed_solve(s, wt, tensors, out2)
+            g = {k: v.cpu().numpy() for k, v in out2.items()}
+            entry[prec] = {"us_per_iteration": 1000 * ms / w.max_iters, "cap": cap_here,
+                           "to_tolerance_ms": mt, "iterations": int(g["iters"][0]), "status": int(g["status"][0]),
+                           "cost": float(g["cost"][0]),
+                           "max_speed_excess": max_speed_excess(g["coeffs"], w.durations, 16, vmax)}
+            sols[(inner, prec)] = g["coeffs"]
+            s.close()
+        line[inner] = entry
+    sc = W.speed_limit(N=N).durations[:, None, None] ** np.arange(8)
+    a, b = sols[("closed", "fp64")], sols[("numeric", "fp64")]
+    line["fp64_closed_vs_numeric_coeff_rel_diff"] = float(np.linalg.norm((a - b) * sc) / np.linalg.norm(a * sc))
+    print(json.dumps(line), flush=True)
+
+
+def grad_line(top, oracle):
+    """top_grad through 100 iterations on the 256 x 256 batch, and the oracle's
+    cost of one directional finite difference for comparison."""
+    import torch
     w = W.grad_batch()
     s = top.Solver(max_batch=w.B, max_segments=w.S, precision="fp32")
     tensors = s.device_inputs(w)
@@ -458,7 +529,10 @@ def run_suite(args):
                       "fp32": {"ms": gms, "segment_iterations_per_s_forward_and_reverse": w.S * 100 / (gms / 1000)},
                       "oracle_one_directional_fd_seconds_per_trajectory": fd_s}), flush=True)
 
-    # the full 1e5-segment general-bounds trajectory on the GPU only (oracle: the N=1000 line above)
+
+def general_full_line(top):
+    """The full 1e5-segment general-bounds trajectory on the GPU only (the
+    oracle's comparison is the N=1000 line)."""
     w = W.general()
     for prec in ("fp32",):
         s = top.Solver(max_batch=1, max_segments=w.S, precision=prec, max_samples=16)
@@ -516,6 +590,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tolerance", action="store_true", help="skip the time-to-tolerance measurement")
+    ap.add_argument("--only", default="", help="with --suite: comma-separated subset of single_box, corridor, "
+                    "batch, adaptive, general, speed, grad, general_full")
     ap.add_argument("--suite", action="store_true",
                     help="one JSON line per benchmark workload (single_box, corridor, batch, grad_batch, general)")
     ap.add_argument("--trajectories", type=int, default=4096,

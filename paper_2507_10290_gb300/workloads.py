@@ -238,6 +238,36 @@ def general(seed: int = 0, N: int = 100000, v_nom: float = 1.0) -> Workload:
     )
 
 
+def speed_limit(seed: int = 0, N: int = 256, M: int = 16, inner: str = "closed", vmax_factor: float = 1.6,
+                max_iters: int = 200, vmax: Optional[float] = None) -> Workload:
+    """1 trajectory, N segments, FREE waypoints, one speed bound ||v(t_ij)|| <= v_max
+    through either constraint path of the paper: the projection of Eq. 14 /
+    18f-g (inner="closed": the velocity-norm family) or the numerical step of
+    Eq. 15-17 (inner="numeric": the general family with an acceleration bound
+    too large to act).  Same geometry for both, from the same seed: random
+    walk (step N(0, 1.5^2)), T ~ U[0.3, 1.5] lengthened to ||dP||_inf / 3.
+    With free interior waypoints the trajectory only has to join the two
+    boundary states in the total time, so v_max is set from that: vmax_factor
+    x ||P_N - P_0|| / sum(T) (a rest-to-rest motion peaks well above its mean
+    speed, so the bound acts for factors below about 2).  An explicit `vmax`
+    overrides the rule."""
+    rng = np.random.default_rng(seed)
+    P = _random_walk(rng, N)
+    T = rng.uniform(0.3, 1.5, size=N)
+    dP = np.diff(P, axis=0)
+    T = np.maximum(T, np.abs(dP).max(axis=1) / 3.0)
+    if vmax is None:
+        vmax = float(vmax_factor * np.linalg.norm(P[N] - P[0]) / T.sum())
+    s, e = _rest_states(P[None, 0], P[None, N])
+    common = dict(seg_offset=np.array([0, N], np.int32), waypoints=P, durations=T, start_state=s, end_state=e,
+                  mode="free", rho=1.0, max_iters=max_iters)
+    if inner == "closed":
+        return Workload(name=f"speed_limit N={N} (projection)", inner="closed", M_vn=M,
+                        vnorm=np.array([vmax]), **common)
+    return Workload(name=f"speed_limit N={N} (numerical step)", inner="numeric", M_gen=M,
+                    gen_vmax=np.array([vmax]), gen_amax=np.array([1e6]), **common)
+
+
 def tiny(seed: int = 0, N: int = 3, mode: str = "pin", T_range=(0.5, 1.5), B: int = 1,
          step: float = 1.5) -> Workload:
     """Small random instances for edge-case tests."""
