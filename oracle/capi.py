@@ -53,6 +53,7 @@ class _Problem(C.Structure):
         ("lbfgs_tol", C.c_double), ("lbfgs_max_iters", C.c_int32), ("lbfgs_mem", C.c_int32),
         ("adaptive_rho", C.c_int32), ("rho_mu", C.c_double), ("rho_tau_incr", C.c_double),
         ("rho_tau_decr", C.c_double),
+        ("M_poly", C.c_int32), ("F_poly", C.c_int32), ("poly_n", C.c_void_p), ("poly_h", C.c_void_p),
     ]
 
 
@@ -141,6 +142,8 @@ def _make_problem(w, keep, lbfgs_tol, lbfgs_max_iters, lbfgs_mem, max_iters=None
         "vnorm": _f64(getattr(w, "vnorm", None)),
         "gen_vmax": _f64(getattr(w, "gen_vmax", None)),
         "gen_amax": _f64(getattr(w, "gen_amax", None)),
+        "poly_n": _f64(getattr(w, "poly_n", None)),
+        "poly_h": _f64(getattr(w, "poly_h", None)),
     }
     keep.extend(a for a in arrs.values() if a is not None)
     pb = _Problem()
@@ -163,6 +166,8 @@ def _make_problem(w, keep, lbfgs_tol, lbfgs_max_iters, lbfgs_mem, max_iters=None
     pb.rho_mu = float(getattr(w, "rho_mu", 10.0))
     pb.rho_tau_incr = float(getattr(w, "rho_tau_incr", 1.1))
     pb.rho_tau_decr = float(getattr(w, "rho_tau_decr", 1.1))
+    pb.M_poly = int(getattr(w, "M_poly", 0) or 0)
+    pb.F_poly = int(getattr(w, "F_poly", 0) or 0)
     return pb, B, S
 
 
@@ -198,7 +203,7 @@ def solve(w, *, real: str = "double", state: bool = False, history: bool = False
         Mb, Mq, Mv, Mg = pb.M_box, pb.M_ball, pb.M_vn, pb.M_gen
         out.update({
             "z": np.zeros((S + B, 3, 7)), "u": np.zeros((S, 42)),
-            "s": np.zeros((S, 6 * Mb)), "v": np.zeros((S, 6 * Mb)),
+            "s": np.zeros((S, 6 * Mb + pb.F_poly * pb.M_poly)), "v": np.zeros((S, 6 * Mb + pb.F_poly * pb.M_poly)),
             "phi_b": np.zeros((S, Mq, 3)), "w_b": np.zeros((S, Mq, 3)),
             "phi_v": np.zeros((S, Mv, 3)), "w_v": np.zeros((S, Mv, 3)),
             "y_gen": np.zeros((S, Mg, 2)), "inner_iters": np.zeros(S, np.int32),

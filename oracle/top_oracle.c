@@ -15,6 +15,8 @@
  *   - the numerical local step of Sec. III-C.3 (Eq. 15-17) solved with L-BFGS,
  *   - primal / dual residuals (Eq. 19-20) and the stopping rule (Eq. 21),
  *   - optionally the residual-balancing update of rho (UpdateRho, Eq. 22),
+ *   - linear rows from velocity boxes and from polytope corridors with
+ *     arbitrary face normals (Eq. 8-10, 18d-e),
  * all with dense matrices built entry by entry (the 24x24 local matrix of
  * Eq. 18a, the 42x24 consensus map, the 2*3*M x 24 linear-constraint matrix,
  * the 3x24 sample matrices), solved with a Cholesky factorisation of the
@@ -99,6 +101,12 @@ typedef struct or_problem {
   /* adaptive penalty (Sec. III-D.4, Eq. 22); 0 keeps rho fixed */
   int32_t adaptive_rho;
   double rho_mu, rho_tau_incr, rho_tau_decr;
+  /* polytope corridor (Sec. III-C.1, Eq. 8-10, 18d-e): segment i must satisfy
+     n_f^T p(t_ij) <= h_f for its F_poly faces at M_poly samples; the rows
+     n_f^T (x) beta(t_ij)^T follow the box rows in the linear-row block */
+  int32_t M_poly, F_poly;
+  const double *poly_n;      /* [S][F_poly][3] face normals */
+  const double *poly_h;      /* [S][F_poly] offsets */
 } or_problem;
 
 typedef struct or_result {
@@ -112,7 +120,8 @@ typedef struct or_result {
   /* optional state after the last iteration */
   double *z;          /* [S+B][3][7] */
   double *u;          /* [S][42] row (a, side, r) = a*14 + side*7 + r */
-  double *s, *v;      /* [S][6*M_box] row ((j*3)+a)*2 + sign */
+  double *s, *v;      /* [S][6*M_box + F_poly*M_poly]: box row ((j*3)+a)*2 + sign, then
+                         polytope row 6*M_box + j*F_poly + f */
   double *phi_b, *w_b;/* [S][M_ball][3] */
   double *phi_v, *w_v;/* [S][M_vn][3] */
   double *y_gen;      /* [S][M_gen][2] (velocity, acceleration) */
@@ -270,11 +279,22 @@ static int build_segment(seg_data *sd, const or_problem *pb, int b, int gi, int 
       for (int q = 0; q < NR; ++q) acc += sd->Mt[q * NL + i] * sd->E[q] * sd->Mt[q * NL + j];
       sd->K[i * NL + j] += rho * acc;
     }
-  sd->nbox = 6 * pb->M_box;
+  const int npoly = pb->M_poly > 0 ? pb->F_poly * pb->M_poly : 0;
+  sd->nbox = 6 * pb->M_box + npoly;
   sd->Ao = sd->b = sd->Ab = sd->Av = sd->Agv = sd->Aga = NULL;
-  if (pb->M_box > 0) {
+  if (sd->nbox > 0) {
     sd->Ao = (real *)calloc((size_t)sd->nbox * NL, sizeof(real));
     sd->b = (real *)calloc((size_t)sd->nbox, sizeof(real));
+    for (int j = 0; j < pb->M_poly && npoly; ++j) {
+      real t = (real)(j + 1) * T / (real)pb->M_poly;
+      for (int f = 0; f < pb->F_poly; ++f) {
+        int row = 6 * pb->M_box + j * pb->F_poly + f;
+        const double *nf = pb->poly_n + ((size_t)gi * pb->F_poly + f) * 3;
+        for (int a = 0; a < AX; ++a)
+          for (int k = 0; k < NC; ++k) sd->Ao[row * NL + a * NC + k] = (real)nf[a] * beta_rk(0, k, t);
+        sd->b[row] = pb->poly_h[(size_t)gi * pb->F_poly + f];
+      }
+    }
     for (int j = 0; j < pb->M_box; ++j) {
       real t = (real)(j + 1) * T / (real)pb->M_box;
       for (int a = 0; a < AX; ++a)
@@ -492,7 +512,7 @@ static int solve_one(const or_problem *pb, or_result *res, int b) {
   const double *P = pb->waypoints + (size_t)(s0 + b) * 3;
   real rho = pb->rho;
   const int Mb = pb->M_box, Mq = pb->M_ball, Mv = pb->M_vn, Mg = pb->M_gen;
-  const int nbox = 6 * Mb;
+  const int nbox = 6 * Mb + (pb->M_poly > 0 ? pb->F_poly * pb->M_poly : 0);  /* linear rows (box, polytope) */
   if (N <= 0) {
     res->cost[b] = 0; res->r_primal[b] = 0; res->r_dual[b] = 0;
     res->iters[b] = 0; res->status[b] = OR_CONVERGED;

@@ -67,6 +67,10 @@ class Workload:
     M_gen: int = 0
     gen_vmax: Optional[np.ndarray] = None  # [B]
     gen_amax: Optional[np.ndarray] = None  # [B]
+    M_poly: int = 0                          # polytope corridor: samples per segment
+    F_poly: int = 0                          # faces per segment polytope
+    poly_n: Optional[np.ndarray] = None      # [S, F, 3] face normals
+    poly_h: Optional[np.ndarray] = None      # [S, F] offsets: n_f . p(t_ij) <= h_f
     adaptive_rho: bool = False  # UpdateRho of Eq. 22 (mu, tau_incr, tau_decr as the paper: 10, 1.1, 1.1)
     rho_mu: float = 10.0
     rho_tau_incr: float = 1.1
@@ -123,6 +127,8 @@ class Workload:
             vnorm=per_b(self.vnorm),
             gen_vmax=per_b(self.gen_vmax),
             gen_amax=per_b(self.gen_amax),
+            poly_n=per_s(self.poly_n),
+            poly_h=per_s(self.poly_h),
         )
 
 
@@ -236,6 +242,41 @@ def general(seed: int = 0, N: int = 100000, v_nom: float = 1.0) -> Workload:
         durations=T, start_state=s, end_state=e, mode="pin", inner="numeric", rho=1.0,
         max_iters=200, M_gen=16, gen_vmax=np.array([4.0]), gen_amax=np.array([8.0]),
     )
+
+
+def with_polytopes(w: Workload, F: int = 8, M: int = 8, seed: int = 0, margin=(0.3, 1.5)) -> Workload:
+    """Polytope corridors around every segment's chord, standing in for the
+    paper's FIRI corridors (which need point-cloud maps): per segment, the six
+    faces of a randomly rotated cube plus F - 6 faces with random unit normals,
+    each offset to the farther chord end plus a margin ~ U[margin], so both
+    waypoints (hence the chord) lie inside and consecutive polytopes overlap
+    at the shared waypoint.  Normals are never axis-aligned in general, so the
+    rows n_f^T (x) beta(t)^T couple the three axes."""
+    if F < 6:
+        raise ValueError("F >= 6 (the rotated cube keeps every polytope bounded)")
+    rng = np.random.default_rng([seed, 7])
+    off = np.asarray(w.seg_offset)
+    S = int(off[-1])
+    n = np.zeros((S, F, 3))
+    h = np.zeros((S, F))
+    for b in range(len(off) - 1):
+        for g in range(int(off[b]), int(off[b + 1])):
+            Qm, Rm = np.linalg.qr(rng.normal(size=(3, 3)))
+            Qm = Qm * np.sign(np.diag(Rm))[None, :]
+            faces = np.concatenate([Qm.T, -Qm.T, rng.normal(size=(F - 6, 3))], axis=0)
+            faces /= np.linalg.norm(faces, axis=1, keepdims=True)
+            ends = w.waypoints[[g + b, g + b + 1]]                 # [2, 3]
+            n[g] = faces
+            h[g] = (faces @ ends.T).max(axis=1) + rng.uniform(margin[0], margin[1], size=F)
+    return w.with_(name=f"{w.name} + polytopes F={F} M={M}", M_poly=M, F_poly=F, poly_n=n, poly_h=h)
+
+
+def polytope_corridor(seed: int = 0, N: int = 1024, F: int = 8, M: int = 8) -> Workload:
+    """1 trajectory, N segments: the corridor recipe's random walk and
+    durations, FREE waypoints, |v_axis| <= 3 at 16 samples, and a polytope of
+    F faces around every chord sampled at M points (with_polytopes)."""
+    w = corridor(seed=seed, N=N).with_(M_ball=0, ball_c=None, ball_r=None)
+    return with_polytopes(w, F=F, M=M, seed=seed).with_(name=f"polytope_corridor N={N} F={F} M={M}")
 
 
 def speed_limit(seed: int = 0, N: int = 256, M: int = 16, inner: str = "closed", vmax_factor: float = 1.6,

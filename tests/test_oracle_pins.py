@@ -515,3 +515,88 @@ def adaptive_dual_continuity_error(lib=None):
 
 def test_adaptive_rho_unscaled_dual_is_continuous():
     assert adaptive_dual_continuity_error() < 1e-12
+
+
+# ------------------------------------------- polytope corridors (Eq. 8-10) --
+
+def _polytope_instance():
+    """Tiny FREE instance inside tight polytopes (F=6 faces, M=4 samples):
+    two rows are active at the optimum; rho = 10 converges to 1e-9."""
+    w0 = W.tiny(seed=5, N=3, mode="free", T_range=(0.9, 1.3), step=2.0)
+    return W.with_polytopes(w0, F=6, M=4, seed=1, margin=(0.05, 0.2)).with_(max_iters=200000, eps=1e-9, rho=10.0)
+
+
+def polytope_kkt_errors(lib=None):
+    """KKT conditions of the sampled-polytope QP at the converged oracle state,
+    with every matrix rebuilt here from the basis: stationarity with
+    lambda = rho u and mu = rho v, dual feasibility mu >= 0, primal feasibility,
+    complementarity (each relative to |2 Qt c|), and the number of active rows."""
+    w = _polytope_instance()
+    r = oracle.solve(w, state=True, **({} if lib is None else {"real": lib}))
+    rho = w.rho
+    T, M, F = w.durations, w.M_poly, w.F_poly
+    N = len(T)
+    worst = {"stat": 0.0, "dual": 0.0, "primal": 0.0, "compl": 0.0}
+    active = 0
+    for i in range(N):
+        Mt, E = _consensus_rows(T[i], i == 0, i == N - 1)
+        A, h = [], []
+        for j in range(1, M + 1):
+            beta = CZ.deriv_row(0, j * T[i] / M)
+            for f in range(F):
+                A.append(np.kron(w.poly_n[i, f], beta))
+                h.append(w.poly_h[i, f])
+        A, h = np.array(A), np.array(h)
+        Qt = np.zeros((24, 24))
+        for a in range(3):
+            Qt[a * 8:(a + 1) * 8, a * 8:(a + 1) * 8] = CZ.snap_gram(T[i])
+        ci = r["coeffs"][i].reshape(24)
+        mu = rho * r["v"][i]
+        scale = np.abs(2 * Qt @ ci).max()
+        stat = 2 * Qt @ ci + rho * Mt.T @ (E * r["u"][i]) + A.T @ mu
+        worst["stat"] = max(worst["stat"], np.abs(stat).max() / scale)
+        worst["dual"] = max(worst["dual"], max(0.0, -mu.min()) / scale)
+        worst["primal"] = max(worst["primal"], max(0.0, (A @ ci - h).max()))
+        worst["compl"] = max(worst["compl"], np.abs(mu * (A @ ci - h)).max() / scale)
+        active += int((mu > 1e-6 * scale).sum())
+    return worst, active, r
+
+
+def test_polytope_kkt_certificate():
+    worst, active, r = polytope_kkt_errors()
+    assert r["status"][0] == 0
+    assert active >= 2, "the polytopes must bind"
+    assert worst["stat"] < 1e-6 and worst["dual"] < 1e-9 and worst["primal"] < 1e-7 and worst["compl"] < 1e-6, worst
+
+
+def _rotation(seed):
+    Qm, Rm = np.linalg.qr(np.random.default_rng(seed).normal(size=(3, 3)))
+    Qm = Qm * np.sign(np.diag(Rm))[None, :]
+    return Qm * np.sign(np.linalg.det(Qm))
+
+
+def polytope_rotation_error(lib=None):
+    """Rotating the waypoints, boundary states and face normals by R rotates
+    every iterate: c'_i[a, k] = sum_b R[a, b] c_i[b, k] (the ADMM of Eq. 18 with
+    rotation-invariant rows is rotation-equivariant)."""
+    w = _polytope_instance().with_(max_iters=300, eps=0.0)
+    R = _rotation(11)
+    wr = w.with_(waypoints=w.waypoints @ R.T, start_state=w.start_state @ R.T, end_state=w.end_state @ R.T,
+                 poly_n=w.poly_n @ R.T)
+    kw = {} if lib is None else {"real": lib}
+    a = oracle.solve(w, **kw)["coeffs"]
+    b = oracle.solve(wr, **kw)["coeffs"]
+    rot = np.einsum("ab,ibk->iak", R, a)
+    return float(np.abs(rot - b).max() / np.abs(a).max())
+
+
+def test_polytope_rotation_equivariance():
+    assert polytope_rotation_error() < 1e-11
+
+
+def test_inactive_polytopes_keep_the_free_fixed_point():
+    w0 = W.tiny(seed=5, N=3, mode="free", T_range=(0.9, 1.3), step=2.0)
+    w = W.with_polytopes(w0, F=8, M=4, seed=2, margin=(50.0, 60.0)).with_(max_iters=100000, eps=1e-10)
+    r = oracle.solve(w)
+    ref = CZ.free_polynomial(w.durations, w.start_state[0], w.end_state[0])
+    assert scaled_relerr(r["coeffs"], ref, w.durations) < 1e-9

@@ -16,7 +16,8 @@ from oracle import centralized as CZ
 from paper_2507_10290_gb300 import workloads as W
 
 from test_oracle_pins import (_box_instance, _numpy_F, adaptive_dual_continuity_error, adaptive_kkt_error,
-                              adaptive_rule_violations, read_golden, scaled_relerr)
+                              adaptive_rule_violations, polytope_kkt_errors, polytope_rotation_error, read_golden,
+                              scaled_relerr)
 
 
 def pin_closed_form(lib):
@@ -121,8 +122,19 @@ def pin_adaptive_dual(lib):
     return adaptive_dual_continuity_error(lib) < 1e-12
 
 
+def pin_polytope_kkt(lib):
+    worst, active, r = polytope_kkt_errors(lib)
+    return (r["status"][0] == 0 and active >= 2 and worst["stat"] < 1e-6 and worst["dual"] < 1e-9
+            and worst["primal"] < 1e-7 and worst["compl"] < 1e-6)
+
+
+def pin_polytope_rotation(lib):
+    return polytope_rotation_error(lib) < 1e-11
+
+
 ALL_PINS = [pin_projection, pin_closed_form, pin_numeric_stationary, pin_free_fixed_point,
-            pin_active_set, pin_pin_fixed_point, pin_adaptive_rule, pin_adaptive_dual, pin_adaptive_kkt]
+            pin_active_set, pin_pin_fixed_point, pin_adaptive_rule, pin_adaptive_dual, pin_adaptive_kkt,
+            pin_polytope_rotation, pin_polytope_kkt]
 
 PLANTS = {
     "rhs without rho": ("for (int l = 0; l < NL; ++l) rhs[l] *= rho;\n        chol_solve",
@@ -146,6 +158,12 @@ PLANTS = {
     "rho rule inverted": ("rn = rho * (real)pb->rho_tau_incr;", "rn = rho / (real)pb->rho_tau_incr;"),
     "K kept at old rho": ("if (refactor_segment(&sd[i], pb, rho) != 0)",
                           "if (0 && refactor_segment(&sd[i], pb, rho) != 0)"),
+    "polytope normal on the wrong axis": ("sd->Ao[row * NL + a * NC + k] = (real)nf[a] * beta_rk(0, k, t);",
+                                          "sd->Ao[row * NL + a * NC + k] = (real)nf[(a + 1) % 3] * beta_rk(0, k, t);"),
+    "polytope rows on velocity": ("sd->Ao[row * NL + a * NC + k] = (real)nf[a] * beta_rk(0, k, t);",
+                                  "sd->Ao[row * NL + a * NC + k] = (real)nf[a] * beta_rk(1, k, t);"),
+    "polytope offset sign": ("sd->b[row] = pb->poly_h[(size_t)gi * pb->F_poly + f];",
+                             "sd->b[row] = -pb->poly_h[(size_t)gi * pb->F_poly + f];"),
 }
 
 
