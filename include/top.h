@@ -130,6 +130,17 @@ typedef struct top_problem {
   double rho_mu;              /* >= 1 (0 = 10) */
   double rho_tau_incr;        /* >= 1 (0 = 1.1) */
   double rho_tau_decr;        /* >= 1 (0 = 1.1) */
+  /* Polytope corridors (Sec. III-C.1, Eq. 8-10, 18d-e): segment i must satisfy
+   * n_f . p(t_ij) <= h_f for its F_poly faces at the M_poly sample times
+   * t_ij = j T_i / M_poly, each row with its own slack and dual.  The rows
+   * couple the axes; the library factorises each segment's local matrix in
+   * the eigenbasis of sum_f n_f n_f^T, where it is block diagonal.  Closed-form
+   * step only, fixed rho (adaptive_rho: TOP_E_NOTSUP); such problems run in the
+   * streaming form.  M_poly = 0: no polytopes. */
+  int32_t M_poly;
+  int32_t F_poly;             /* faces per segment (>= 1 when M_poly > 0) */
+  const double *poly_n;       /* [S][F_poly][3] face normals (any length; rows scale with it) */
+  const double *poly_h;       /* [S][F_poly] offsets */
 } top_problem;
 
 /* Outputs (same memory kind as the problem).  history may be NULL. */

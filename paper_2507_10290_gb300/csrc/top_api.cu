@@ -26,6 +26,10 @@ struct top_handle {
   void *G = nullptr;          // [36][max_segments] of the iteration type
   void *E = nullptr;          // [NE][S] adaptive-rho data (allocated on first use)
   size_t E_bytes = 0;
+  void *P = nullptr;          // polytope family data (PolyData), allocated on first use
+  size_t P_bytes = 0;
+  unsigned char *d_pstage = nullptr;  // staging of host polytope arrays
+  size_t pstage_bytes = 0;
   Pack *d_packs = nullptr;    // [max_segments]
   int *d_err = nullptr;       // error flag of the precompute kernel
   // staging for TOP_MEM_HOST problems
@@ -67,12 +71,29 @@ int cuda_fail(top_handle *h, cudaError_t e) {
 
 size_t rbytes(const top_handle *h) { return h->cfg.precision == TOP_FP64 ? 8 : 4; }
 
+// grow-only device buffer; cudaSuccess or the allocation's error (sticky errors cleared)
+cudaError_t grow(void **ptr, size_t *cap, size_t want) {
+  if (want <= *cap) return cudaSuccess;
+  cudaFree(*ptr);
+  *ptr = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc(ptr, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return e;
+  }
+  *cap = want;
+  return cudaSuccess;
+}
+
 int families(const top_problem *pb) {
   int f = 0;
   if (pb->inner == TOP_CLOSED_FORM) {
     if (pb->M_box > 0) f |= FAM_BOX;
     if (pb->M_ball > 0) f |= FAM_BALL;
     if (pb->M_vn > 0) f |= FAM_VN;
+    if (pb->M_poly > 0) f |= FAM_POLY;
   } else if (pb->M_gen > 0) {
     f |= FAM_GEN;
   }
@@ -224,6 +245,9 @@ int validate(const top_handle *h, const top_problem *pb, const top_result *res) 
   if (pb->M_gen > 0 && (!pb->gen_vmax || !pb->gen_amax)) return TOP_E_INVAL;
   if (pb->inner == TOP_NUMERIC && (pb->M_box || pb->M_ball || pb->M_vn)) return TOP_E_NOTSUP;
   if (pb->inner == TOP_CLOSED_FORM && pb->M_gen) return TOP_E_NOTSUP;
+  if (pb->M_poly < 0 || (pb->M_poly > 0 && (pb->F_poly < 1 || !pb->poly_n || !pb->poly_h))) return TOP_E_INVAL;
+  if (pb->M_poly > h->cfg.max_samples) return TOP_E_NOMEM;
+  if (pb->M_poly > 0 && (pb->inner != TOP_CLOSED_FORM || pb->adaptive_rho)) return TOP_E_NOTSUP;
   if (pb->adaptive_rho != 0 && pb->adaptive_rho != 1) return TOP_E_INVAL;
   if (pb->adaptive_rho) {
     for (double v : {pb->rho_mu, pb->rho_tau_incr, pb->rho_tau_decr})
@@ -288,6 +312,8 @@ void top_destroy(top_handle *h) {
   cudaSetDevice(h->device);
   cudaFree(h->G);
   cudaFree(h->E);
+  cudaFree(h->P);
+  cudaFree(h->d_pstage);
   cudaFree(h->d_packs);
   cudaFree(h->d_err);
   cudaFree(h->d_stage);
@@ -396,6 +422,15 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     pb.vnorm = pb.M_vn ? (const double *)up(pb_in->vnorm, SP.off_vn, sizeof(double) * B) : nullptr;
     pb.gen_vmax = pb.M_gen ? (const double *)up(pb_in->gen_vmax, SP.off_gv, sizeof(double) * B) : nullptr;
     pb.gen_amax = pb.M_gen ? (const double *)up(pb_in->gen_amax, SP.off_ga, sizeof(double) * B) : nullptr;
+    if (pb.M_poly > 0) {
+      const size_t bn = sizeof(double) * 3 * (size_t)pb.F_poly * S, bh = sizeof(double) * (size_t)pb.F_poly * S;
+      cudaError_t e = grow((void **)&h->d_pstage, &h->pstage_bytes, align_up(bn, 256) + bh);
+      if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TOP_E_NOMEM : cuda_fail(h, e);
+      TOP_CUDA(h, cudaMemcpyAsync(h->d_pstage, pb_in->poly_n, bn, cudaMemcpyHostToDevice, st));
+      TOP_CUDA(h, cudaMemcpyAsync(h->d_pstage + align_up(bn, 256), pb_in->poly_h, bh, cudaMemcpyHostToDevice, st));
+      pb.poly_n = (const double *)h->d_pstage;
+      pb.poly_h = (const double *)(h->d_pstage + align_up(bn, 256));
+    }
     TOP_CUDA(h, cudaGetLastError());
     res.coeffs = (double *)(base + SP.off_coef);
     res.cost = (double *)(base + SP.off_cost);
@@ -425,6 +460,8 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   dp.lbfgs_mem = pb.lbfgs_mem > 0 ? pb.lbfgs_mem : 8;
   dp.lbfgs_max_iters = pb.lbfgs_max_iters > 0 ? pb.lbfgs_max_iters : 50;
   dp.lbfgs_tol = pb.lbfgs_tol > 0 ? pb.lbfgs_tol : (h->cfg.precision == TOP_FP64 ? 1e-12 : 1e-6);
+  dp.M_poly = pb.M_poly; dp.F_poly = pb.M_poly > 0 ? pb.F_poly : 0;
+  dp.poly_n = pb.poly_n; dp.poly_h = pb.poly_h;
   dp.adaptive = pb.adaptive_rho;
   dp.rho_mu = pb.rho_mu > 0 ? pb.rho_mu : 10.0;
   dp.rho_incr = pb.rho_tau_incr > 0 ? pb.rho_tau_incr : 1.1;
@@ -462,9 +499,25 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   TOP_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
   const bool fp64 = h->cfg.precision == TOP_FP64;
   h->ran[0] = h->ran[1] = h->ran[2] = false;
+  PolyData pdata{nullptr, nullptr, nullptr, nullptr};
   {
     if (h->profiling) cudaEventRecord(h->ev[0], st);
-    int e = launch_kinv(dp, pb.rho, fp64 ? nullptr : h->G, fp64 ? h->G : nullptr, h->d_err, st);
+    int e = 0;
+    if (pb.M_poly > 0) {
+      const size_t rb = rbytes(h), Sz = (size_t)S, Fp = (size_t)pb.F_poly;
+      const size_t bG = align_up(rb * 3 * NG * Sz, 256), bU = align_up(rb * 9 * Sz, 256);
+      const size_t bN = align_up(rb * 3 * Fp * Sz, 256), bH = align_up(rb * Fp * Sz, 256);
+      cudaError_t ge = grow(&h->P, &h->P_bytes, bG + bU + bN + bH);
+      if (ge != cudaSuccess) {
+        if (d_hist) cudaFree(d_hist);
+        return ge == cudaErrorMemoryAllocation ? TOP_E_NOMEM : cuda_fail(h, ge);
+      }
+      unsigned char *pbase = (unsigned char *)h->P;
+      pdata = PolyData{pbase, pbase + bG, pbase + bG + bU, pbase + bG + bU + bN};
+      e = launch_kinv_poly(dp, pb.rho, fp64, pdata, h->d_err, st);
+    } else {
+      e = launch_kinv(dp, pb.rho, fp64 ? nullptr : h->G, fp64 ? h->G : nullptr, h->d_err, st);
+    }
     if (e) return cuda_fail(h, (cudaError_t)e);
     if (adapt) {
       e = launch_keig(dp, fp64 ? nullptr : h->E, fp64 ? h->E : nullptr, h->d_err, st);
@@ -474,7 +527,8 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   }
   // ---- plan: resident packs of whole trajectories ----
   const int fam = families(&pb);
-  const int cap = (h->cfg.schedule == TOP_SCHED_STREAM || pb.inner == TOP_NUMERIC) ? 0 : resident_capacity(h, &pb);
+  const int cap = (h->cfg.schedule == TOP_SCHED_STREAM || pb.inner == TOP_NUMERIC || pb.M_poly > 0)
+                      ? 0 : resident_capacity(h, &pb);
   const int ntp_cap = std::max(1, cap / 4);
   // the plan is reused while the batch layout and the capacity repeat
   const bool same_plan = h->plan_valid && h->plan_B == B && h->plan_cap == cap &&
@@ -542,6 +596,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     const size_t o_qv = take(rb * 3 * Mv * (size_t)S);
     const int Mg = (fam & FAM_GEN) ? pb.M_gen : 0;
     const size_t o_yg = take(rb * 2 * Mg * (size_t)S);
+    const size_t o_yp = take(rb * (size_t)dp.F_poly * dp.M_poly * (size_t)S);
     const size_t o_rp = take(sizeof(double) * total), o_rd = take(sizeof(double) * total);
     const size_t o_done = take(sizeof(int) * nl), o_trp = take(sizeof(double) * nl), o_trd = take(sizeof(double) * nl);
     const size_t o_rho = take(sizeof(double) * nl), o_fac = take(sizeof(double) * nl);
@@ -571,6 +626,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     sa.eS = base + o_eS; sa.eE = base + o_eE; sa.ch = base + o_ch;
     sa.ybox = base + o_yb; sa.qball = base + o_qb; sa.qvn = base + o_qv;
     sa.ygen = base + o_yg; sa.inner_iters = nullptr;
+    sa.ypoly = base + o_yp; sa.poly = pdata;
     sa.rp2 = (double *)(base + o_rp); sa.rd2 = (double *)(base + o_rd);
     sa.done = (int *)(base + o_done); sa.tr_rp = (double *)(base + o_trp); sa.tr_rd = (double *)(base + o_trd);
     sa.rho_t = (double *)(base + o_rho); sa.fac_t = (double *)(base + o_fac);
@@ -610,7 +666,7 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
   fake.iters = fake.status = (int32_t *)ddurations;
   int rc = validate(h, pb_in, &fake);
   if (rc != TOP_OK) return rc;
-  if (pb_in->M_box || pb_in->M_ball || pb_in->M_vn || pb_in->M_gen) return TOP_E_NOTSUP;
+  if (pb_in->M_box || pb_in->M_ball || pb_in->M_vn || pb_in->M_gen || pb_in->M_poly) return TOP_E_NOTSUP;
   if (pb_in->adaptive_rho) return TOP_E_NOTSUP;
   cudaStream_t st = (cudaStream_t)stream;
   TOP_CUDA(h, cudaSetDevice(h->device));

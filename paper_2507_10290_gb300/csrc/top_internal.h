@@ -6,7 +6,7 @@
 
 namespace top {
 
-enum Family : int { FAM_BOX = 1, FAM_BALL = 2, FAM_VN = 4, FAM_GEN = 8 };
+enum Family : int { FAM_BOX = 1, FAM_BALL = 2, FAM_VN = 4, FAM_GEN = 8, FAM_POLY = 16 };
 
 // A pack is a set of whole trajectories processed by one CTA of the
 // resident kernel (all of its state stays in shared memory for every
@@ -35,6 +35,7 @@ struct DevProblem {
   double lbfgs_tol;
   int adaptive;   // residual balancing of rho (Eq. 22)
   double rho_mu, rho_incr, rho_decr;
+  int M_poly, F_poly; const double *poly_n, *poly_h;  // polytope corridors
 };
 
 struct DevResult {
@@ -49,6 +50,16 @@ struct DevResult {
 // with A0 supported on the top-left 4x4 block (packed lower, 10 values),
 // Y = [y_0 .. y_3] (8 x 4, row-major) and lambda_k >= 0.  Layout [NE][S].
 constexpr int NE_A0 = 0, NE_Y = 10, NE_L = 42, NE = 46;
+
+// Per-segment data of the polytope family, element type = iteration type,
+// layout [rows][S]: with N3 = sum_f n_f n_f^T = U diag(nu) U^T, the local
+// matrix is block diagonal in the rotated axes c~_b = sum_a U[a][b] c_a:
+//   PG: [3 * 36]  packed inverses of K8 + rho nu_b B_pos, one per rotated axis b
+//   PU: [9]       U[a][b] at row a * 3 + b
+//   PN: [3 F]     normals, row f * 3 + a;   PH: [F] offsets
+struct PolyData {
+  void *G, *U, *N, *H;
+};
 
 struct ResidentArgs {
   DevProblem p;
@@ -112,6 +123,7 @@ struct StreamArgs {
   DevResult r;
   const void *G;           // [36][S] (rewritten on a change of rho)
   const void *E;           // [NE][S] adaptive-rho data, or null
+  PolyData poly;           // polytope family (FAM_POLY), else null pointers
   const int *lt_b;         // [nl]
   const int *lt_prefix;    // [nl+1]
   int nl, total;           // trajectories, segments in the streaming set
@@ -124,6 +136,7 @@ struct StreamArgs {
   void *ch;                // [24][S]
   void *ybox, *qball, *qvn;  // [6 M_box][S], [3 M_ball][S], [3 M_vn][S]
   void *ygen;              // [2 M_gen][S] numerical-step duals (velocity, acceleration)
+  void *ypoly;             // [F_poly M_poly][S] compressed slack / dual of the polytope rows, row j * F + f
   int *inner_iters;        // [S] L-BFGS iterations summed over the run (numerical step), or null
   double *rp2, *rd2;       // [total]
   int *done;               // [nl]
@@ -134,6 +147,7 @@ struct StreamArgs {
 // launchers (defined in the .cu files)
 int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_flag, void *stream);
 int launch_keig(const DevProblem &p, void *E32, void *E64, int *err_flag, void *stream);
+int launch_kinv_poly(const DevProblem &p, double rho, bool fp64, const PolyData &out, int *err_flag, void *stream);
 int launch_fill(double *x, int n, double v, void *stream);
 int launch_resident_f32(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
 int launch_resident_f64(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);

@@ -160,6 +160,25 @@ __device__ __forceinline__ bool equil_chol_inv(double (&A)[NG], double (&d)[NC])
   return true;
 }
 
+// K^-1 from A = L^-1 of D K D (packed lower) and the scaling d:
+// (D K D)^-1 = L^-T L^-1, so K^-1 = D L^-T L^-1 D; packed symmetric entries
+// written to rows base + gidx(k, l) of the [rows][S] output
+__device__ __forceinline__ void store_inverse(const double (&A)[NG], const double (&d)[NC], int S, int g, int base,
+                                              float *G32, double *G64) {
+#pragma unroll
+  for (int k = 0; k < NC; ++k)
+#pragma unroll
+    for (int l = k; l < NC; ++l) {
+      double a = 0.0;
+#pragma unroll
+      for (int q = l; q < NC; ++q) a += A[lidx(q, k)] * A[lidx(q, l)];
+      const double v = d[k] * a * d[l];
+      const size_t idx = size_t(base + gidx(k, l)) * S + g;
+      if (G64) G64[idx] = v;
+      if (G32) G32[idx] = float(v);
+    }
+}
+
 template <bool SAMPLES>
 __global__ void __launch_bounds__(128) kinv_kernel(const DevProblem p, double rho, float *__restrict__ G32,
                                                    double *__restrict__ G64, int *__restrict__ err) {
@@ -182,47 +201,35 @@ __global__ void __launch_bounds__(128) kinv_kernel(const DevProblem p, double rh
       atomicOr(err, 2);
       continue;
     }
-    // (D K D)^-1 = L^-T L^-1, so K^-1 = D L^-T L^-1 D
-#pragma unroll
-    for (int k = 0; k < NC; ++k)
-#pragma unroll
-      for (int l = k; l < NC; ++l) {
-        double a = 0.0;
-#pragma unroll
-        for (int q = l; q < NC; ++q) a += A[lidx(q, k)] * A[lidx(q, l)];
-        const double v = d[k] * a * d[l];
-        const int idx = gidx(k, l);
-        if (G64) G64[size_t(idx) * S + g] = v;
-        if (G32) G32[size_t(idx) * S + g] = float(v);
-      }
+    store_inverse(A, d, S, g, 0, G32, G64);
   }
 }
 
-// one cyclic-Jacobi rotation of the symmetric 4x4 matrix C zeroing C[P][Q]
+// one cyclic-Jacobi rotation of the symmetric D x D matrix C zeroing C[P][Q]
 // (textbook symmetric Schur decomposition, e.g. Golub & Van Loan, Sec. 8.5),
 // accumulated into the eigenvector columns of V
-template <int P, int Q>
-__device__ __forceinline__ void jacobi_rot(double (&C)[4][4], double (&V)[4][4]) {
+template <int P, int Q, int D>
+__device__ __forceinline__ void jacobi_rot(double (&C)[D][D], double (&V)[D][D]) {
   const double apq = C[P][Q];
   if (apq == 0.0) return;
   const double theta = (C[Q][Q] - C[P][P]) / (2.0 * apq);
   const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
   const double c = rsqrt(1.0 + t * t), sn = t * c;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {  // columns P, Q of C J
+  for (int k = 0; k < D; ++k) {  // columns P, Q of C J
     const double ckp = C[k][P], ckq = C[k][Q];
     C[k][P] = c * ckp - sn * ckq;
     C[k][Q] = sn * ckp + c * ckq;
   }
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {  // rows P, Q of J^T (C J)
+  for (int k = 0; k < D; ++k) {  // rows P, Q of J^T (C J)
     const double cpk = C[P][k], cqk = C[Q][k];
     C[P][k] = c * cpk - sn * cqk;
     C[Q][k] = sn * cpk + c * cqk;
   }
   C[P][Q] = C[Q][P] = 0.0;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < D; ++k) {
     const double vkp = V[k][P], vkq = V[k][Q];
     V[k][P] = c * vkp - sn * vkq;
     V[k][Q] = sn * vkp + c * vkq;
@@ -330,6 +337,94 @@ __global__ void __launch_bounds__(128) keig_kernel(const DevProblem p, float *__
       if (E32) E32[size_t(q) * S + g] = float(out[q]);
     }
   }
+}
+
+// Polytope family (FP64, once per solve).  N3 = sum_f n_f n_f^T = U diag(nu) U^T
+// by cyclic Jacobi; in the rotated axes the polytope rows add rho nu_b B_pos to
+// the isotropic 8x8 local matrix of axis b (B_pos = sum_j b_j b_j^T, position
+// samples b_j[k] = tau_j^k), so each rotated axis gets its own 8x8 inverse.
+// The normals and offsets are also stored in the iteration type.
+template <bool SAMPLES, class R>
+__global__ void __launch_bounds__(128) kinv_poly_kernel(const DevProblem p, double rho, R *__restrict__ PG,
+                                                        R *__restrict__ PU, R *__restrict__ PN, R *__restrict__ PH,
+                                                        int *__restrict__ err) {
+  const int S = p.S, F = p.F_poly;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < S; g += gridDim.x * blockDim.x) {
+    bool first, last;
+    double s[NC];
+    if (!segment_setup(p, g, first, last, s)) {
+      atomicOr(err, 1);
+      continue;
+    }
+    double C3[3][3], U[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) { C3[a][b] = 0.0; U[a][b] = (a == b) ? 1.0 : 0.0; }
+    for (int f = 0; f < F; ++f) {
+      const double *nf = p.poly_n + ((size_t)g * F + f) * 3;
+      const double n0 = nf[0], n1 = nf[1], n2 = nf[2], hf = p.poly_h[(size_t)g * F + f];
+      if (!(n0 == n0 && n1 == n1 && n2 == n2 && hf == hf)) atomicOr(err, 1);
+      C3[0][0] += n0 * n0; C3[0][1] += n0 * n1; C3[0][2] += n0 * n2;
+      C3[1][1] += n1 * n1; C3[1][2] += n1 * n2; C3[2][2] += n2 * n2;
+      PN[(size_t)(f * 3 + 0) * S + g] = R(n0);
+      PN[(size_t)(f * 3 + 1) * S + g] = R(n1);
+      PN[(size_t)(f * 3 + 2) * S + g] = R(n2);
+      PH[(size_t)f * S + g] = R(hf);
+    }
+    C3[1][0] = C3[0][1]; C3[2][0] = C3[0][2]; C3[2][1] = C3[1][2];
+    for (int sweep = 0; sweep < 16; ++sweep) {
+      double off = 0.0, dia = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        dia += C3[i][i] * C3[i][i];
+#pragma unroll
+        for (int j = i + 1; j < 3; ++j) off += C3[i][j] * C3[i][j];
+      }
+      if (!(off > 1e-34 * dia)) break;
+      jacobi_rot<0, 1>(C3, U); jacobi_rot<0, 2>(C3, U); jacobi_rot<1, 2>(C3, U);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) PU[(size_t)(a * 3 + b) * S + g] = R(U[a][b]);
+    for (int b = 0; b < 3; ++b) {
+      const double nu = C3[b][b] > 0.0 ? C3[b][b] : 0.0;
+      double A[NG];
+#pragma unroll
+      for (int r = 0; r < NC; ++r)
+#pragma unroll
+        for (int c = 0; c <= r; ++c) A[lidx(r, c)] = 2.0 * s[7] * qhat(r, c);
+      add_rho_terms<SAMPLES>(p, s, first, last, rho, A);
+      if (nu > 0.0) add_sample_rows(A, p.M_poly, 0, rho * nu);
+      double d[NC];
+      if (!equil_chol_inv(A, d)) {
+        atomicOr(err, 2);
+        break;
+      }
+      if (sizeof(R) == 8) store_inverse(A, d, S, g, b * NG, nullptr, (double *)PG);
+      else store_inverse(A, d, S, g, b * NG, (float *)PG, nullptr);
+    }
+  }
+}
+
+int launch_kinv_poly(const DevProblem &p, double rho, bool fp64, const PolyData &out, int *err_flag, void *stream) {
+  if (p.S == 0) return 0;
+  const int threads = 128;
+  int blocks = (p.S + threads - 1) / threads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool samples = p.inner == 0 && (p.M_box > 0 || p.M_ball > 0 || p.M_vn > 0);
+#define TOP_KP(SMP, R)                                                                                   \
+  kinv_poly_kernel<SMP, R><<<blocks, threads, 0, st>>>(p, rho, (R *)out.G, (R *)out.U, (R *)out.N, (R *)out.H, \
+                                                       err_flag)
+  if (fp64) {
+    if (samples) TOP_KP(true, double); else TOP_KP(false, double);
+  } else {
+    if (samples) TOP_KP(true, float); else TOP_KP(false, float);
+  }
+#undef TOP_KP
+  return (int)cudaGetLastError();
 }
 
 int launch_keig(const DevProblem &p, void *E32, void *E64, int *err_flag, void *stream) {

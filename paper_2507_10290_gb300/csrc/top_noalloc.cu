@@ -95,6 +95,7 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
   if (pb->mode != TOP_PIN && pb->mode != TOP_FREE) return TOP_E_INVAL;
   if (pb->inner != TOP_CLOSED_FORM || pb->M_gen != 0) return TOP_E_NOTSUP;
   if (pb->adaptive_rho != 0) return TOP_E_NOTSUP;  // the fixed scratch has no room for the adaptive-rho data
+  if (pb->M_poly != 0) return TOP_E_NOTSUP;        // nor for the polytope family's per-axis inverses
   if (pb->M_box < 0 || pb->M_ball < 0 || pb->M_vn < 0) return TOP_E_INVAL;
   if ((pb->M_box && !pb->vbox) || (pb->M_ball && (!pb->ball_c || !pb->ball_r)) || (pb->M_vn && !pb->vnorm))
     return TOP_E_INVAL;

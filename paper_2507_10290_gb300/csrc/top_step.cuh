@@ -43,16 +43,17 @@ __device__ __forceinline__ void fill_sample_table(R *tab, int M, int order, int 
   }
 }
 
+// The right-hand side of Eq. 18a for the consensus rows and the box / ball /
+// velocity-norm families (the first half of the local step).
 // FS: the start-side targets wS already carry the factor k! (see consensus_rhs_f)
 template <class R, int F, bool FS = false>
-__device__ __forceinline__ void local_step(const SegConst<R> &sc, const R (&wS)[AX][ND], const R (&wE)[AX][ND],
-                                           R rho, bool first_iter, R *ybox, R *qball, R *qvn, int stride,
-                                           const R *tabB, const R *tabQ, const R *tabV, int Mb, int Mq, int Mv,
-                                           R (&ch)[AX][NC]) {
+__device__ __forceinline__ void family_rhs(const SegConst<R> &sc, const R (&wS)[AX][ND], const R (&wE)[AX][ND],
+                                           R rho, bool first_iter, const R *ybox, const R *qball, const R *qvn,
+                                           int stride, const R *tabB, const R *tabQ, const R *tabV, int Mb, int Mq,
+                                           int Mv, R (&rhs)[AX][NC]) {
   constexpr bool BOX = (F & FAM_BOX) != 0;
   constexpr bool BALL = (F & FAM_BALL) != 0;
   constexpr bool VN = (F & FAM_VN) != 0;
-  R rhs[AX][NC];
 #pragma unroll
   for (int a = 0; a < AX; ++a) {
 #pragma unroll
@@ -101,9 +102,17 @@ __device__ __forceinline__ void local_step(const SegConst<R> &sc, const R (&wS)[
       }
     }
   }
-#pragma unroll
-  for (int a = 0; a < AX; ++a) apply_g(sc.G, rhs[a], ch[a]);
-  // projections and their duals with the new coefficients (Eq. 18d-g)
+}
+
+// Projections and their duals with the new coefficients (Eq. 18d-g) for the
+// box / ball / velocity-norm families (the second half of the local step).
+template <class R, int F>
+__device__ __forceinline__ void family_update(const SegConst<R> &sc, bool first_iter, R *ybox, R *qball, R *qvn,
+                                              int stride, const R *tabB, const R *tabQ, const R *tabV, int Mb,
+                                              int Mq, int Mv, const R (&ch)[AX][NC]) {
+  constexpr bool BOX = (F & FAM_BOX) != 0;
+  constexpr bool BALL = (F & FAM_BALL) != 0;
+  constexpr bool VN = (F & FAM_VN) != 0;
   if (BOX) {
     for (int j = 0; j < Mb; ++j) {
 #pragma unroll
@@ -158,6 +167,98 @@ __device__ __forceinline__ void local_step(const SegConst<R> &sc, const R (&wS)[
         const R wprev = first_iter ? R(0) : qv[a] - ph[a];
         qvn[(j * 3 + a) * stride] = vel[a] + wprev;
       }
+    }
+  }
+}
+
+// The closed-form local step of Eq. 18a with the box / ball / velocity-norm
+// families (Eq. 18d-g): right-hand side, ch = G rhs per axis, projections.
+template <class R, int F, bool FS = false>
+__device__ __forceinline__ void local_step(const SegConst<R> &sc, const R (&wS)[AX][ND], const R (&wE)[AX][ND],
+                                           R rho, bool first_iter, R *ybox, R *qball, R *qvn, int stride,
+                                           const R *tabB, const R *tabQ, const R *tabV, int Mb, int Mq, int Mv,
+                                           R (&ch)[AX][NC]) {
+  R rhs[AX][NC];
+  family_rhs<R, F, FS>(sc, wS, wE, rho, first_iter, ybox, qball, qvn, stride, tabB, tabQ, tabV, Mb, Mq, Mv, rhs);
+#pragma unroll
+  for (int a = 0; a < AX; ++a) apply_g(sc.G, rhs[a], ch[a]);
+  family_update<R, F>(sc, first_iter, ybox, qball, qvn, stride, tabB, tabQ, tabV, Mb, Mq, Mv, ch);
+}
+
+// ---- polytope family (FAM_POLY; streaming form) ----
+// Data of segment g in the layout of PolyData: PN[(f * 3 + a) * S + g],
+// PH[f * S + g], PU[(a * 3 + b) * S + g], PG[(b * 36 + q) * S + g]; the
+// compressed slack / dual y of row (j, f) at ypoly[(j * F + f) * stride].
+
+// rhs_a += rho sum_j tau_j^k sum_f n_f[a] (h_f - |y_jf|)   (A°^T (b - s - v), Eq. 18a)
+template <class R>
+__device__ __forceinline__ void poly_rhs(const R *PN, const R *PH, size_t S, size_t g, int F, int M, R rho,
+                                         const R *ypoly, int stride, const R *tabP, R (&rhs)[AX][NC]) {
+  for (int j = 0; j < M; ++j) {
+    R w[3] = {R(0), R(0), R(0)};
+    for (int f = 0; f < F; ++f) {
+      const R c = PH[(size_t)f * S + g] - rabs(ypoly[(j * F + f) * stride]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) w[a] += PN[(size_t)(f * 3 + a) * S + g] * c;
+    }
+#pragma unroll
+    for (int a = 0; a < AX; ++a) {
+      const R coef = rho * w[a];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) rhs[a][q] += coef * tabP[j * 8 + q];
+    }
+  }
+}
+
+// ch = U blockdiag(G_b) U^T rhs: rotate the axes into the eigenbasis of
+// sum_f n_f n_f^T, one packed 8x8 inverse per rotated axis, rotate back
+template <class R>
+__device__ __forceinline__ void poly_solve(const R *PG, const R *PU, size_t S, size_t g, const R (&rhs)[AX][NC],
+                                           R (&ch)[AX][NC]) {
+  R U[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) U[a][b] = PU[(size_t)(a * 3 + b) * S + g];
+#pragma unroll
+  for (int a = 0; a < AX; ++a)
+#pragma unroll
+    for (int q = 0; q < NC; ++q) ch[a][q] = R(0);
+#pragma unroll 1
+  for (int b = 0; b < 3; ++b) {
+    R rt[NC], ct[NC], Gb[NG];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) rt[q] = U[0][b] * rhs[0][q] + U[1][b] * rhs[1][q] + U[2][b] * rhs[2][q];
+#pragma unroll
+    for (int q = 0; q < NG; ++q) Gb[q] = PG[(size_t)(b * NG + q) * S + g];
+    apply_g(Gb, rt, ct);
+#pragma unroll
+    for (int a = 0; a < AX; ++a)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) ch[a][q] += U[a][b] * ct[q];
+  }
+}
+
+// y_jf <- n_f . p(t_j) - h_f + max(0, y_jf): the slack projection and dual
+// update of Eq. 18d-e in the compressed form (s = max(0, -y), v = max(0, y))
+template <class R>
+__device__ __forceinline__ void poly_update(const R *PN, const R *PH, size_t S, size_t g, int F, int M, R *ypoly,
+                                            int stride, const R *tabP, const R (&ch)[AX][NC]) {
+  for (int j = 0; j < M; ++j) {
+    R pos[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      R acc = R(0);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) acc += tabP[j * 8 + q] * ch[a][q];
+      pos[a] = acc;
+    }
+    for (int f = 0; f < F; ++f) {
+      R v = R(0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) v += PN[(size_t)(f * 3 + a) * S + g] * pos[a];
+      R *y = &ypoly[(j * F + f) * stride];
+      *y = v - PH[(size_t)f * S + g] + rmax0(*y);
     }
   }
 }

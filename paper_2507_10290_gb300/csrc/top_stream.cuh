@@ -2,7 +2,8 @@
 // CTA's shared memory holds: all iteration state in global memory, one launch
 // per phase of each iteration (Algorithm 1, Eq. 18a-g, 19-21):
 //   stream_local     every segment: local step + projections (shared
-//                    local_step), end derivatives to global memory
+//                    local_step; polytope rows through the rotated per-axis
+//                    inverses), end derivatives to global memory
 //   stream_junction  every segment's end junction: consensus average, scaled
 //                    duals, primal-residual share, consensus change
 //   stream_reduce    on check iterations: dual-residual shares, then one block
@@ -75,6 +76,8 @@ __global__ void stream_init(const StreamArgs A) {
     if (BOX) for (int q = 0; q < 6 * p.M_box; ++q) ybox[(size_t)q * A.S + g] = R(0);
     if (BALL) for (int q = 0; q < 3 * p.M_ball; ++q) qball[(size_t)q * A.S + g] = R(0);
     if (VN) for (int q = 0; q < 3 * p.M_vn; ++q) qvn[(size_t)q * A.S + g] = R(0);
+    if (F & FAM_POLY)
+      for (int q = 0; q < p.F_poly * p.M_poly; ++q) ((R *)A.ypoly)[(size_t)q * A.S + g] = R(0);
     if (F & FAM_GEN) {
       for (int q = 0; q < 2 * p.M_gen; ++q) ((R *)A.ygen)[(size_t)q * A.S + g] = R(0);
       if (A.inner_iters) A.inner_iters[g] = 0;
@@ -106,6 +109,10 @@ __global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
     fill_sample_table(tabGV, Mg, 1, threadIdx.x, blockDim.x);
     fill_accel_table(tabGA, Mg, threadIdx.x, blockDim.x);
   }
+  constexpr bool POLY = (F & FAM_POLY) != 0;
+  const int Mp = POLY ? p.M_poly : 0, Fp = POLY ? p.F_poly : 0;
+  R *tabP = tabGA + 8 * Mg;
+  if (POLY) fill_sample_table(tabP, Mp, 0, threadIdx.x, blockDim.x);
   __syncthreads();
   const R *z = (const R *)A.z, *uL = (const R *)A.uL, *uRp = (const R *)A.uRp, *uR0 = (const R *)A.uR0;
   const R *Gp = (const R *)A.G;
@@ -119,8 +126,10 @@ __global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
     const bool first = i == 0, last = i == N - 1;
     const int jS = g + b, jE = g + b + 1;
     SegConst<R> sc;
+    if (!POLY) {  // the polytope family keeps its per-axis inverses in A.poly
 #pragma unroll
-    for (int q = 0; q < NG; ++q) sc.G[q] = Gp[(size_t)q * A.S + g];
+      for (int q = 0; q < NG; ++q) sc.G[q] = Gp[(size_t)q * A.S + g];
+    }
     inv_powers(R(p.durations[g]), sc.s);
     sc.vbox = BOX ? R(p.vbox[b]) : R(0);
     sc.vnorm = VN ? R(p.vnorm[b]) : R(0);
@@ -154,8 +163,20 @@ __global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
           wS[a][r] = sc.s[r] * w[a][0][r];
           wE[a][r] = sc.s[r] * w[a][1][r];
         }
-      local_step<R, F & 7>(sc, wS, wE, rho, k == 0, (R *)A.ybox + g, (R *)A.qball + g, (R *)A.qvn + g, A.S,
-                           tabB, tabQ, tabV, Mb, Mq, Mv, ch);
+      if (POLY) {
+        const R *PN = (const R *)A.poly.N, *PH = (const R *)A.poly.H;
+        R rhs[AX][NC];
+        family_rhs<R, F & 7>(sc, wS, wE, rho, k == 0, (R *)A.ybox + g, (R *)A.qball + g, (R *)A.qvn + g, A.S,
+                             tabB, tabQ, tabV, Mb, Mq, Mv, rhs);
+        poly_rhs(PN, PH, (size_t)A.S, (size_t)g, Fp, Mp, rho, (const R *)A.ypoly + g, A.S, tabP, rhs);
+        poly_solve((const R *)A.poly.G, (const R *)A.poly.U, (size_t)A.S, (size_t)g, rhs, ch);
+        family_update<R, F & 7>(sc, k == 0, (R *)A.ybox + g, (R *)A.qball + g, (R *)A.qvn + g, A.S, tabB, tabQ,
+                                tabV, Mb, Mq, Mv, ch);
+        poly_update(PN, PH, (size_t)A.S, (size_t)g, Fp, Mp, (R *)A.ypoly + g, A.S, tabP, ch);
+      } else {
+        local_step<R, F & 7>(sc, wS, wE, rho, k == 0, (R *)A.ybox + g, (R *)A.qball + g, (R *)A.qvn + g, A.S,
+                             tabB, tabQ, tabV, Mb, Mq, Mv, ch);
+      }
     }
 #pragma unroll
     for (int a = 0; a < AX; ++a) {
@@ -402,7 +423,8 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
   const int Mb = (fam & FAM_BOX) ? p.M_box : 0, Mq = (fam & FAM_BALL) ? p.M_ball : 0,
             Mv = (fam & FAM_VN) ? p.M_vn : 0;
   const int Mg = (fam & FAM_GEN) ? p.M_gen : 0;
-  const size_t tab_bytes = sizeof(R) * 8 * (size_t)(Mb + Mq + Mv + 2 * Mg);
+  const int Mp = (fam & FAM_POLY) ? p.M_poly : 0;
+  const size_t tab_bytes = sizeof(R) * 8 * (size_t)(Mb + Mq + Mv + 2 * Mg + Mp);
   void (*init)(const StreamArgs) = nullptr;
   void (*local)(const StreamArgs, int) = nullptr;
   void (*rescale)(const StreamArgs) = nullptr;
@@ -411,6 +433,8 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
   case FV: init = stream_init<R, FV>; local = stream_local<R, FV>; rescale = stream_rescale<R, FV>; break;
     TOP_ST_CASE(0) TOP_ST_CASE(1) TOP_ST_CASE(2) TOP_ST_CASE(3)
     TOP_ST_CASE(4) TOP_ST_CASE(5) TOP_ST_CASE(6) TOP_ST_CASE(7) TOP_ST_CASE(8)
+    TOP_ST_CASE(16) TOP_ST_CASE(17) TOP_ST_CASE(18) TOP_ST_CASE(19)
+    TOP_ST_CASE(20) TOP_ST_CASE(21) TOP_ST_CASE(22) TOP_ST_CASE(23)
 #undef TOP_ST_CASE
     default: return (int)cudaErrorInvalidValue;
   }

@@ -72,7 +72,8 @@ class top_problem(C.Structure):
                 ("M_gen", C.c_int32), ("gen_vmax", C.c_void_p), ("gen_amax", C.c_void_p),
                 ("lbfgs_mem", C.c_int32), ("lbfgs_max_iters", C.c_int32), ("lbfgs_tol", C.c_double),
                 ("adaptive_rho", C.c_int32), ("rho_mu", C.c_double), ("rho_tau_incr", C.c_double),
-                ("rho_tau_decr", C.c_double)]
+                ("rho_tau_decr", C.c_double),
+                ("M_poly", C.c_int32), ("F_poly", C.c_int32), ("poly_n", C.c_void_p), ("poly_h", C.c_void_p)]
 
 
 class top_result(C.Structure):
@@ -209,6 +210,7 @@ class Solver:
             "vbox": t(getattr(w, "vbox", None)), "ball_c": t(getattr(w, "ball_c", None)),
             "ball_r": t(getattr(w, "ball_r", None)), "vnorm": t(getattr(w, "vnorm", None)),
             "gen_vmax": t(getattr(w, "gen_vmax", None)), "gen_amax": t(getattr(w, "gen_amax", None)),
+            "poly_n": t(getattr(w, "poly_n", None)), "poly_h": t(getattr(w, "poly_h", None)),
         }
 
     def make_problem(self, w, tensors, memory=TOP_MEM_DEVICE, max_iters=None, eps=None, check_every=1):
@@ -216,7 +218,7 @@ class Solver:
         pb.B = int(np.asarray(w.seg_offset).shape[0] - 1)
         pb.memory = memory
         for k in ("seg_offset", "waypoints", "durations", "start_state", "end_state", "vbox", "ball_c",
-                  "ball_r", "vnorm", "gen_vmax", "gen_amax"):
+                  "ball_r", "vnorm", "gen_vmax", "gen_amax", "poly_n", "poly_h"):
             x = tensors.get(k)
             if x is None:
                 setattr(pb, k, None)
@@ -241,6 +243,8 @@ class Solver:
         pb.rho_mu = float(getattr(w, "rho_mu", 0.0) or 0.0)
         pb.rho_tau_incr = float(getattr(w, "rho_tau_incr", 0.0) or 0.0)
         pb.rho_tau_decr = float(getattr(w, "rho_tau_decr", 0.0) or 0.0)
+        pb.M_poly = int(getattr(w, "M_poly", 0) or 0)
+        pb.F_poly = int(getattr(w, "F_poly", 0) or 0)
         return pb
 
     def alloc_result(self, B: int, S: int, max_iters: int = 0, history: bool = False, device="cuda"):
@@ -316,7 +320,7 @@ class Solver:
                 "start_state": np.ascontiguousarray(w.start_state, dtype=np.float64),
                 "end_state": np.ascontiguousarray(w.end_state, dtype=np.float64),
             }
-            for k in ("vbox", "ball_c", "ball_r", "vnorm", "gen_vmax", "gen_amax"):
+            for k in ("vbox", "ball_c", "ball_r", "vnorm", "gen_vmax", "gen_amax", "poly_n", "poly_h"):
                 x = getattr(w, k, None)
                 arrays[k] = None if x is None else np.ascontiguousarray(x, dtype=np.float64)
         if out is None:
