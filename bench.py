@@ -445,8 +445,15 @@ def run_suite(args):
                  precs=("fp32", "fp64"))
     if want("general"):
         gpu_case("general (N=1000, numerical step)", W.general(N=1000), tol_eps=1e-4)
+    if want("polytope"):
+        gpu_case("polytope corridor (N=1024, F=8 faces at M=8, box rows at M=16; streaming)",
+                 W.polytope_corridor(), tol_eps=1e-4)
     if want("speed"):
         speed_bound_comparison(top, oracle)
+    if want("segments"):
+        segment_count_line(top, oracle)
+    if want("timealloc"):
+        time_alloc_line(top)
     if want("grad"):
         grad_line(top, oracle)
     if want("general_full"):
@@ -501,6 +508,68 @@ def speed_bound_comparison(top, oracle):
     sc = W.speed_limit(N=N).durations[:, None, None] ** np.arange(8)
     a, b = sols[("closed", "fp64")], sols[("numeric", "fp64")]
     line["fp64_closed_vs_numeric_coeff_rel_diff"] = float(np.linalg.norm((a - b) * sc) / np.linalg.norm(a * sc))
+    print(json.dumps(line), flush=True)
+
+
+def segment_count_line(top, oracle, Ns=(16, 64, 256, 1024, 4096, 16384), iters=3000, M=8192):
+    """The segment-count experiment (Sec. IV-A.2): N + 1 points of a
+    parameterized curve (trefoil), PIN, 3000 iterations; GPU time and the
+    similarity e_simi = lg sum_m |p_m - p_m^ref| over 8192 uniform samples
+    (top_sample), with fixed rho = 1 and with residual balancing (Eq. 22)."""
+    import torch
+    rows = []
+    for N in Ns:
+        row = {"N": N}
+        for tag, adapt in (("fixed_rho", False), ("adaptive_rho", True)):
+            w = W.curve(N=N, max_iters=iters).with_(adaptive_rho=adapt)
+            s = top.Solver(max_batch=1, max_segments=N, precision="fp32", max_samples=0)
+            tensors = s.device_inputs(w)
+            out = s.alloc_result(1, N, iters)
+            s.solve(w, tensors=tensors, out=out, max_iters=5)
+            ms = _timed_solve(s, w, tensors, out)
+            samp = s.sample(w, out["coeffs"], M, 0, tensors=tensors).cpu().numpy()[0]
+            ref = W.trefoil(np.linspace(0.0, 1.0, M), 0, w.notes["scale"])
+            e = float(np.log10(np.linalg.norm(samp - ref, axis=1).sum()))
+            row[tag] = {"ms": ms, "us_per_iteration": 1000 * ms / iters, "e_simi": e,
+                        "r_primal": float(out["r_primal"][0]), "r_dual": float(out["r_dual"][0]),
+                        "rho_final": float(out["rho"][0])}
+            if N <= 64:  # the oracle's coefficients through the same sampling, for parity of the metric
+                o = oracle.solve(w)
+                so = s.sample(w, torch.as_tensor(o["coeffs"], device="cuda"), M, 0, tensors=tensors)
+                row[tag]["e_simi_oracle_fp64"] = float(np.log10(np.linalg.norm(so.cpu().numpy()[0] - ref,
+                                                                               axis=1).sum()))
+            s.close()
+        rows.append(row)
+    print(json.dumps({"suite": "segment count on a parameterized curve (Sec. IV-A.2)",
+                      "workload": f"trefoil, PIN through N+1 uniform points, T_i = 0.5 s, {iters} iterations, "
+                                  f"FP32, e_simi over {M} samples", "rows": rows}), flush=True)
+
+
+def time_alloc_line(top, N=64, steps=100):
+    """Outer time allocation (top_time_alloc) on one PIN trajectory: wall time
+    per outer step (one top_grad through 1000 iterations and one update) and
+    the objective before and after."""
+    import torch
+    w0 = W.tiny(seed=4, N=[N], mode="pin", T_range=(1.6, 2.4), step=2.0)
+    w = w0.with_(durations=1.4 * w0.durations, max_iters=1000, rho=10.0)
+    kT = 40.0
+    line = {"suite": "outer time allocation (top_time_alloc)", "segments": N, "k_T": kT, "steps": steps,
+            "inner_iterations": 1000}
+    for prec in ("fp32", "fp64"):
+        s = top.Solver(max_batch=1, max_segments=N, precision=prec, max_samples=0)
+        tensors = s.device_inputs(w)
+        before = s.solve(w, tensors=tensors)
+        F0 = float(before["cost"][0]) + kT * float(w.durations.sum())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Tout, out = s.time_alloc(w, k_T=kT, lr=0.3 / (8 * kT * float(w.durations.mean())), steps=steps,
+                                 tensors=tensors)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        F1 = float(out["cost"][0]) + kT * float(Tout.sum())
+        line[prec] = {"seconds": dt, "ms_per_outer_step": 1000 * dt / steps, "F_before": F0, "F_after": F1,
+                      "total_time_before": float(w.durations.sum()), "total_time_after": float(Tout.sum())}
+        s.close()
     print(json.dumps(line), flush=True)
 
 
@@ -591,7 +660,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tolerance", action="store_true", help="skip the time-to-tolerance measurement")
     ap.add_argument("--only", default="", help="with --suite: comma-separated subset of single_box, corridor, "
-                    "batch, adaptive, general, speed, grad, general_full")
+                    "batch, adaptive, general, polytope, speed, segments, timealloc, grad, general_full")
     ap.add_argument("--suite", action="store_true",
                     help="one JSON line per benchmark workload (single_box, corridor, batch, grad_batch, general)")
     ap.add_argument("--trajectories", type=int, default=4096,

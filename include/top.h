@@ -178,6 +178,32 @@ int top_solve(top_handle *h, const top_problem *pb, top_result *res, void *strea
 int top_grad(top_handle *h, const top_problem *pb, const double *dJ, double *dwaypoints,
              double *ddurations, void *stream);
 
+/* Sample trajectories: for each trajectory b, the derivative of order
+ * `order` (0 = position .. 3 = jerk) of the piecewise polynomial given by
+ * `coeffs` ([S][3][8], the layout of top_result.coeffs) at the M times
+ * t_m = m T_b / (M - 1), m = 0..M-1, T_b the trajectory's total duration
+ * (Sec. III-D.1: sigma_i(t) = c_i^T beta(t - t_{i-1}); at a junction the
+ * later segment is used).  Only B, memory, seg_offset and durations of `pb`
+ * are read.  out: [B][M][3]; coeffs and out in the memory kind of `pb`.
+ * An empty trajectory gets zeros.  The paper evaluates its similarity metric
+ * e_simi on such samples (Sec. IV-A.2, M = 8192).
+ * Errors: TOP_E_INVAL (M < 2, order outside 0..3, bad offsets), TOP_E_NOMEM
+ * (B or S above the handle's capacity), TOP_E_CUDA. */
+int top_sample(top_handle *h, const top_problem *pb, const double *coeffs, int32_t M, int32_t order, double *out,
+               void *stream);
+
+/* Outer time allocation (an extension: the paper takes the durations as
+ * given).  Minimises F(T) = sum_b J_b(T) + k_T sum_i T_i over the durations,
+ * J_b the cost after pb->max_iters iterations as in top_grad, by `steps`
+ * gradient steps in log T:  T_i <- T_i exp(-clamp(lr T_i dF/dT_i, -0.5, 0.5)),
+ * dF/dT_i = dJ/dT_i + k_T from top_grad.  durations_io: [S] initial durations
+ * in, final durations out; pb->durations is not read.  res (may be NULL) gets
+ * a top_solve with the final durations.  Same restrictions as top_grad
+ * (closed-form step, no inequality families, fixed rho).  Memory kind of pb.
+ * Errors: as top_grad; TOP_E_INVAL for k_T < 0, lr <= 0 or steps < 0. */
+int top_time_alloc(top_handle *h, const top_problem *pb, double k_T, double lr, int32_t steps,
+                   double *durations_io, top_result *res, void *stream);
+
 /* Kernel timing.  With profiling enabled, top_solve records CUDA events on
  * the launching stream around each kernel it launches; top_kernel_times then
  * returns, for the last top_solve, ms[0] = local-matrix precompute, ms[1] =

@@ -30,6 +30,8 @@ struct top_handle {
   size_t P_bytes = 0;
   unsigned char *d_pstage = nullptr;  // staging of host polytope arrays
   size_t pstage_bytes = 0;
+  unsigned char *d_aux = nullptr;     // top_sample / top_time_alloc workspace (grow-only)
+  size_t aux_bytes = 0;
   Pack *d_packs = nullptr;    // [max_segments]
   int *d_err = nullptr;       // error flag of the precompute kernel
   // staging for TOP_MEM_HOST problems
@@ -314,6 +316,7 @@ void top_destroy(top_handle *h) {
   cudaFree(h->E);
   cudaFree(h->P);
   cudaFree(h->d_pstage);
+  cudaFree(h->d_aux);
   cudaFree(h->d_packs);
   cudaFree(h->d_err);
   cudaFree(h->d_stage);
@@ -810,6 +813,140 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
   TOP_CUDA(h, cudaStreamSynchronize(st));
   if (*h->h_err & 1) return TOP_E_INVAL;
   if (*h->h_err & 2) return TOP_E_NUMERIC;
+  return TOP_OK;
+}
+
+int top_sample(top_handle *h, const top_problem *pb, const double *coeffs, int32_t M, int32_t order, double *out,
+               void *stream) {
+  if (!h || !pb || !coeffs || !out || M < 2 || order < 0 || order > 3) return TOP_E_INVAL;
+  if (pb->B < 0 || (pb->memory != TOP_MEM_DEVICE && pb->memory != TOP_MEM_HOST)) return TOP_E_INVAL;
+  if (pb->B > h->cfg.max_batch) return TOP_E_NOMEM;
+  const int B = pb->B;
+  if (B == 0) return TOP_OK;
+  if (!pb->seg_offset) return TOP_E_INVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  TOP_CUDA(h, cudaSetDevice(h->device));
+  const bool host = pb->memory == TOP_MEM_HOST;
+  if (host) {
+    std::memcpy(h->h_off, pb->seg_offset, sizeof(int32_t) * (B + 1));
+  } else {
+    TOP_CUDA(h, cudaMemcpyAsync(h->h_off, pb->seg_offset, sizeof(int32_t) * (B + 1), cudaMemcpyDeviceToHost, st));
+    TOP_CUDA(h, cudaStreamSynchronize(st));
+  }
+  const int32_t *off = h->h_off;
+  if (off[0] != 0) return TOP_E_INVAL;
+  for (int b = 0; b < B; ++b)
+    if (off[b + 1] < off[b]) return TOP_E_INVAL;
+  const int S = off[B];
+  if (S > h->cfg.max_segments) return TOP_E_NOMEM;
+  if (S > 0 && !pb->durations) return TOP_E_INVAL;
+  // workspace: start times, totals, and for host memory the staged inputs and samples
+  const size_t b_ts = align_up(sizeof(double) * (size_t)S + 8, 256), b_tt = align_up(sizeof(double) * B, 256);
+  const size_t b_off = align_up(sizeof(int32_t) * (B + 1), 256), b_T = align_up(sizeof(double) * (size_t)S + 8, 256);
+  const size_t b_c = align_up(sizeof(double) * 24 * (size_t)S + 8, 256);
+  const size_t b_out = align_up(sizeof(double) * 3 * (size_t)B * M, 256);
+  const size_t want = b_ts + b_tt + (host ? b_off + b_T + b_c + b_out : 0);
+  cudaError_t ge = grow((void **)&h->d_aux, &h->aux_bytes, want);
+  if (ge != cudaSuccess) return ge == cudaErrorMemoryAllocation ? TOP_E_NOMEM : cuda_fail(h, ge);
+  unsigned char *base = h->d_aux;
+  double *tstart = (double *)base, *ttot = (double *)(base + b_ts);
+  const int32_t *d_off = pb->seg_offset;
+  const double *d_T = pb->durations, *d_c = coeffs;
+  double *d_out = out;
+  if (host) {
+    unsigned char *p = base + b_ts + b_tt;
+    TOP_CUDA(h, cudaMemcpyAsync(p, pb->seg_offset, sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, st));
+    d_off = (const int32_t *)p;
+    p += b_off;
+    if (S > 0) TOP_CUDA(h, cudaMemcpyAsync(p, pb->durations, sizeof(double) * S, cudaMemcpyHostToDevice, st));
+    d_T = (const double *)p;
+    p += b_T;
+    if (S > 0) TOP_CUDA(h, cudaMemcpyAsync(p, coeffs, sizeof(double) * 24 * (size_t)S, cudaMemcpyHostToDevice, st));
+    d_c = (const double *)p;
+    p += b_c;
+    d_out = (double *)p;
+  }
+  int e = launch_sample(d_off, d_T, B, M, order, d_c, tstart, ttot, d_out, st);
+  if (e) return cuda_fail(h, (cudaError_t)e);
+  if (host)
+    TOP_CUDA(h, cudaMemcpyAsync(out, d_out, sizeof(double) * 3 * (size_t)B * M, cudaMemcpyDeviceToHost, st));
+  TOP_CUDA(h, cudaStreamSynchronize(st));
+  return TOP_OK;
+}
+
+int top_time_alloc(top_handle *h, const top_problem *pb_in, double k_T, double lr, int32_t steps,
+                   double *durations_io, top_result *res, void *stream) {
+  if (!h || !pb_in || !durations_io) return TOP_E_INVAL;
+  if (!(k_T >= 0.0) || !(lr > 0.0) || steps < 0) return TOP_E_INVAL;
+  if (pb_in->M_box || pb_in->M_ball || pb_in->M_vn || pb_in->M_gen || pb_in->M_poly || pb_in->adaptive_rho ||
+      pb_in->inner != TOP_CLOSED_FORM)
+    return TOP_E_NOTSUP;
+  if (pb_in->B < 0 || pb_in->B > h->cfg.max_batch) return pb_in->B < 0 ? TOP_E_INVAL : TOP_E_NOMEM;
+  const int B = pb_in->B;
+  if (B == 0) return TOP_OK;
+  if (!pb_in->seg_offset || !pb_in->waypoints || !pb_in->start_state || !pb_in->end_state) return TOP_E_INVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  TOP_CUDA(h, cudaSetDevice(h->device));
+  const bool host = pb_in->memory == TOP_MEM_HOST;
+  if (host) {
+    std::memcpy(h->h_off, pb_in->seg_offset, sizeof(int32_t) * (B + 1));
+  } else {
+    TOP_CUDA(h, cudaMemcpyAsync(h->h_off, pb_in->seg_offset, sizeof(int32_t) * (B + 1), cudaMemcpyDeviceToHost, st));
+    TOP_CUDA(h, cudaStreamSynchronize(st));
+  }
+  const int32_t *off = h->h_off;
+  if (off[0] != 0) return TOP_E_INVAL;
+  for (int b = 0; b < B; ++b)
+    if (off[b + 1] < off[b]) return TOP_E_INVAL;
+  const int S = off[B];
+  if (S > h->cfg.max_segments) return TOP_E_NOMEM;
+  const size_t Jn = (size_t)S + B;
+  // workspace: durations, their gradient, dJ = 1, the waypoint-gradient scratch,
+  // and for host problems device copies of the inputs
+  const size_t bS = align_up(sizeof(double) * (size_t)S + 8, 256), bB = align_up(sizeof(double) * B, 256);
+  const size_t bW = align_up(sizeof(double) * 3 * Jn, 256), bOff = align_up(sizeof(int32_t) * (B + 1), 256);
+  const size_t bSt = align_up(sizeof(double) * 12 * B, 256);
+  const size_t want = 2 * bS + bB + bW + (host ? bOff + bW + 2 * bSt : 0);
+  cudaError_t ge = grow((void **)&h->d_aux, &h->aux_bytes, want);
+  if (ge != cudaSuccess) return ge == cudaErrorMemoryAllocation ? TOP_E_NOMEM : cuda_fail(h, ge);
+  unsigned char *p = h->d_aux;
+  double *dT_cur = (double *)p; p += bS;
+  double *dT_grad = (double *)p; p += bS;
+  double *d_ones = (double *)p; p += bB;
+  double *d_wgrad = (double *)p; p += bW;
+  top_problem pbd = *pb_in;
+  pbd.memory = TOP_MEM_DEVICE;
+  if (host) {
+    TOP_CUDA(h, cudaMemcpyAsync(p, pb_in->seg_offset, sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, st));
+    pbd.seg_offset = (const int32_t *)p; p += bOff;
+    TOP_CUDA(h, cudaMemcpyAsync(p, pb_in->waypoints, sizeof(double) * 3 * Jn, cudaMemcpyHostToDevice, st));
+    pbd.waypoints = (const double *)p; p += bW;
+    TOP_CUDA(h, cudaMemcpyAsync(p, pb_in->start_state, sizeof(double) * 12 * B, cudaMemcpyHostToDevice, st));
+    pbd.start_state = (const double *)p; p += bSt;
+    TOP_CUDA(h, cudaMemcpyAsync(p, pb_in->end_state, sizeof(double) * 12 * B, cudaMemcpyHostToDevice, st));
+    pbd.end_state = (const double *)p; p += bSt;
+  }
+  if (S > 0)
+    TOP_CUDA(h, cudaMemcpyAsync(dT_cur, durations_io, sizeof(double) * S,
+                                host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  int e = launch_fill(d_ones, B, 1.0, st);
+  if (e) return cuda_fail(h, (cudaError_t)e);
+  pbd.durations = dT_cur;
+  for (int it = 0; it < steps; ++it) {
+    int rc = top_grad(h, &pbd, d_ones, d_wgrad, dT_grad, stream);
+    if (rc != TOP_OK) return rc;
+    e = launch_time_step(dT_cur, dT_grad, S, k_T, lr, st);
+    if (e) return cuda_fail(h, (cudaError_t)e);
+  }
+  if (S > 0)
+    TOP_CUDA(h, cudaMemcpyAsync(durations_io, dT_cur, sizeof(double) * S,
+                                host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  TOP_CUDA(h, cudaStreamSynchronize(st));
+  if (res) {
+    top_problem pbs = *pb_in;  // the caller's memory kind, the final durations
+    pbs.durations = durations_io;
+    return top_solve(h, &pbs, res, stream);
+  }
   return TOP_OK;
 }
 

@@ -149,6 +149,9 @@ int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_
 int launch_keig(const DevProblem &p, void *E32, void *E64, int *err_flag, void *stream);
 int launch_kinv_poly(const DevProblem &p, double rho, bool fp64, const PolyData &out, int *err_flag, void *stream);
 int launch_fill(double *x, int n, double v, void *stream);
+int launch_sample(const int32_t *off, const double *T, int B, int M, int order, const double *coeffs,
+                  double *tstart, double *ttot, double *out, void *stream);
+int launch_time_step(double *T, const double *dT, int S, double kT, double lr, void *stream);
 int launch_resident_f32(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
 int launch_resident_f64(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
 int launch_stream_f32(const StreamArgs &a, int fam, void *stream);

@@ -97,6 +97,12 @@ _lib.top_last_cuda_error.argtypes = [C.c_void_p]
 _lib.top_last_cuda_error.restype = C.c_int
 _lib.top_solve_noalloc.argtypes = [C.POINTER(top_problem), C.POINTER(top_result), C.c_int, C.c_void_p]
 _lib.top_solve_noalloc.restype = C.c_int
+_lib.top_sample.argtypes = [C.c_void_p, C.POINTER(top_problem), C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                            C.c_void_p]
+_lib.top_sample.restype = C.c_int
+_lib.top_time_alloc.argtypes = [C.c_void_p, C.POINTER(top_problem), C.c_double, C.c_double, C.c_int32, C.c_void_p,
+                                C.c_void_p, C.c_void_p]
+_lib.top_time_alloc.restype = C.c_int
 _lib.top_set_profiling.argtypes = [C.c_void_p, C.c_int]
 _lib.top_set_profiling.restype = C.c_int
 _lib.top_kernel_times.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int]
@@ -135,6 +141,22 @@ def top_solve_noalloc(problem: top_problem, result: top_result, precision: int, 
     """int top_solve_noalloc(const top_problem*, top_result*, int precision, void* stream):
     the solve for callers that cannot allocate device memory (fixed scratch, no handle)."""
     return _lib.top_solve_noalloc(C.byref(problem), C.byref(result), int(precision), C.c_void_p(stream))
+
+
+def top_sample(handle, problem: top_problem, coeffs: int, M: int, order: int, out: int, stream: int = 0) -> int:
+    """int top_sample(top_handle*, const top_problem*, const double* coeffs, int M, int order, double* out,
+    void* stream): trajectories sampled at M uniform times."""
+    return _lib.top_sample(handle, C.byref(problem), C.c_void_p(coeffs), int(M), int(order), C.c_void_p(out),
+                           C.c_void_p(stream))
+
+
+def top_time_alloc(handle, problem: top_problem, k_T: float, lr: float, steps: int, durations_io: int,
+                   result, stream: int = 0) -> int:
+    """int top_time_alloc(top_handle*, const top_problem*, double k_T, double lr, int steps,
+    double* durations_io, top_result* res, void* stream): outer time allocation."""
+    return _lib.top_time_alloc(handle, C.byref(problem), float(k_T), float(lr), int(steps),
+                               C.c_void_p(durations_io), None if result is None else C.byref(result),
+                               C.c_void_p(stream))
 
 
 def top_set_profiling(handle, enable: bool) -> int:
@@ -305,6 +327,39 @@ class Solver:
         if rc != TOP_OK:
             raise TopError(rc, "top_grad", top_last_cuda_error(self.handle))
         return dw, dT
+
+    def sample(self, w, coeffs, M: int, order: int = 0, tensors=None, stream=None):
+        """Every trajectory of w with coefficients `coeffs` ([S,3,8] device tensor)
+        sampled at M uniform times (top_sample); returns a [B, M, 3] device tensor."""
+        torch = self.torch
+        tensors = tensors if tensors is not None else self.device_inputs(w)
+        B = int(np.asarray(w.seg_offset).shape[0] - 1)
+        out = torch.empty((B, M, 3), dtype=torch.float64, device="cuda")
+        pb = self.make_problem(w, tensors, TOP_MEM_DEVICE)
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        rc = top_sample(self.handle, pb, coeffs.contiguous().data_ptr(), M, order, out.data_ptr(), s)
+        if rc != TOP_OK:
+            raise TopError(rc, "top_sample", top_last_cuda_error(self.handle))
+        return out
+
+    def time_alloc(self, w, k_T: float, lr: float, steps: int, max_iters=None, tensors=None, stream=None,
+                   result: bool = True):
+        """Outer time allocation (top_time_alloc): returns (durations [S] device
+        tensor, solve outputs with them or None)."""
+        torch = self.torch
+        tensors = tensors if tensors is not None else self.device_inputs(w)
+        B = int(np.asarray(w.seg_offset).shape[0] - 1)
+        S = int(np.asarray(w.seg_offset)[-1])
+        K = int(w.max_iters if max_iters is None else max_iters)
+        T = tensors["durations"].clone()
+        out = self.alloc_result(B, S, K) if result else None
+        pb = self.make_problem(w, tensors, TOP_MEM_DEVICE, max_iters=K, eps=0.0)
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        rc = top_time_alloc(self.handle, pb, k_T, lr, steps, T.data_ptr(),
+                            self.result_struct(out) if result else None, s)
+        if rc != TOP_OK:
+            raise TopError(rc, "top_time_alloc", top_last_cuda_error(self.handle))
+        return T, out
 
     def solve_host(self, w, history: bool = False, max_iters=None, eps=None, check_every: int = 1,
                    arrays=None, out=None, stream=None):

@@ -279,6 +279,46 @@ def polytope_corridor(seed: int = 0, N: int = 1024, F: int = 8, M: int = 8) -> W
     return with_polytopes(w, F=F, M=M, seed=seed).with_(name=f"polytope_corridor N={N} F={F} M={M}")
 
 
+def trefoil(s, order: int = 0, scale: float = 5.0) -> np.ndarray:
+    """Derivative `order` (0..3) with respect to s of the reference curve
+    r(s) = scale (sin 2 pi s + 2 sin 4 pi s, cos 2 pi s - 2 cos 4 pi s, -sin 6 pi s),
+    s in [0, 1]: a trefoil knot, the stand-in for the paper's parameterized
+    curve.  Returns [len(s), 3]."""
+    s = np.atleast_1d(np.asarray(s, dtype=np.float64))
+
+    def d(fn, w):  # order-th derivative of fn(w s), fn in {sin, cos}
+        ph = order * np.pi / 2.0
+        base = np.sin(w * s + ph) if fn == "sin" else np.cos(w * s + ph)
+        return w ** order * base
+
+    tp = 2.0 * np.pi
+    x = d("sin", tp) + 2.0 * d("sin", 2 * tp)
+    y = d("cos", tp) - 2.0 * d("cos", 2 * tp)
+    z = -d("sin", 3 * tp)
+    return scale * np.stack([x, y, z], axis=1)
+
+
+def curve(N: int = 256, T_total: Optional[float] = None, scale: float = 5.0, max_iters: int = 3000) -> Workload:
+    """The segment-count experiment (Sec. IV-A.2): N + 1 points sampled
+    uniformly in the parameter of the reference curve (trefoil), PIN waypoints
+    so the trajectory passes through them, uniform durations T_total / N
+    (default 0.5 s per segment, which keeps T^-r moderate at every N), and the
+    curve's own velocity, acceleration and jerk (time t = s T_total) as the
+    boundary states."""
+    if T_total is None:
+        T_total = 0.5 * N
+    sN = np.linspace(0.0, 1.0, N + 1)
+    P = trefoil(sN, 0, scale)
+    s = np.zeros((1, P_ORDER, 3))
+    e = np.zeros((1, P_ORDER, 3))
+    for r in range(P_ORDER):
+        s[0, r] = trefoil([0.0], r, scale)[0] / T_total ** r
+        e[0, r] = trefoil([1.0], r, scale)[0] / T_total ** r
+    return Workload(name=f"curve N={N}", seg_offset=np.array([0, N], np.int32), waypoints=P,
+                    durations=np.full(N, T_total / N), start_state=s, end_state=e, mode="pin", rho=1.0,
+                    max_iters=max_iters, notes={"T_total": T_total, "scale": scale})
+
+
 def speed_limit(seed: int = 0, N: int = 256, M: int = 16, inner: str = "closed", vmax_factor: float = 1.6,
                 max_iters: int = 200, vmax: Optional[float] = None) -> Workload:
     """1 trajectory, N segments, FREE waypoints, one speed bound ||v(t_ij)|| <= v_max
