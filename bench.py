@@ -405,11 +405,11 @@ def run_suite(args):
             s.solve(w, tensors=tensors, out=out)
             top.top_set_profiling(s.handle, True)
             ms = [_timed_solve(s, w, tensors, out) for _ in range(3)]
-            kt = top.top_kernel_times(s.handle)[1]
+            kt = top.top_kernel_times(s.handle, 4)[1]
             top.top_set_profiling(s.handle, False)
             g = {k: v.cpu().numpy() for k, v in out.items()}
             entry = {"ms": float(np.median(ms)), "us_per_iteration": 1000 * float(np.median(ms)) / w.max_iters,
-                     "kernel_ms": {"precompute": kt[0], "resident": kt[1], "streaming": kt[2]},
+                     "kernel_ms": {"precompute": kt[0], "resident": kt[1], "streaming": kt[2], "cluster": kt[3]},
                      "segment_iterations_per_s": w.S * w.max_iters / (float(np.median(ms)) / 1000),
                      "coeff_rel_err_vs_oracle": scaled_err(g["coeffs"], o["coeffs"], w.durations),
                      "cost_rel_err_vs_oracle": float(np.max(np.abs(g["cost"] - o["cost"]) / np.abs(o["cost"])))}

@@ -80,7 +80,11 @@ typedef struct top_config {
   int32_t max_batch;      /* largest B a call may pass */
   int32_t max_segments;   /* largest total segment count S a call may pass */
   int32_t max_samples;    /* largest M (samples per segment) of any constraint family */
-  int32_t schedule;       /* TOP_SCHED_AUTO picks per trajectory length; the others force one form */
+  int32_t schedule;       /* TOP_SCHED_AUTO: trajectories that fit one CTA run resident (packed),
+                             longer ones in a thread-block cluster of up to 16 CTAs with distributed
+                             shared memory (closed-form families, fixed rho), the rest streaming;
+                             TOP_SCHED_RESIDENT: resident only (longer: TOP_E_NOTSUP);
+                             TOP_SCHED_STREAM: streaming only */
   int32_t segs_per_cta;   /* resident-form capacity per CTA; 0 = chosen from shared-memory size */
   int32_t ckpt_interval;  /* adjoint checkpoint interval in iterations (0 = 10) */
   int32_t reserved[9];    /* must be zero */
@@ -207,9 +211,10 @@ int top_time_alloc(top_handle *h, const top_problem *pb, double k_T, double lr, 
 /* Kernel timing.  With profiling enabled, top_solve records CUDA events on
  * the launching stream around each kernel it launches; top_kernel_times then
  * returns, for the last top_solve, ms[0] = local-matrix precompute, ms[1] =
- * resident iteration kernel, ms[2] = streaming iteration kernels (0 for a
- * kernel that did not run), for up to n entries.  Returns the number of
- * entries written, or TOP_E_INVAL / TOP_E_STATE (profiling off). */
+ * resident iteration kernel, ms[2] = streaming iteration kernels, ms[3] =
+ * cluster-resident kernels (0 for a kernel that did not run), for up to n
+ * entries.  Returns the number of entries written, or TOP_E_INVAL /
+ * TOP_E_STATE (profiling off). */
 int top_set_profiling(top_handle *h, int enable);
 int top_kernel_times(const top_handle *h, float *ms, int n);
 

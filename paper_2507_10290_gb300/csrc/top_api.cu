@@ -54,8 +54,13 @@ struct top_handle {
   size_t stream_bytes = 0;
   // kernel timing (top_set_profiling)
   bool profiling = false;
-  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  bool ran[3] = {false, false, false};
+  cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool ran[4] = {false, false, false, false};
+  // cluster-resident form: trajectory lists (pinned host, device) and the cached
+  // largest co-schedulable cluster size for (C, family, precision)
+  int *h_ctraj = nullptr, *d_ctraj = nullptr;  // [max_batch]
+  int csz_key_C = -1, csz_key_fam = -1, csz_val = 0;
+  size_t csz_key_smem = 0;
 };
 
 namespace {
@@ -112,6 +117,20 @@ int resident_capacity(const top_handle *h, const top_problem *pb) {
   int cap = h->cfg.segs_per_cta > 0 ? std::min(512, h->cfg.segs_per_cta / 32 * 32) : 512;
   for (int C = cap; C >= 32; C -= 32) {
     ResLayout L = res_layout(C, C / 4, Mb, Mq, Mv, (int)rbytes(h));
+    if (L.total <= (size_t)h->smem_optin) return C;
+  }
+  return 0;
+}
+
+// per-CTA capacity of the cluster-resident form (one trajectory per cluster)
+int cluster_capacity(const top_handle *h, const top_problem *pb) {
+  const int fam = families(pb);
+  const int Mb = (fam & FAM_BOX) ? pb->M_box : 0;
+  const int Mq = (fam & FAM_BALL) ? pb->M_ball : 0;
+  const int Mv = (fam & FAM_VN) ? pb->M_vn : 0;
+  int cap = h->cfg.segs_per_cta > 0 ? std::min(512, h->cfg.segs_per_cta / 32 * 32) : 512;
+  for (int C = cap; C >= 32; C -= 32) {
+    ResLayout L = res_layout(C, kClusterNtp, Mb, Mq, Mv, (int)rbytes(h));
     if (L.total <= (size_t)h->smem_optin) return C;
   }
   return 0;
@@ -300,7 +319,7 @@ int top_kernel_times(const top_handle *h, float *ms, int n) {
   if (!h || !ms || n < 0) return TOP_E_INVAL;
   if (!h->profiling) return TOP_E_STATE;
   int w = 0;
-  for (int q = 0; q < 3 && w < n; ++q, ++w) {
+  for (int q = 0; q < 4 && w < n; ++q, ++w) {
     ms[q] = 0.0f;
     if (h->ran[q] && cudaEventElapsedTime(&ms[q], h->ev[2 * q], h->ev[2 * q + 1]) != cudaSuccess) ms[q] = -1.0f;
   }
@@ -328,6 +347,8 @@ void top_destroy(top_handle *h) {
   cudaFree(h->d_tlist);
   std::free(h->plan_off);
   cudaFreeHost(h->h_err);
+  cudaFreeHost(h->h_ctraj);
+  cudaFree(h->d_ctraj);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
   cudaSetDevice(prev);
@@ -368,6 +389,8 @@ int top_create(const top_config *cfg, top_handle **out) {
     if (!h->plan_off) e = cudaErrorMemoryAllocation;
   }
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_ctraj, sizeof(int) * B);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_ctraj, sizeof(int) * B);
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? TOP_E_NOMEM : TOP_E_CUDA;
     h->last_cuda = (int)e;
@@ -501,7 +524,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   // ---- FP64 local-matrix inverses (Eq. 18a) ----
   TOP_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
   const bool fp64 = h->cfg.precision == TOP_FP64;
-  h->ran[0] = h->ran[1] = h->ran[2] = false;
+  h->ran[0] = h->ran[1] = h->ran[2] = h->ran[3] = false;
   PolyData pdata{nullptr, nullptr, nullptr, nullptr};
   {
     if (h->profiling) cudaEventRecord(h->ev[0], st);
@@ -572,15 +595,78 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     if (e) return cuda_fail(h, (cudaError_t)e);
     if (h->profiling) { cudaEventRecord(h->ev[3], st); h->ran[1] = true; }
   }
-  // ---- streaming form for trajectories longer than a resident CTA ----
-  if (has_long) {
+  // ---- cluster-resident form for trajectories longer than a CTA but within a cluster ----
+  // (closed-form step with the box / ball / velocity-norm families and a fixed rho)
+  int ccap = 0, cmax = 0;
+  size_t csmem = 0;
+  const bool cluster_ok = has_long && cap > 0 && h->cfg.schedule == TOP_SCHED_AUTO && !adapt &&
+                          (fam & ~(FAM_BOX | FAM_BALL | FAM_VN)) == 0;
+  if (cluster_ok) {
+    ccap = cluster_capacity(h, &pb);
+    if (ccap > 0) {
+      const int Mb = (fam & FAM_BOX) ? pb.M_box : 0, Mq = (fam & FAM_BALL) ? pb.M_ball : 0,
+                Mv = (fam & FAM_VN) ? pb.M_vn : 0;
+      csmem = res_layout(ccap, kClusterNtp, Mb, Mq, Mv, (int)rbytes(h)).total;
+      if (h->csz_key_C != ccap || h->csz_key_fam != fam || h->csz_key_smem != csmem) {
+        h->csz_val = cluster_max_size(ccap, csmem, fam, fp64);
+        h->csz_key_C = ccap;
+        h->csz_key_fam = fam;
+        h->csz_key_smem = csmem;
+      }
+      cmax = h->csz_val;
+    }
+  }
+  auto cluster_size_for = [&](int nb) -> int {  // smallest power of two of CTAs that holds nb segments
+    if (cmax < 2 || ccap <= 0) return 0;
+    for (int c = 2; c <= cmax; c <<= 1)
+      if ((long long)c * ccap >= nb) return c;
+    return 0;
+  };
+  bool any_cluster = false;
+  if (cluster_ok && cmax >= 2) {
+    DevResult drc = dr;
+    ClusterArgs ca{};
+    ca.p = dp; ca.r = drc; ca.G = h->G; ca.traj = h->d_ctraj;
+    // one launch per cluster size, trajectories listed back to back in d_ctraj
+    int nlist = 0;
+    for (int c = 2; c <= cmax; c <<= 1)
+      for (int b = 0; b < B; ++b) {
+        const int nb = off[b + 1] - off[b];
+        if (nb > cap && cluster_size_for(nb) == c) h->h_ctraj[nlist++] = b;
+      }
+    if (nlist > 0) {
+      any_cluster = true;
+      TOP_CUDA(h, cudaMemcpyAsync(h->d_ctraj, h->h_ctraj, sizeof(int) * nlist, cudaMemcpyHostToDevice, st));
+      if (h->profiling) cudaEventRecord(h->ev[6], st);
+      int at = 0;
+      for (int c = 2; c <= cmax; c <<= 1) {
+        int n = 0;
+        while (at + n < nlist && cluster_size_for(off[h->h_ctraj[at + n] + 1] - off[h->h_ctraj[at + n]]) == c) ++n;
+        if (n == 0) continue;
+        ca.traj = h->d_ctraj + at;
+        int e = fp64 ? launch_cluster_f64(ca, n, c, ccap, csmem, fam, st)
+                     : launch_cluster_f32(ca, n, c, ccap, csmem, fam, st);
+        if (e) return cuda_fail(h, (cudaError_t)e);
+        at += n;
+      }
+      if (h->profiling) { cudaEventRecord(h->ev[7], st); h->ran[3] = true; }
+    }
+  }
+  // ---- streaming form for the remaining long trajectories ----
+  int n_stream_traj = 0;
+  if (has_long)
+    for (int b = 0; b < B; ++b) {
+      const int nb = off[b + 1] - off[b];
+      if (nb > 0 && (cap == 0 || nb > cap) && !(any_cluster && cluster_size_for(nb) > 0)) ++n_stream_traj;
+    }
+  if (n_stream_traj > 0) {
     int nl = 0, total = 0;
     h->h_lt[0] = 0;  // h_lt = [lt_b (B) | lt_prefix (B+1)]
     int *lt_b = h->h_lt, *lt_pre = h->h_lt + h->cfg.max_batch;
     lt_pre[0] = 0;
     for (int b = 0; b < B; ++b) {
       const int nb = off[b + 1] - off[b];
-      if (nb > 0 && (cap == 0 || nb > cap)) {
+      if (nb > 0 && (cap == 0 || nb > cap) && !(any_cluster && cluster_size_for(nb) > 0)) {
         lt_b[nl] = b;
         total += nb;
         lt_pre[++nl] = total;

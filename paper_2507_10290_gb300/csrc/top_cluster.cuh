@@ -1,0 +1,411 @@
+// top_cluster.cuh -- the cluster-resident CADMM kernel: one thread-block
+// cluster per trajectory that is longer than one CTA holds but not longer than
+// a cluster of CTAs (Algorithm 1 of the paper, Eq. 18a-g, 19-21).
+//
+// CTA `rank` of the cluster owns segments rank*C .. rank*C + C - 1 of the
+// trajectory, one thread per segment, with all iteration state in its shared
+// memory in the layout of the resident kernel (top_resident.cuh: junction
+// targets p, m per slot, thread l owns the junction at its segment's end).
+// The only state that crosses CTAs is at the C-boundaries, read through
+// distributed shared memory:
+//   - thread 0 of rank r > 0 reads its start target p (and, on check
+//     iterations, the change of z there) from slot C of rank r - 1, the
+//     junction's owner;
+//   - thread C - 1 of rank r reads the start derivatives of thread 0 of
+//     rank r + 1 in the junction step.
+// The CTA barriers of the resident kernel become cluster barriers.  On check
+// iterations every CTA reduces its share of ||r_p||^2, ||r_d||^2 in a fixed
+// order, rank 0 adds the shares in rank order, applies the stopping test
+// (Eq. 21) and publishes the verdict, which every CTA reads back.  All CTAs of
+// a cluster run the same number of cluster barriers (no early exit), and the
+// kernel ends with one, so no CTA leaves while another may still read its
+// shared memory.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "top_internal.h"
+#include "top_math.cuh"
+#include "top_step.cuh"
+
+namespace top {
+
+namespace cg = cooperative_groups;
+
+template <class R, int F>
+__global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
+  constexpr bool BOX = (F & FAM_BOX) != 0;
+  constexpr bool BALL = (F & FAM_BALL) != 0;
+  constexpr bool VN = (F & FAM_VN) != 0;
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int csz = (int)cl.num_blocks();
+  const DevProblem &p = A.p;
+  const DevResult &res = A.r;
+  const int b = A.traj[blockIdx.x / csz];
+  const int g0 = p.seg_offset[b];
+  const int Nb = p.seg_offset[b + 1] - g0;
+  const int C = blockDim.x;
+  const int l = threadIdx.x;
+  const int Mb = BOX ? p.M_box : 0, Mq = BALL ? p.M_ball : 0, Mv = VN ? p.M_vn : 0;
+  const ResLayout L = res_layout(C, kClusterNtp, Mb, Mq, Mv, (int)sizeof(R));
+  double *red = (double *)(smem + L.red_rp);   // [C] FP64 cost shares (epilogue)
+  R *sh_rp = (R *)(smem + L.red_rp);           // [C] residual shares
+  R *sh_rd = (R *)(smem + L.red_rd);
+  double *part = (double *)(smem + L.tr_rp);   // [8]: shares ||r_p||^2, ||r_d||^2, rank 0's norms, cost share
+  int *sdone = (int *)(smem + L.done);         // rank 0: the verdict
+  R *sp = (R *)(smem + L.p);
+  R *sm = (R *)(smem + L.m);
+  R *szP = (R *)(smem + L.zP);
+  R *seS = (R *)(smem + L.eS);
+  R *sdz = (R *)(smem + L.dz);
+  R *sybox = (R *)(smem + L.ybox);
+  R *sqball = (R *)(smem + L.qball);
+  R *sqvn = (R *)(smem + L.qvn);
+  R *tabB = (R *)(smem + L.tabB);
+  R *tabQ = (R *)(smem + L.tabQ);
+  R *tabV = (R *)(smem + L.tabV);
+
+  const R rho = R(p.rho);
+  const int K = p.max_iters;
+  const bool pin = (p.mode == 0);
+  const int i = rank * C + l;  // segment within the trajectory
+  const bool valid = i < Nb;
+  const bool first = valid && i == 0;
+  const bool last = valid && i == Nb - 1;
+  const int g = g0 + i;
+  const int J = C + kClusterNtp;
+  const int jS = l, jE = l + 1;
+
+  // ---- set-up: zeroed state, tables ----
+  for (int q = l; q < NJ * J; q += C) { sdz[q] = R(0); sp[q] = R(0); sm[q] = R(0); }
+  for (int q = l; q < 3 * J; q += C) szP[q] = R(0);
+  if (BOX) for (int q = l; q < 6 * Mb * C; q += C) sybox[q] = R(0);
+  if (BALL) for (int q = l; q < 3 * Mq * C; q += C) sqball[q] = R(0);
+  if (VN) for (int q = l; q < 3 * Mv * C; q += C) sqvn[q] = R(0);
+  if (BOX) fill_sample_table(tabB, Mb, 1, l, C);
+  if (BALL) fill_sample_table(tabQ, Mq, 0, l, C);
+  if (VN) fill_sample_table(tabV, Mv, 1, l, C);
+  if (l == 0) sdone[0] = 0;
+  __syncthreads();
+
+  // targets at the start junction: local slot, or the owner's slot C in rank - 1
+  const bool remote_start = (l == 0 && rank > 0);
+  R *pS = remote_start ? cl.map_shared_rank(sp + C * NJ, rank - 1) : sp + jS * NJ;
+  R *mS = sm + jS * NJ;  // read only by the trajectory's first segment (rank 0, local)
+  const R *dzS = remote_start ? cl.map_shared_rank(sdz + C * NJ, rank - 1) : sdz + jS * NJ;
+  R *pE = sp + jE * NJ, *mE = sm + jE * NJ;
+  const bool remote_next = (l == C - 1 && rank + 1 < csz);
+  const R *eSnext = remote_next ? cl.map_shared_rank(seS, rank + 1) : seS + (l + 1) * NJ;
+
+  SegConst<R> sc;
+  R Tq = R(1);
+  sc.vbox = sc.vnorm = sc.brad = R(0);
+  sc.bo[0] = sc.bo[1] = sc.bo[2] = R(0);
+  if (valid) {
+    const R *Gp = (const R *)A.G;
+#pragma unroll
+    for (int q = 0; q < NG; ++q) sc.G[q] = Gp[(size_t)q * p.S + g];
+    Tq = R(p.durations[g]);
+    inv_powers(Tq, sc.s);
+    if (BOX) sc.vbox = R(p.vbox[b]);
+    if (VN) sc.vnorm = R(p.vnorm[b]);
+    if (BALL) {
+      sc.brad = R(p.ball_r[g]);
+      for (int a = 0; a < 3; ++a) sc.bo[a] = R(p.ball_c[(size_t)g * 3 + a]);
+    }
+    // Init of Algorithm 1 (the owner writes its end junction; the first
+    // segment also its start junction)
+    for (int a = 0; a < AX; ++a)
+      for (int r = 0; r < ND; ++r) {
+        const int row = a * ND + r;
+        if (!last) {
+          const R P = (r == 0) ? R(p.waypoints[(size_t)(g + b + 1) * 3 + a]) : R(0);
+          pE[row] = P;
+          mE[row] = P;
+          if (r == 0) szP[jE * 3 + a] = P;
+        } else if (r < PO) {
+          const R zN = R(p.end_state[((size_t)b * PO + r) * 3 + a]);
+          pE[row] = zN;
+          mE[row] = zN;
+        }
+        if (first && r < PO) {
+          const R z0 = R(p.start_state[((size_t)b * PO + r) * 3 + a]);
+          pS[row] = z0;
+          mS[row] = z0;
+        }
+      }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NG; ++q) sc.G[q] = R(0);
+#pragma unroll
+    for (int r = 0; r < NC; ++r) sc.s[r] = R(0);
+  }
+  cl.sync();
+  R fs[ND];  // r! T^-r
+#pragma unroll
+  for (int r = 0; r < ND; ++r) fs[r] = R(fact(r)) * sc.s[r];
+
+  R ch[AX][NC];
+#pragma unroll
+  for (int a = 0; a < AX; ++a)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) ch[a][k] = R(0);
+
+  const int cev = p.check_every > 0 ? p.check_every : 1;
+  const bool periodic = p.eps > 0.0 || res.history != nullptr;
+  int done = 0;     // the verdict, identical in every CTA of the cluster
+  double rp_last = 0.0, rd_last = 0.0;
+  const int warp = l >> 5, lane = l & 31;
+  for (int k = 0; k < K; ++k) {
+    const bool check = (k == K - 1) || (periodic && ((k + 1) % cev == 0));
+    const bool act = valid && !done;
+    R eE[AX][ND];
+    R eSv[AX][ND];
+    if (act) {
+      // ---- 1. local step (Eq. 18a, 18d-g) ----
+      R wS[AX][ND], wE[AX][ND];
+#pragma unroll
+      for (int a = 0; a < AX; ++a)
+#pragma unroll
+        for (int r = 0; r < ND; ++r) {
+          wS[a][r] = fs[r] * pS[a * ND + r];
+          wE[a][r] = sc.s[r] * mE[a * ND + r];
+        }
+      local_step<R, F, true>(sc, wS, wE, rho, k == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq,
+                             Mv, ch);
+      // ---- 2. publish start derivatives ----
+#pragma unroll
+      for (int a = 0; a < AX; ++a) {
+        end_derivs_f(ch[a], sc.s, fs, eSv[a], eE[a]);
+#pragma unroll
+        for (int r = 0; r < ND; ++r) seS[l * NJ + a * ND + r] = eSv[a][r];
+      }
+    }
+    cl.sync();
+    // ---- 3. junction update (Eq. 18b, 18c) and primal residual (Eq. 19) ----
+    R rp2 = R(0);
+    if (act) {
+      if (!last) {
+#pragma unroll
+        for (int a = 0; a < AX; ++a) {
+#pragma unroll
+          for (int r = 0; r < ND; ++r) {
+            const int row = a * ND + r;
+            const R ee = eE[a][r], en = eSnext[row];
+            const R pv = pE[row], mv = mE[row];
+            if (check) {
+              const R gap = ee - en;
+              rp2 += gap * gap;
+            }
+            if (pin && r == 0) {
+              const R P = szP[jE * 3 + a];
+              mE[row] = mv + (P - ee);
+              pE[row] = pv + (P - en);
+              if (check) sdz[jE * NJ + row] = R(0);
+            } else {
+              const R uL = R(0.5) * (pv - mv);
+              pE[row] = ee + uL;
+              mE[row] = en - uL;
+              if (check) sdz[jE * NJ + row] = R(0.5) * ((ee + en) - (pv + mv));
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < AX; ++a)
+#pragma unroll
+          for (int r = 0; r < PO; ++r) {
+            const int row = a * ND + r;
+            mE[row] += pE[row] - eE[a][r];
+          }
+      }
+      if (first) {
+#pragma unroll
+        for (int a = 0; a < AX; ++a)
+#pragma unroll
+          for (int r = 0; r < PO; ++r) {
+            const int row = a * ND + r;
+            pS[row] += mS[row] - eSv[a][r];
+          }
+      }
+    }
+    cl.sync();
+    if (check) {
+      // ---- 4. dual residual (Eq. 20), cluster reduction, stopping rule (Eq. 21) ----
+      R rd2 = R(0);
+      if (act) {
+        R Tk[NC];
+        Tk[0] = R(1);
+#pragma unroll
+        for (int q = 1; q < NC; ++q) Tk[q] = Tk[q - 1] * Tq;
+#pragma unroll
+        for (int a = 0; a < AX; ++a) {
+          R dS[ND], dE[ND];
+#pragma unroll
+          for (int r = 0; r < ND; ++r) {
+            dS[r] = first ? R(0) : sc.s[r] * dzS[a * ND + r];
+            dE[r] = last ? R(0) : sc.s[r] * sdz[jE * NJ + a * ND + r];
+          }
+          rd2 += dual_residual_sq(dS, dE, rho, Tk);
+        }
+      }
+      sh_rp[l] = rp2;
+      sh_rd[l] = rd2;
+      __syncthreads();
+      if (warp == 0) {  // this CTA's shares in a fixed order
+        R a1 = R(0), a2 = R(0);
+        for (int x = lane; x < C; x += 32) { a1 += sh_rp[x]; a2 += sh_rd[x]; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+          a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (lane == 0) { part[0] = double(a1); part[1] = double(a2); }
+      }
+      cl.sync();
+      if (rank == 0 && l == 0 && !done) {  // shares in rank order, the verdict
+        double s1 = 0.0, s2 = 0.0;
+        for (int q = 0; q < csz; ++q) {
+          const double *pq = cl.map_shared_rank(part, q);
+          s1 += pq[0];
+          s2 += pq[1];
+        }
+        const double rp = sqrt(s1), rd = sqrt(s2);
+        part[2] = rp;
+        part[3] = rd;
+        if (res.history) {
+          res.history[((size_t)k * p.B + b) * 2 + 0] = rp;
+          res.history[((size_t)k * p.B + b) * 2 + 1] = rd;
+        }
+        const double tol = double(Nb) * p.eps;
+        int st = -1;
+        if (!finite_d(rp) || !finite_d(rd)) st = 2;
+        else if (p.eps > 0.0 && rp < tol && rd < tol) st = 0;
+        if (st >= 0) {
+          sdone[0] = 1;
+          res.iters[b] = k + 1;
+          res.status[b] = st;
+        }
+      }
+      cl.sync();
+      const int *vd = cl.map_shared_rank(sdone, 0);
+      done = vd[0];
+      if (rank == 0) { rp_last = part[2]; rd_last = part[3]; }
+      cl.sync();  // the verdict is read everywhere before rank 0 may write the next shares
+      if (done) break;  // the same verdict in every CTA: a uniform exit from the loop
+    }
+  }
+
+  // ---- outputs: coefficients in the paper's basis, FP64 cost (cluster sum in rank order) ----
+  double Ji = 0.0;
+  if (valid) {
+    const double T = p.durations[g];
+    double sd[NC];
+    sd[0] = 1.0;
+    for (int q = 1; q < NC; ++q) sd[q] = sd[q - 1] / T;
+#pragma unroll
+    for (int a = 0; a < AX; ++a)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) res.coeffs[((size_t)g * AX + a) * NC + q] = double(ch[a][q]) * sd[q];
+    Ji = segment_cost(ch, sd[7]);
+  }
+  red[l] = Ji;
+  __syncthreads();
+  if (warp == 0) {
+    double a1 = 0.0;
+    for (int x = lane; x < C; x += 32) a1 += red[x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    if (lane == 0) part[4] = a1;
+  }
+  cl.sync();
+  if (rank == 0 && l == 0) {
+    double J = 0.0;
+    for (int q = 0; q < csz; ++q) J += cl.map_shared_rank(part, q)[4];
+    res.cost[b] = J;
+    res.r_primal[b] = rp_last;
+    res.r_dual[b] = rd_last;
+    if (!done) {
+      res.iters[b] = K;
+      res.status[b] = 1;
+    }
+  }
+  cl.sync();  // no CTA leaves while rank 0 reads its shared memory
+}
+
+}  // namespace top
+
+namespace top {
+
+template <class R>
+__host__ void *cluster_kernel_for(int fam) {
+  switch (fam) {
+    case 0: return (void *)cluster_kernel<R, 0>;
+    case 1: return (void *)cluster_kernel<R, 1>;
+    case 2: return (void *)cluster_kernel<R, 2>;
+    case 3: return (void *)cluster_kernel<R, 3>;
+    case 4: return (void *)cluster_kernel<R, 4>;
+    case 5: return (void *)cluster_kernel<R, 5>;
+    case 6: return (void *)cluster_kernel<R, 6>;
+    case 7: return (void *)cluster_kernel<R, 7>;
+    default: return nullptr;
+  }
+}
+
+template <class R>
+__host__ int cluster_max_size_t(int C, size_t smem, int fam) {
+  void *kern = cluster_kernel_for<R>(fam);
+  if (!kern) return 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  for (int csz = 16; csz >= 2; csz >>= 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csz);
+    cfg.blockDim = dim3(C);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csz;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0) return csz;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+template <class R>
+__host__ int launch_cluster_t(const ClusterArgs &a, int nclusters, int csz, int C, size_t smem, int fam,
+                              void *stream) {
+  void *kern = cluster_kernel_for<R>(fam);
+  if (!kern || nclusters <= 0) return kern ? 0 : (int)cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return (int)e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nclusters * csz);
+  cfg.blockDim = dim3(C);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csz;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void *args[] = {(void *)&a};
+  e = cudaLaunchKernelExC(&cfg, kern, args);
+  return (int)e;
+}
+
+}  // namespace top

@@ -1,0 +1,9 @@
+// FP32 instantiations of the cluster-resident kernel (top_cluster.cuh).
+#include "top_cluster.cuh"
+
+namespace top {
+int launch_cluster_f32(const ClusterArgs &a, int nclusters, int csz, int C, size_t smem, int fam, void *stream) {
+  return launch_cluster_t<float>(a, nclusters, csz, C, smem, fam, stream);
+}
+int cluster_max_size_f32(int C, size_t smem, int fam) { return cluster_max_size_t<float>(C, smem, fam); }
+}  // namespace top

@@ -71,6 +71,16 @@ struct ResidentArgs {
   int ntp;              // trajectory slots per pack (shared-memory sizing)
 };
 
+// Cluster-resident form (top_cluster.cuh): one trajectory per thread-block
+// cluster, CTA rank r owning segments r*C .. r*C + C - 1.
+struct ClusterArgs {
+  DevProblem p;
+  DevResult r;
+  const void *G;        // [36][S], element type = iteration type
+  const int *traj;      // [nclusters] trajectory ids
+};
+constexpr int kClusterNtp = 8;  // res_layout's trajectory slots for the cluster form (room for its shares)
+
 // Shared-memory layout of the resident kernel; the same function sizes the
 // launch on the host and carves the buffer on the device.
 struct ResLayout {
@@ -154,6 +164,13 @@ int launch_sample(const int32_t *off, const double *T, int B, int M, int order, 
 int launch_time_step(double *T, const double *dT, int S, double kT, double lr, void *stream);
 int launch_resident_f32(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
 int launch_resident_f64(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
+int launch_cluster_f32(const ClusterArgs &a, int nclusters, int csz, int C, size_t smem, int fam, void *stream);
+int launch_cluster_f64(const ClusterArgs &a, int nclusters, int csz, int C, size_t smem, int fam, void *stream);
+// largest cluster size (power of two <= 16) whose CTAs of C threads and `smem`
+// bytes can be co-scheduled, 0 if none
+int cluster_max_size(int C, size_t smem, int fam, bool fp64);
+int cluster_max_size_f32(int C, size_t smem, int fam);
+int cluster_max_size_f64(int C, size_t smem, int fam);
 int launch_stream_f32(const StreamArgs &a, int fam, void *stream);
 int launch_stream_f64(const StreamArgs &a, int fam, void *stream);
 // Adjoint of the unrolled iteration (top_grad)

@@ -163,8 +163,8 @@ def top_set_profiling(handle, enable: bool) -> int:
     return _lib.top_set_profiling(handle, int(bool(enable)))
 
 
-def top_kernel_times(handle, n: int = 3):
-    """(code, [ms...]) of the last top_solve's kernels: precompute, resident, streaming."""
+def top_kernel_times(handle, n: int = 4):
+    """(code, [ms...]) of the last top_solve's kernels: precompute, resident, streaming, cluster-resident."""
     buf = (C.c_float * n)()
     rc = _lib.top_kernel_times(handle, buf, n)
     return rc, [float(x) for x in buf]

@@ -1,0 +1,88 @@
+"""GPU parity of the cluster-resident form (one trajectory per thread-block
+cluster, distributed shared memory at the CTA boundaries) against the oracle.
+
+A handle with 64 segments per CTA sends trajectories of 65 .. 1024 segments
+through clusters of 2 .. 16 CTAs, while shorter ones stay resident and longer
+ones stream; every form must agree with the oracle (FP64 1e-9, FP32 1e-4) and
+the cluster kernel must actually have run.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_10290_gb300 import workloads as W
+
+from test_parity_gpu import T, TOL, compare, to_np  # noqa: F401  (fixture)
+
+pytestmark = pytest.mark.gpu
+
+NS = [0, 1, 5, 64, 65, 128, 129, 200, 333, 1024, 1025, 40]
+
+
+def small_cta_solver(T, precision, schedule="auto"):
+    from test_parity_gpu import _solvers
+    key = ("cta64", precision, schedule)
+    if key not in _solvers:
+        _solvers[key] = T.Solver(64, 20000, precision=precision, max_samples=16, segs_per_cta=64, schedule=schedule)
+    return _solvers[key]
+
+
+def solve_profiled(T, s, w, **kw):
+    T.top_set_profiling(s.handle, True)
+    g = to_np(s.solve(w, **kw))
+    rc, ms = T.top_kernel_times(s.handle, 4)
+    T.top_set_profiling(s.handle, False)
+    return g, ms
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("mode", ["pin", "free"])
+def test_cluster_form_matches_the_oracle(T, precision, mode):
+    w = W.tiny(seed=21, N=NS, mode=mode).with_(max_iters=120)
+    o = oracle.solve(w)
+    g, ms = solve_profiled(T, small_cta_solver(T, precision), w)
+    assert ms[3] > 0.0, "the cluster-resident kernel did not run"
+    assert ms[2] > 0.0, "the 1025-segment trajectory must stream"
+    compare(g, o, w, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cluster_form_with_box_and_ball_rows(T, precision):
+    w = W.corridor(N=300).with_(max_iters=120)
+    o = oracle.solve(w)
+    g, ms = solve_profiled(T, small_cta_solver(T, precision), w)
+    assert ms[3] > 0.0
+    compare(g, o, w, TOL[precision])
+
+
+def test_cluster_stopping_rule_and_history_fp64(T):
+    w = W.tiny(seed=1, N=[150, 70, 300], mode="free", T_range=(0.8, 1.6)).with_(eps=1e-3, max_iters=20000)
+    o = oracle.solve(w, history=True)
+    g, ms = solve_profiled(T, small_cta_solver(T, "fp64"), w, history=True, check_every=1)
+    assert ms[3] > 0.0
+    compare(g, o, w, TOL["fp64"])
+    for b in range(w.B):
+        kb = int(o["iters"][b])
+        scale = np.abs(o["history"][:kb, b]).max(axis=0)
+        assert np.all(np.abs(g["history"][:kb, b] - o["history"][:kb, b]) <= 1e-9 * scale)
+
+
+def test_cluster_and_streaming_forms_agree(T):
+    w = W.tiny(seed=4, N=[700, 90], mode="pin").with_(max_iters=100)
+    a = to_np(small_cta_solver(T, "fp64").solve(w))
+    b = to_np(small_cta_solver(T, "fp64", schedule="stream").solve(w))
+    sc = w.durations[:, None, None] ** np.arange(8)
+    assert np.linalg.norm((a["coeffs"] - b["coeffs"]) * sc) <= 1e-11 * np.linalg.norm(a["coeffs"] * sc)
+    assert np.array_equal(a["iters"], b["iters"])
+
+
+def test_default_capacity_corridor_runs_in_clusters(T):
+    """The 1024-segment corridor (box + ball rows at 16 samples) on the default
+    handle: more segments than one CTA holds, so it runs in a cluster."""
+    from test_parity_gpu import solver
+    w = W.corridor()
+    s = solver(T, "fp32")
+    g, ms = solve_profiled(T, s, w)
+    assert ms[3] > 0.0
+    o = oracle.solve(w)
+    compare(g, o, w, TOL["fp32"])
