@@ -214,6 +214,9 @@ def run_ours(args):
     out = solver.alloc_result(B, S, iters)
     out.pop("rho")  # fixed rho: the step does not ask for the final rho (no fill launch)
     stream = torch.cuda.current_stream()
+    # segments per CTA chosen by the library's autotuner on this batch (outside the timed region)
+    seg_cta, tune_ms = (solver.autotune(w, iters=30, tensors=tensors) if not args.no_autotune
+                        else (512, {}))
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def step():
@@ -228,7 +231,7 @@ def run_ours(args):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     top.top_set_profiling(solver.handle, True)
-    kinv_ms, res_ms = [], []
+    kinv_ms, res_ms, cl_ms = [], [], []
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -241,13 +244,15 @@ def run_ours(args):
             rc, kt = top.top_kernel_times(solver.handle)  # top_solve has synchronised the stream
             kinv_ms.append(kt[0])
             res_ms.append(kt[1])
+            cl_ms.append(kt[3])
         torch.cuda.synchronize()
     top.top_set_profiling(solver.handle, False)
     if world > 1:
         torch.distributed.barrier()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms_step, value = aggregate_ranks(float(np.mean(ms)), S * iters, world, device="cuda")
-    kern = {"kinv_ms": float(np.mean(kinv_ms)), "resident_ms": float(np.mean(res_ms))}
+    kern = {"kinv_ms": float(np.mean(kinv_ms)), "resident_ms": float(np.mean(res_ms)),
+            "cluster_ms": float(np.mean(cl_ms))}
 
     # e2e through the C ABI with host buffers (H2D + D2H inside the timed region)
     arrays = {
@@ -288,7 +293,9 @@ def run_ours(args):
     clocks = clk.summary()
     sm_max = peaks.get("sm_max_mhz") or 2070.0
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FFMA pipe at the maximum SM clock
-    res_ms = kern["resident_ms"]
+    # the iteration kernels: resident packs, plus clusters for trajectories longer
+    # than the chosen capacity (same work per segment-iteration, run one after the other)
+    res_ms = kern["resident_ms"] + kern["cluster_ms"]
     achieved = FLOP_PER_SEG_IT * S * iters / (res_ms / 1000.0) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -298,11 +305,13 @@ def run_ours(args):
                                f"{iters} CADMM iterations, {args.precision} iteration",
                    "trajectories": B, "segments": S, "iterations": iters, "precision": args.precision,
                    "l2": "flushed between steps (256 MiB write); inputs+workspace > L2",
+                   "segs_per_cta": seg_cta, "autotune_ms_30_iterations": tune_ms,
                    "parallelism": f"replicas x{world}"},
         "trajectories_per_s": world * B / (ms_step / 1000.0),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": resident_traffic(S),
-                     "kernel": "resident_kernel<float,0>", "kernel_ms": res_ms,
+                     "kernel": "resident_kernel<float,0>" + (" + cluster_kernel<float,0>" if kern["cluster_ms"] > 0 else ""),
+                     "kernel_ms": res_ms,
                      "peak_source": f"FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x {sm_max:.0f} MHz (max SM clock)",
                      "flop_per_segment_iteration": FLOP_PER_SEG_IT},
         "kinv_ms": kern["kinv_ms"],
@@ -659,6 +668,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tolerance", action="store_true", help="skip the time-to-tolerance measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="keep 512 segments per CTA (skip top_autotune)")
     ap.add_argument("--only", default="", help="with --suite: comma-separated subset of single_box, corridor, "
                     "batch, adaptive, general, polytope, speed, segments, timealloc, grad, general_full")
     ap.add_argument("--suite", action="store_true",

@@ -82,7 +82,7 @@ typedef struct top_config {
   int32_t max_samples;    /* largest M (samples per segment) of any constraint family */
   int32_t schedule;       /* TOP_SCHED_AUTO: trajectories that fit one CTA run resident (packed),
                              longer ones in a thread-block cluster of up to 16 CTAs with distributed
-                             shared memory (closed-form families, fixed rho), the rest streaming;
+                             shared memory (closed-form families), the rest streaming;
                              TOP_SCHED_RESIDENT: resident only (longer: TOP_E_NOTSUP);
                              TOP_SCHED_STREAM: streaming only */
   int32_t segs_per_cta;   /* resident-form capacity per CTA; 0 = chosen from shared-memory size */
@@ -207,6 +207,18 @@ int top_sample(top_handle *h, const top_problem *pb, const double *coeffs, int32
  * Errors: as top_grad; TOP_E_INVAL for k_T < 0, lr <= 0 or steps < 0. */
 int top_time_alloc(top_handle *h, const top_problem *pb, double k_T, double lr, int32_t steps,
                    double *durations_io, top_result *res, void *stream);
+
+/* Autotuner for the resident capacity (segments per CTA; an extension, the
+ * paper has none): times a solve of `iters` iterations (eps = 0) of the given
+ * batch at every capacity from 512 down to 128 in steps of 64 that fits the
+ * shared memory (trajectories longer than the capacity run in clusters or
+ * streaming), after one untimed solve each, and keeps the fastest in the
+ * handle in place of top_config.segs_per_cta.  out_segs_per_cta (may be NULL)
+ * gets the choice; ms (may be NULL) gets up to n_ms timings, in the order
+ * 512, 448, ... (negative for a capacity that does not fit).  Results of the
+ * trial solves are discarded.  Errors: as top_solve. */
+int top_autotune(top_handle *h, const top_problem *pb, int32_t iters, int32_t *out_segs_per_cta, float *ms,
+                 int32_t n_ms, void *stream);
 
 /* Kernel timing.  With profiling enabled, top_solve records CUDA events on
  * the launching stream around each kernel it launches; top_kernel_times then

@@ -599,7 +599,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   // (closed-form step with the box / ball / velocity-norm families and a fixed rho)
   int ccap = 0, cmax = 0;
   size_t csmem = 0;
-  const bool cluster_ok = has_long && cap > 0 && h->cfg.schedule == TOP_SCHED_AUTO && !adapt &&
+  const bool cluster_ok = has_long && cap > 0 && h->cfg.schedule == TOP_SCHED_AUTO &&
                           (fam & ~(FAM_BOX | FAM_BALL | FAM_VN)) == 0;
   if (cluster_ok) {
     ccap = cluster_capacity(h, &pb);
@@ -626,7 +626,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   if (cluster_ok && cmax >= 2) {
     DevResult drc = dr;
     ClusterArgs ca{};
-    ca.p = dp; ca.r = drc; ca.G = h->G; ca.traj = h->d_ctraj;
+    ca.p = dp; ca.r = drc; ca.G = h->G; ca.E = adapt ? h->E : nullptr; ca.traj = h->d_ctraj;
     // one launch per cluster size, trajectories listed back to back in d_ctraj
     int nlist = 0;
     for (int c = 2; c <= cmax; c <<= 1)
@@ -900,6 +900,73 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
   if (*h->h_err & 1) return TOP_E_INVAL;
   if (*h->h_err & 2) return TOP_E_NUMERIC;
   return TOP_OK;
+}
+
+int top_autotune(top_handle *h, const top_problem *pb_in, int32_t iters, int32_t *out_segs_per_cta, float *ms,
+                 int32_t n_ms, void *stream) {
+  if (!h || !pb_in || iters < 1 || (ms && n_ms < 0)) return TOP_E_INVAL;
+  if (pb_in->B < 0 || pb_in->B > h->cfg.max_batch) return pb_in->B < 0 ? TOP_E_INVAL : TOP_E_NOMEM;
+  const int B = pb_in->B;
+  if (B == 0 || !pb_in->seg_offset) return B == 0 ? TOP_OK : TOP_E_INVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  TOP_CUDA(h, cudaSetDevice(h->device));
+  const bool host = pb_in->memory == TOP_MEM_HOST;
+  if (host) {
+    std::memcpy(h->h_off, pb_in->seg_offset, sizeof(int32_t) * (B + 1));
+  } else {
+    TOP_CUDA(h, cudaMemcpyAsync(h->h_off, pb_in->seg_offset, sizeof(int32_t) * (B + 1), cudaMemcpyDeviceToHost, st));
+    TOP_CUDA(h, cudaStreamSynchronize(st));
+  }
+  const int S = h->h_off[B];
+  if (S < 0 || S > h->cfg.max_segments) return TOP_E_NOMEM;
+  // scratch outputs in the problem's memory kind
+  const size_t bytes = sizeof(double) * (24 * (size_t)S + 3 * (size_t)B) + 2 * sizeof(int32_t) * B + 64;
+  unsigned char *buf = nullptr;
+  if (host) {
+    buf = (unsigned char *)std::malloc(bytes);
+    if (!buf) return TOP_E_NOMEM;
+  } else {
+    cudaError_t e = cudaMalloc((void **)&buf, bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); return e == cudaErrorMemoryAllocation ? TOP_E_NOMEM : cuda_fail(h, e); }
+  }
+  top_result r{};
+  r.coeffs = (double *)buf;
+  r.cost = r.coeffs + 24 * (size_t)S;
+  r.r_primal = r.cost + B;
+  r.r_dual = r.r_primal + B;
+  r.iters = (int32_t *)(r.r_dual + B);
+  r.status = r.iters + B;
+  top_problem pb = *pb_in;
+  pb.max_iters = iters;
+  pb.eps = 0.0;
+  const int saved = h->cfg.segs_per_cta;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = TOP_OK, best = saved, q = 0;
+  float best_ms = -1.0f;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = cuda_fail(h, cudaErrorUnknown);
+  for (int C = 512; rc == TOP_OK && C >= 128; C -= 64, ++q) {
+    h->cfg.segs_per_cta = C;
+    float t = -1.0f;
+    if (resident_capacity(h, &pb) == C) {
+      rc = top_solve(h, &pb, &r, stream);  // untimed: plan, workspace, first-touch
+      if (rc == TOP_OK) {
+        cudaEventRecord(e0, st);
+        rc = top_solve(h, &pb, &r, stream);
+        cudaEventRecord(e1, st);
+        if (rc == TOP_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+      }
+      if (rc == TOP_OK && t > 0.0f && (best_ms < 0.0f || t < best_ms)) { best_ms = t; best = C; }
+    }
+    if (ms && q < n_ms) ms[q] = t;
+  }
+  for (; ms && q < n_ms; ++q) ms[q] = -1.0f;
+  h->cfg.segs_per_cta = (rc == TOP_OK && best_ms > 0.0f) ? best : saved;
+  h->plan_valid = false;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (host) std::free(buf); else cudaFree(buf);
+  if (rc == TOP_OK && out_segs_per_cta) *out_segs_per_cta = h->cfg.segs_per_cta;
+  return rc;
 }
 
 int top_sample(top_handle *h, const top_problem *pb, const double *coeffs, int32_t M, int32_t order, double *out,

@@ -19,7 +19,9 @@
 // (Eq. 21) and publishes the verdict, which every CTA reads back.  All CTAs of
 // a cluster run the same number of cluster barriers (no early exit), and the
 // kernel ends with one, so no CTA leaves while another may still read its
-// shared memory.
+// shared memory.  With adaptive rho, rank 0 also applies Eq. 22 and every CTA
+// rescales its own state and local inverses after a change (step 5 of the
+// resident kernel), followed by a cluster barrier.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -33,7 +35,7 @@ namespace top {
 
 namespace cg = cooperative_groups;
 
-template <class R, int F>
+template <class R, int F, bool ADAPT>
 __global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
   constexpr bool BOX = (F & FAM_BOX) != 0;
   constexpr bool BALL = (F & FAM_BALL) != 0;
@@ -54,7 +56,8 @@ __global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
   double *red = (double *)(smem + L.red_rp);   // [C] FP64 cost shares (epilogue)
   R *sh_rp = (R *)(smem + L.red_rp);           // [C] residual shares
   R *sh_rd = (R *)(smem + L.red_rd);
-  double *part = (double *)(smem + L.tr_rp);   // [8]: shares ||r_p||^2, ||r_d||^2, rank 0's norms, cost share
+  double *part = (double *)(smem + L.tr_rp);   // [8]: shares ||r_p||^2, ||r_d||^2, rank 0's norms, cost share,
+                                               //      rank 0's rho and rho_old / rho_new (Eq. 22)
   int *sdone = (int *)(smem + L.done);         // rank 0: the verdict
   R *sp = (R *)(smem + L.p);
   R *sm = (R *)(smem + L.m);
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
   R *tabQ = (R *)(smem + L.tabQ);
   R *tabV = (R *)(smem + L.tabV);
 
-  const R rho = R(p.rho);
+  R rho = R(p.rho);  // the trajectory's rho (changes only with adaptive rho)
   const int K = p.max_iters;
   const bool pin = (p.mode == 0);
   const int i = rank * C + l;  // segment within the trajectory
@@ -88,7 +91,11 @@ __global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
   if (BOX) fill_sample_table(tabB, Mb, 1, l, C);
   if (BALL) fill_sample_table(tabQ, Mq, 0, l, C);
   if (VN) fill_sample_table(tabV, Mv, 1, l, C);
-  if (l == 0) sdone[0] = 0;
+  if (l == 0) {
+    sdone[0] = 0;
+    part[5] = p.rho;
+    part[6] = 1.0;
+  }
   __syncthreads();
 
   // targets at the start junction: local slot, or the owner's slot C in rank - 1
@@ -160,7 +167,7 @@ __global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
   double rp_last = 0.0, rd_last = 0.0;
   const int warp = l >> 5, lane = l & 31;
   for (int k = 0; k < K; ++k) {
-    const bool check = (k == K - 1) || (periodic && ((k + 1) % cev == 0));
+    const bool check = ADAPT || (k == K - 1) || (periodic && ((k + 1) % cev == 0));
     const bool act = valid && !done;
     R eE[AX][ND];
     R eSv[AX][ND];
@@ -284,18 +291,66 @@ __global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
         int st = -1;
         if (!finite_d(rp) || !finite_d(rd)) st = 2;
         else if (p.eps > 0.0 && rp < tol && rd < tol) st = 0;
+        part[6] = 1.0;
         if (st >= 0) {
           sdone[0] = 1;
           res.iters[b] = k + 1;
           res.status[b] = st;
+        } else if (ADAPT) {  // UpdateRho (Eq. 22)
+          const double ro = part[5], rn = next_rho(p, ro, rp, rd);
+          part[5] = rn;
+          part[6] = ro / rn;
         }
       }
       cl.sync();
       const int *vd = cl.map_shared_rank(sdone, 0);
       done = vd[0];
+      double fac = 1.0, rho_new = 0.0;
+      if (ADAPT) {
+        const double *p0 = cl.map_shared_rank(part, 0);
+        fac = p0[6];
+        rho_new = p0[5];
+      }
       if (rank == 0) { rp_last = part[2]; rd_last = part[3]; }
       cl.sync();  // the verdict is read everywhere before rank 0 may write the next shares
       if (done) break;  // the same verdict in every CTA: a uniform exit from the loop
+      // ---- 5. after a change of rho (adaptive rho): keep the unscaled duals, new local inverse ----
+      if (ADAPT && fac != 1.0 && k + 1 < K) {  // the same fac in every CTA
+        if (valid) {
+          const R f = R(fac);
+#pragma unroll
+          for (int a = 0; a < AX; ++a)
+#pragma unroll
+            for (int r = 0; r < ND; ++r) {
+              const int row = a * ND + r;
+              if (!last) {
+                const R zc = (pin && r == 0) ? szP[jE * 3 + a] : R(0.5) * (pE[row] + mE[row]);
+                pE[row] = zc + f * (pE[row] - zc);
+                mE[row] = zc + f * (mE[row] - zc);
+              } else if (r < PO) {
+                mE[row] = pE[row] + f * (mE[row] - pE[row]);
+              }
+              if (first && r < PO) pS[row] = mS[row] + f * (pS[row] - mS[row]);
+            }
+          if (BOX)
+            for (int q = 0; q < 6 * Mb; ++q) {
+              const R y = sybox[q * C + l];
+              if (y > R(0)) sybox[q * C + l] = f * y;
+            }
+          if (BALL)
+            for (int j = 0; j < Mq; ++j) rescale_projected(sqball + j * 3 * C + l, C, sc.bo, sc.brad, f);
+          if (VN) {
+            const R zero3[3] = {R(0), R(0), R(0)};
+            for (int j = 0; j < Mv; ++j) rescale_projected(sqvn + j * 3 * C + l, C, zero3, sc.vnorm, f);
+          }
+          R *Gw = (R *)A.G;
+          g_from_eig_store((const R *)A.E, (size_t)p.S, (size_t)g, rho_new, Gw);
+#pragma unroll
+          for (int q = 0; q < NG; ++q) sc.G[q] = Gw[(size_t)q * p.S + g];
+          rho = R(rho_new);
+        }
+        cl.sync();  // the owners' rescaled targets before any start-side read
+      }
     }
   }
 
@@ -326,6 +381,7 @@ __global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
     double J = 0.0;
     for (int q = 0; q < csz; ++q) J += cl.map_shared_rank(part, q)[4];
     res.cost[b] = J;
+    if (res.rho) res.rho[b] = part[5];
     res.r_primal[b] = rp_last;
     res.r_dual[b] = rd_last;
     if (!done) {
@@ -340,24 +396,29 @@ __global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
 
 namespace top {
 
-template <class R>
-__host__ void *cluster_kernel_for(int fam) {
+template <class R, bool ADAPT>
+__host__ void *cluster_kernel_for_t(int fam) {
   switch (fam) {
-    case 0: return (void *)cluster_kernel<R, 0>;
-    case 1: return (void *)cluster_kernel<R, 1>;
-    case 2: return (void *)cluster_kernel<R, 2>;
-    case 3: return (void *)cluster_kernel<R, 3>;
-    case 4: return (void *)cluster_kernel<R, 4>;
-    case 5: return (void *)cluster_kernel<R, 5>;
-    case 6: return (void *)cluster_kernel<R, 6>;
-    case 7: return (void *)cluster_kernel<R, 7>;
+    case 0: return (void *)cluster_kernel<R, 0, ADAPT>;
+    case 1: return (void *)cluster_kernel<R, 1, ADAPT>;
+    case 2: return (void *)cluster_kernel<R, 2, ADAPT>;
+    case 3: return (void *)cluster_kernel<R, 3, ADAPT>;
+    case 4: return (void *)cluster_kernel<R, 4, ADAPT>;
+    case 5: return (void *)cluster_kernel<R, 5, ADAPT>;
+    case 6: return (void *)cluster_kernel<R, 6, ADAPT>;
+    case 7: return (void *)cluster_kernel<R, 7, ADAPT>;
     default: return nullptr;
   }
 }
 
 template <class R>
+__host__ void *cluster_kernel_for(int fam, bool adapt) {
+  return adapt ? cluster_kernel_for_t<R, true>(fam) : cluster_kernel_for_t<R, false>(fam);
+}
+
+template <class R>
 __host__ int cluster_max_size_t(int C, size_t smem, int fam) {
-  void *kern = cluster_kernel_for<R>(fam);
+  void *kern = cluster_kernel_for<R>(fam, false);
   if (!kern) return 0;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
@@ -386,7 +447,7 @@ __host__ int cluster_max_size_t(int C, size_t smem, int fam) {
 template <class R>
 __host__ int launch_cluster_t(const ClusterArgs &a, int nclusters, int csz, int C, size_t smem, int fam,
                               void *stream) {
-  void *kern = cluster_kernel_for<R>(fam);
+  void *kern = cluster_kernel_for<R>(fam, a.p.adaptive != 0 && a.E != nullptr);
   if (!kern || nclusters <= 0) return kern ? 0 : (int)cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

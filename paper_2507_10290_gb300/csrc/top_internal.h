@@ -76,7 +76,8 @@ struct ResidentArgs {
 struct ClusterArgs {
   DevProblem p;
   DevResult r;
-  const void *G;        // [36][S], element type = iteration type
+  const void *G;        // [36][S], element type = iteration type (rewritten on a change of rho)
+  const void *E;        // [NE][S] adaptive-rho data, or null
   const int *traj;      // [nclusters] trajectory ids
 };
 constexpr int kClusterNtp = 8;  // res_layout's trajectory slots for the cluster form (room for its shares)

@@ -103,6 +103,9 @@ _lib.top_sample.restype = C.c_int
 _lib.top_time_alloc.argtypes = [C.c_void_p, C.POINTER(top_problem), C.c_double, C.c_double, C.c_int32, C.c_void_p,
                                 C.c_void_p, C.c_void_p]
 _lib.top_time_alloc.restype = C.c_int
+_lib.top_autotune.argtypes = [C.c_void_p, C.POINTER(top_problem), C.c_int32, C.POINTER(C.c_int32),
+                              C.POINTER(C.c_float), C.c_int32, C.c_void_p]
+_lib.top_autotune.restype = C.c_int
 _lib.top_set_profiling.argtypes = [C.c_void_p, C.c_int]
 _lib.top_set_profiling.restype = C.c_int
 _lib.top_kernel_times.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int]
@@ -157,6 +160,15 @@ def top_time_alloc(handle, problem: top_problem, k_T: float, lr: float, steps: i
     return _lib.top_time_alloc(handle, C.byref(problem), float(k_T), float(lr), int(steps),
                                C.c_void_p(durations_io), None if result is None else C.byref(result),
                                C.c_void_p(stream))
+
+
+def top_autotune(handle, problem: top_problem, iters: int, n_ms: int = 7, stream: int = 0):
+    """int top_autotune(top_handle*, const top_problem*, int iters, int* out_segs_per_cta, float* ms, int n_ms,
+    void* stream) -> (code, chosen segments per CTA, [ms per capacity 512, 448, ..., 128])."""
+    out = C.c_int32(0)
+    buf = (C.c_float * n_ms)()
+    rc = _lib.top_autotune(handle, C.byref(problem), int(iters), C.byref(out), buf, int(n_ms), C.c_void_p(stream))
+    return rc, int(out.value), [float(x) for x in buf]
 
 
 def top_set_profiling(handle, enable: bool) -> int:
@@ -327,6 +339,17 @@ class Solver:
         if rc != TOP_OK:
             raise TopError(rc, "top_grad", top_last_cuda_error(self.handle))
         return dw, dT
+
+    def autotune(self, w, iters: int = 20, tensors=None, stream=None):
+        """top_autotune on this batch: returns (segments per CTA chosen, {capacity: ms})."""
+        torch = self.torch
+        tensors = tensors if tensors is not None else self.device_inputs(w)
+        pb = self.make_problem(w, tensors, TOP_MEM_DEVICE)
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        rc, best, ms = top_autotune(self.handle, pb, iters, 7, s)
+        if rc != TOP_OK:
+            raise TopError(rc, "top_autotune", top_last_cuda_error(self.handle))
+        return best, {512 - 64 * q: t for q, t in enumerate(ms)}
 
     def sample(self, w, coeffs, M: int, order: int = 0, tensors=None, stream=None):
         """Every trajectory of w with coefficients `coeffs` ([S,3,8] device tensor)

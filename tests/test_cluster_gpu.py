@@ -86,3 +86,32 @@ def test_default_capacity_corridor_runs_in_clusters(T):
     assert ms[3] > 0.0
     o = oracle.solve(w)
     compare(g, o, w, TOL["fp32"])
+
+
+@pytest.mark.parametrize("mode", ["pin", "free"])
+def test_cluster_form_with_adaptive_rho_fp64(T, mode):
+    """Residual balancing (Eq. 22) inside clusters: rank 0 applies the rule,
+    every CTA rescales its state; final rho identical to the oracle's."""
+    w = W.tiny(seed=21, N=NS, mode=mode).with_(max_iters=150, adaptive_rho=True)
+    o = oracle.solve(w)
+    g, ms = solve_profiled(T, small_cta_solver(T, "fp64"), w)
+    assert ms[3] > 0.0
+    compare(g, o, w, TOL["fp64"])
+    assert np.array_equal(g["rho"], o["rho_final"]), (g["rho"], o["rho_final"])
+    c = W.corridor(N=300).with_(max_iters=150, adaptive_rho=True)
+    o = oracle.solve(c)
+    g, ms = solve_profiled(T, small_cta_solver(T, "fp64"), c)
+    assert ms[3] > 0.0
+    compare(g, o, c, TOL["fp64"])
+    assert np.array_equal(g["rho"], o["rho_final"])
+
+
+def test_autotuner_picks_a_fitting_capacity_and_keeps_parity(T):
+    w = W.batch(B=48, seed=7).with_(max_iters=40)
+    s = T.Solver(64, 30000, precision="fp32", max_samples=0)
+    best, table = s.autotune(w, iters=10)
+    assert best in table and table[best] > 0
+    assert all(v < 0 or v >= table[best] for v in table.values())
+    o = oracle.solve(w)
+    compare(to_np(s.solve(w)), o, w, TOL["fp32"])
+    s.close()
