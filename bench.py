@@ -254,6 +254,37 @@ def run_ours(args):
     kern = {"kinv_ms": float(np.mean(kinv_ms)), "resident_ms": float(np.mean(res_ms)),
             "cluster_ms": float(np.mean(cl_ms))}
 
+    # the same step recorded into a CUDA graph (capture-safe mode) and replayed
+    graph_ms = None
+    try:
+        off32 = np.ascontiguousarray(w.seg_offset, dtype=np.int32)
+        if top.top_set_layout(solver.handle, B, off32) == top.TOP_OK:
+            gstream = torch.cuda.Stream()  # capture needs a stream other than the default one
+            gstream.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(gstream):
+                solver.solve(w, tensors=tensors, out=out, stream=gstream.cuda_stream)  # async path once
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=gstream):
+                solver.solve(w, tensors=tensors, out=out, stream=gstream.cuda_stream)
+            torch.cuda.synchronize()
+            total = 0.0
+            with torch.cuda.stream(gstream):
+                for k in range(args.steps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(gstream)
+                    graph.replay()
+                    e1.record(gstream)
+                    torch.cuda.synchronize()
+                    total += e0.elapsed_time(e1)
+            graph_ms = total / args.steps
+            if top.top_sync(solver.handle, gstream.cuda_stream) != top.TOP_OK:
+                graph_ms = None
+            top.top_set_layout(solver.handle, 0, None)
+    except RuntimeError:
+        graph_ms = None
+
     # e2e through the C ABI with host buffers (H2D + D2H inside the timed region)
     arrays = {
         "seg_offset": np.ascontiguousarray(w.seg_offset, dtype=np.int32),
@@ -315,6 +346,7 @@ def run_ours(args):
                      "peak_source": f"FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x {sm_max:.0f} MHz (max SM clock)",
                      "flop_per_segment_iteration": FLOP_PER_SEG_IT},
         "kinv_ms": kern["kinv_ms"],
+        "cuda_graph_ms_per_step": graph_ms,
         "step_ms_all": ms,
         "clocks": clocks,
         "gpu_launches": 2 * args.steps,

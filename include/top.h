@@ -208,6 +208,21 @@ int top_sample(top_handle *h, const top_problem *pb, const double *coeffs, int32
 int top_time_alloc(top_handle *h, const top_problem *pb, double k_T, double lr, int32_t steps,
                    double *durations_io, top_result *res, void *stream);
 
+/* Capture-safe mode (an extension: lets a caller record a whole top_solve
+ * into a CUDA graph and replay it).  After top_set_layout(h, B, host_off)
+ * (host_off: [B+1] host copy of the batch's seg_offset), top_solve calls whose
+ * problem is in device memory with that B take the layout from this copy
+ * instead of reading seg_offset back from the device, and return without
+ * synchronising the stream: every operation they issue is asynchronous on it.
+ * Their device-side error flag (bad durations, a non-positive-definite local
+ * matrix) is read by top_sync(h, stream), which synchronises the stream and
+ * returns TOP_OK, TOP_E_INVAL or TOP_E_NUMERIC for the most recent such call.
+ * Workspace is allocated on first need: make one call with the same problem
+ * kind before beginning a capture.  top_set_layout(h, 0, NULL) leaves the mode.
+ * Errors: TOP_E_INVAL (bad offsets), TOP_E_NOMEM (above the capacities). */
+int top_set_layout(top_handle *h, int32_t B, const int32_t *host_seg_offset);
+int top_sync(top_handle *h, void *stream);
+
 /* Autotuner for the resident capacity (segments per CTA; an extension, the
  * paper has none): times a solve of `iters` iterations (eps = 0) of the given
  * batch at every capacity from 512 down to 128 in steps of 64 that fits the

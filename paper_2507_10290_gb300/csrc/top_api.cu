@@ -61,6 +61,9 @@ struct top_handle {
   int *h_ctraj = nullptr, *d_ctraj = nullptr;  // [max_batch]
   int csz_key_C = -1, csz_key_fam = -1, csz_val = 0;
   size_t csz_key_smem = 0;
+  // capture-safe mode (top_set_layout): host copy of the batch layout
+  int layout_B = 0;
+  int32_t *layout_off = nullptr;  // [max_batch + 1]
 };
 
 namespace {
@@ -348,6 +351,7 @@ void top_destroy(top_handle *h) {
   std::free(h->plan_off);
   cudaFreeHost(h->h_err);
   cudaFreeHost(h->h_ctraj);
+  std::free(h->layout_off);
   cudaFree(h->d_ctraj);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
@@ -410,8 +414,11 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   const int B = pb_in->B;
   if (B == 0) return TOP_OK;
   // ---- batch layout on the host ----
+  const bool async = pb_in->memory == TOP_MEM_DEVICE && h->layout_B == B && h->layout_off;
   if (pb_in->memory == TOP_MEM_HOST) {
     std::memcpy(h->h_off, pb_in->seg_offset, sizeof(int32_t) * (B + 1));
+  } else if (async) {
+    std::memcpy(h->h_off, h->layout_off, sizeof(int32_t) * (B + 1));
   } else {
     TOP_CUDA(h, cudaMemcpyAsync(h->h_off, pb_in->seg_offset, sizeof(int32_t) * (B + 1),
                                 cudaMemcpyDeviceToHost, st));
@@ -739,9 +746,42 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
       TOP_CUDA(h, cudaMemcpyAsync(res_in->history, d_hist, sizeof(double) * 2 * (size_t)pb.max_iters * B,
                                   cudaMemcpyDeviceToHost, st));
   }
+  if (async) return TOP_OK;  // the error flag is read by top_sync
   TOP_CUDA(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   TOP_CUDA(h, cudaStreamSynchronize(st));
   if (d_hist) cudaFree(d_hist);
+  if (*h->h_err & 1) return TOP_E_INVAL;
+  if (*h->h_err & 2) return TOP_E_NUMERIC;
+  return TOP_OK;
+}
+
+int top_set_layout(top_handle *h, int32_t B, const int32_t *host_seg_offset) {
+  if (!h || B < 0) return TOP_E_INVAL;
+  if (B == 0) {
+    h->layout_B = 0;
+    return TOP_OK;
+  }
+  if (!host_seg_offset) return TOP_E_INVAL;
+  if (B > h->cfg.max_batch) return TOP_E_NOMEM;
+  if (host_seg_offset[0] != 0) return TOP_E_INVAL;
+  for (int b = 0; b < B; ++b)
+    if (host_seg_offset[b + 1] < host_seg_offset[b]) return TOP_E_INVAL;
+  if (host_seg_offset[B] > h->cfg.max_segments) return TOP_E_NOMEM;
+  if (!h->layout_off) {
+    h->layout_off = (int32_t *)std::malloc(sizeof(int32_t) * (h->cfg.max_batch + 1));
+    if (!h->layout_off) return TOP_E_NOMEM;
+  }
+  std::memcpy(h->layout_off, host_seg_offset, sizeof(int32_t) * (B + 1));
+  h->layout_B = B;
+  return TOP_OK;
+}
+
+int top_sync(top_handle *h, void *stream) {
+  if (!h) return TOP_E_INVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  TOP_CUDA(h, cudaSetDevice(h->device));
+  TOP_CUDA(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TOP_CUDA(h, cudaStreamSynchronize(st));
   if (*h->h_err & 1) return TOP_E_INVAL;
   if (*h->h_err & 2) return TOP_E_NUMERIC;
   return TOP_OK;

@@ -420,8 +420,8 @@ template <class R>
 __host__ int cluster_max_size_t(int C, size_t smem, int fam) {
   void *kern = cluster_kernel_for<R>(fam, false);
   if (!kern) return 0;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+  if (func_attr_once(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      func_attr_once(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -449,8 +449,8 @@ __host__ int launch_cluster_t(const ClusterArgs &a, int nclusters, int csz, int 
                               void *stream) {
   void *kern = cluster_kernel_for<R>(fam, a.p.adaptive != 0 && a.E != nullptr);
   if (!kern || nclusters <= 0) return kern ? 0 : (int)cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaError_t e = func_attr_once(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = func_attr_once(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return (int)e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nclusters * csz);

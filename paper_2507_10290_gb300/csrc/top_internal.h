@@ -1,8 +1,11 @@
 // top_internal.h -- argument blocks shared by the host driver and the kernels.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 
 namespace top {
 
@@ -154,6 +157,30 @@ struct StreamArgs {
   double *tr_rp, *tr_rd;   // [nl]
   double *rho_t, *fac_t;   // [nl] current rho, rescale factor of the last update
 };
+
+// A kernel attribute set once per (device, kernel, value): cudaFuncSetAttribute
+// is not a stream operation, so launches that only repeat known settings stay
+// free of it (and can be recorded in a CUDA graph).
+inline cudaError_t func_attr_once(const void *kern, cudaFuncAttribute attr, int value) {
+  static std::mutex mu;
+  static const void *keys[512];
+  static int devs[512], attrs[512], vals[512];
+  static int n = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  int slot = -1;
+  for (int i = 0; i < n; ++i)
+    if (keys[i] == kern && devs[i] == dev && attrs[i] == (int)attr) {
+      if (vals[i] >= value) return cudaSuccess;
+      slot = i;
+    }
+  const cudaError_t e = cudaFuncSetAttribute(kern, attr, value);
+  if (e != cudaSuccess) return e;
+  if (slot < 0 && n < 512) slot = n++;
+  if (slot >= 0) { keys[slot] = kern; devs[slot] = dev; attrs[slot] = (int)attr; vals[slot] = value; }
+  return cudaSuccess;
+}
 
 // launchers (defined in the .cu files)
 int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_flag, void *stream);

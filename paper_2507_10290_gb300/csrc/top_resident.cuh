@@ -411,7 +411,7 @@ int launch_resident_t(const ResidentArgs &a, int nblocks, int C, size_t smem, in
 #define TOP_RES_CASE(FV)                                                                               \
   case FV: {                                                                                           \
     auto kern = adapt ? resident_kernel<R, FV, true> : resident_kernel<R, FV, false>;                  \
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    cudaError_t e = func_attr_once((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return (int)e;                                                               \
     kern<<<nblocks, C, smem, st>>>(a);                                                                 \
     return (int)cudaGetLastError();                                                                    \

@@ -106,6 +106,10 @@ _lib.top_time_alloc.restype = C.c_int
 _lib.top_autotune.argtypes = [C.c_void_p, C.POINTER(top_problem), C.c_int32, C.POINTER(C.c_int32),
                               C.POINTER(C.c_float), C.c_int32, C.c_void_p]
 _lib.top_autotune.restype = C.c_int
+_lib.top_set_layout.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
+_lib.top_set_layout.restype = C.c_int
+_lib.top_sync.argtypes = [C.c_void_p, C.c_void_p]
+_lib.top_sync.restype = C.c_int
 _lib.top_set_profiling.argtypes = [C.c_void_p, C.c_int]
 _lib.top_set_profiling.restype = C.c_int
 _lib.top_kernel_times.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int]
@@ -169,6 +173,18 @@ def top_autotune(handle, problem: top_problem, iters: int, n_ms: int = 7, stream
     buf = (C.c_float * n_ms)()
     rc = _lib.top_autotune(handle, C.byref(problem), int(iters), C.byref(out), buf, int(n_ms), C.c_void_p(stream))
     return rc, int(out.value), [float(x) for x in buf]
+
+
+def top_set_layout(handle, B: int, host_seg_offset) -> int:
+    """int top_set_layout(top_handle*, int B, const int32_t* host_seg_offset): capture-safe mode
+    (host_seg_offset: a contiguous int32 numpy array of B+1 entries, or None with B = 0)."""
+    ptr = None if host_seg_offset is None else host_seg_offset.ctypes.data
+    return _lib.top_set_layout(handle, int(B), C.c_void_p(ptr))
+
+
+def top_sync(handle, stream: int = 0) -> int:
+    """int top_sync(top_handle*, void* stream): error flag of the last capture-safe top_solve."""
+    return _lib.top_sync(handle, C.c_void_p(stream))
 
 
 def top_set_profiling(handle, enable: bool) -> int:

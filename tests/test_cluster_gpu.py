@@ -115,3 +115,36 @@ def test_autotuner_picks_a_fitting_capacity_and_keeps_parity(T):
     o = oracle.solve(w)
     compare(to_np(s.solve(w)), o, w, TOL["fp32"])
     s.close()
+
+
+def test_graph_capture_replays_top_solve(T):
+    """Capture-safe mode: a whole top_solve (precompute, resident packs and a
+    cluster) recorded into a CUDA graph and replayed gives the same outputs."""
+    import torch
+    w = W.tiny(seed=3, N=[40, 7, 300, 64, 12], mode="pin").with_(max_iters=60)
+    s = T.Solver(8, 1000, precision="fp32", max_samples=0, segs_per_cta=64)
+    tensors = s.device_inputs(w)
+    out = s.alloc_result(w.B, w.S, 60)
+    off = np.ascontiguousarray(w.seg_offset, dtype=np.int32)
+    assert T.top_set_layout(s.handle, w.B, off) == T.TOP_OK
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        s.solve(w, tensors=tensors, out=out, stream=stream.cuda_stream)  # workspace, plan, attributes
+    torch.cuda.synchronize()
+    assert T.top_sync(s.handle, stream.cuda_stream) == T.TOP_OK
+    ref = {k: v.clone() for k, v in out.items()}
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        s.solve(w, tensors=tensors, out=out, stream=stream.cuda_stream)
+    for v in out.values():
+        v.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert T.top_sync(s.handle, stream.cuda_stream) == T.TOP_OK
+    for k in ref:
+        assert torch.equal(out[k], ref[k]), k
+    o = oracle.solve(w)
+    compare(to_np(out), o, w, TOL["fp32"])
+    assert T.top_set_layout(s.handle, 0, None) == T.TOP_OK
+    s.close()
