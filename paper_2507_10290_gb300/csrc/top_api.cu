@@ -696,6 +696,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     const size_t o_rp = take(sizeof(double) * total), o_rd = take(sizeof(double) * total);
     const size_t o_done = take(sizeof(int) * nl), o_trp = take(sizeof(double) * nl), o_trd = take(sizeof(double) * nl);
     const size_t o_rho = take(sizeof(double) * nl), o_fac = take(sizeof(double) * nl);
+    const size_t o_kc = take(sizeof(int) * nl);
     const size_t o_lt = take(sizeof(int) * (2 * (size_t)nl + 1));
     if (o > h->stream_bytes) {
       cudaFree(h->d_stream);
@@ -726,6 +727,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     sa.rp2 = (double *)(base + o_rp); sa.rd2 = (double *)(base + o_rd);
     sa.done = (int *)(base + o_done); sa.tr_rp = (double *)(base + o_trp); sa.tr_rd = (double *)(base + o_trd);
     sa.rho_t = (double *)(base + o_rho); sa.fac_t = (double *)(base + o_fac);
+    sa.kcount = (int *)(base + o_kc); sa.cev = 1;
     sa.E = adapt ? h->E : nullptr;
     if (h->profiling) cudaEventRecord(h->ev[4], st);
     int e = fp64 ? launch_stream_f64(sa, fam, st) : launch_stream_f32(sa, fam, st);

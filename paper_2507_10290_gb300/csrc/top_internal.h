@@ -156,6 +156,8 @@ struct StreamArgs {
   int *done;               // [nl]
   double *tr_rp, *tr_rd;   // [nl]
   double *rho_t, *fac_t;   // [nl] current rho, rescale factor of the last update
+  int *kcount;             // [nl] periodic residual evaluations so far (or null)
+  int cev;                 // iterations between periodic evaluations
 };
 
 // A kernel attribute set once per (device, kernel, value): cudaFuncSetAttribute

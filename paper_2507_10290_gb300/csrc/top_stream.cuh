@@ -84,6 +84,7 @@ __global__ void stream_init(const StreamArgs A) {
     }
     if (first) {
       A.done[t] = 0;
+      if (A.kcount) A.kcount[t] = 0;
       A.tr_rp[t] = 0.0;
       A.tr_rd[t] = 0.0;
       A.rho_t[t] = p.rho;
@@ -275,12 +276,20 @@ __global__ void __launch_bounds__(256) stream_dual(const StreamArgs A) {
   }
 }
 
-// one block per streaming trajectory: fixed-order sums, history, stopping rule
+// one block per streaming trajectory: fixed-order sums, history, stopping rule.
+// k >= 0: the iteration; k < 0: a periodic evaluation, the n-th of which (kept
+// per trajectory in kcount) falls on iteration (n + 1) cev - 1, so the same
+// launch serves every iteration of a recorded graph.
 template <class R>
 __global__ void __launch_bounds__(256) stream_reduce(const StreamArgs A, int k) {
   __shared__ double s1[256], s2[256];
   const int t = blockIdx.x;
   if (t >= A.nl || A.done[t]) return;
+  if (k < 0) {
+    k = (A.kcount[t] + 1) * A.cev - 1;
+    __syncthreads();  // every thread has k before thread 0 advances the count
+    if (threadIdx.x == 0) A.kcount[t] += 1;
+  }
   const int b = A.lt_b[t];
   const int x0 = A.lt_prefix[t], x1 = A.lt_prefix[t + 1];
   double a1 = 0.0, a2 = 0.0;
@@ -440,18 +449,56 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
   }
   init<<<blocks, threads, 0, st>>>(A);
   const int K = p.max_iters;
-  const int cev = p.check_every > 0 ? p.check_every : 1;
   const bool adapt = p.adaptive && A.E;
-  for (int k = 0; k < K; ++k) {
-    const bool check = adapt || (k == K - 1) || ((p.eps > 0.0 || A.r.history) && ((k + 1) % cev == 0));
-    local<<<blocks, threads, tab_bytes, st>>>(A, k);
-    stream_junction<R><<<blocks, threads, 0, st>>>(A, check ? 1 : 0);
+  const int cev = adapt ? 1 : (p.check_every > 0 ? p.check_every : 1);
+  const bool periodic = adapt || p.eps > 0.0 || A.r.history;
+  StreamArgs Ak = A;
+  Ak.cev = cev;
+  // one iteration; `first` selects the Init-dependent local step, the
+  // final iteration's evaluation names its k unless it is a periodic one
+  auto iteration = [&](cudaStream_t s, int k, bool first) {
+    const bool per = periodic && ((k + 1) % cev == 0);
+    const bool check = per || (k == K - 1);
+    local<<<blocks, threads, tab_bytes, s>>>(Ak, first ? 0 : 1);
+    stream_junction<R><<<blocks, threads, 0, s>>>(Ak, check ? 1 : 0);
     if (check) {
-      stream_dual<R><<<blocks, threads, 0, st>>>(A);
-      stream_reduce<R><<<A.nl, 256, 0, st>>>(A, k);
+      stream_dual<R><<<blocks, threads, 0, s>>>(Ak);
+      stream_reduce<R><<<Ak.nl, 256, 0, s>>>(Ak, per ? -1 : k);
     }
-    if (adapt && k + 1 < K) rescale<<<blocks, threads, 0, st>>>(A);
+    if (adapt && k + 1 < K) rescale<<<blocks, threads, 0, s>>>(Ak);
+  };
+  int k = 0;
+  if (K > 0) iteration(st, k++, true);
+  // iterations 1 .. K-2 in blocks of G recorded once into a CUDA graph: the
+  // launches of a block depend on the iteration only through the pattern of
+  // evaluations, which repeats with period cev (G is a multiple of cev and
+  // every block starts at k = 1 mod cev)
+  const int G = cev * ((32 + cev - 1) / cev);
+  const int nblk = K >= 2 ? (K - 2) / G : 0;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (nblk >= 2 && A.kcount && cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      for (int j = 0; j < G; ++j) iteration(cs, 1 + j, false);
+      ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && graph != nullptr;
+    }
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    bool launched = true;
+    if (ok) {
+      for (int q = 0; launched && q < nblk; ++q) launched = cudaGraphLaunch(exec, st) == cudaSuccess;
+      k = 1 + nblk * G;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    if (!ok) cudaGetLastError();  // no graph: the direct launches below do every iteration
+    if (!launched) return (int)cudaErrorLaunchFailure;  // a partly run graph cannot be resumed
   }
+  for (; k < K; ++k) iteration(st, k, false);
   stream_output<R><<<blocks, threads, 0, st>>>(A);
   stream_finish<R><<<A.nl, 256, 0, st>>>(A, K);
   return (int)cudaGetLastError();
