@@ -10,11 +10,21 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/top.h"
 #include "top_internal.h"
 #include "top_math.cuh"
 
 using namespace top;
+
+namespace {
+// NVTX range for profilers (header-only NVTX; a no-op unless a tool is attached)
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+}  // namespace
 
 struct top_handle {
   top_config cfg{};
@@ -32,6 +42,12 @@ struct top_handle {
   size_t pstage_bytes = 0;
   unsigned char *d_aux = nullptr;     // top_sample / top_time_alloc workspace (grow-only)
   size_t aux_bytes = 0;
+  void *d_ypoly = nullptr;            // polytope slack state of the cluster form (grow-only)
+  size_t ypoly_bytes = 0;
+  // the cluster-resident launches run on a side stream, concurrently with the
+  // resident packs (they share only the precompute, which both wait for)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   Pack *d_packs = nullptr;    // [max_segments]
   int *d_err = nullptr;       // error flag of the precompute kernel
   // staging for TOP_MEM_HOST problems
@@ -112,12 +128,16 @@ int families(const top_problem *pb) {
 
 // largest resident capacity (threads = segments per CTA, multiple of 32, <= 512)
 // whose shared-memory layout fits the device's opt-in limit
+// threads per CTA of the resident and cluster kernels: 512, or 256 with FP64 state
+int max_cta_threads(const top_handle *h) { return h->cfg.precision == TOP_FP64 ? 256 : 512; }
+
 int resident_capacity(const top_handle *h, const top_problem *pb) {
   const int fam = families(pb);
   const int Mb = (fam & FAM_BOX) ? pb->M_box : 0;
   const int Mq = (fam & FAM_BALL) ? pb->M_ball : 0;
   const int Mv = (fam & FAM_VN) ? pb->M_vn : 0;
-  int cap = h->cfg.segs_per_cta > 0 ? std::min(512, h->cfg.segs_per_cta / 32 * 32) : 512;
+  const int tmax = max_cta_threads(h);
+  int cap = h->cfg.segs_per_cta > 0 ? std::min(tmax, h->cfg.segs_per_cta / 32 * 32) : tmax;
   for (int C = cap; C >= 32; C -= 32) {
     ResLayout L = res_layout(C, C / 4, Mb, Mq, Mv, (int)rbytes(h));
     if (L.total <= (size_t)h->smem_optin) return C;
@@ -131,9 +151,11 @@ int cluster_capacity(const top_handle *h, const top_problem *pb) {
   const int Mb = (fam & FAM_BOX) ? pb->M_box : 0;
   const int Mq = (fam & FAM_BALL) ? pb->M_ball : 0;
   const int Mv = (fam & FAM_VN) ? pb->M_vn : 0;
-  int cap = h->cfg.segs_per_cta > 0 ? std::min(512, h->cfg.segs_per_cta / 32 * 32) : 512;
+  const int tmax = max_cta_threads(h);
+  int cap = h->cfg.segs_per_cta > 0 ? std::min(tmax, h->cfg.segs_per_cta / 32 * 32) : tmax;
+  const int Mp = (fam & FAM_POLY) ? pb->M_poly : 0;
   for (int C = cap; C >= 32; C -= 32) {
-    ResLayout L = res_layout(C, kClusterNtp, Mb, Mq, Mv, (int)rbytes(h));
+    ResLayout L = res_layout(C, kClusterNtp, Mb, Mq, Mv, (int)rbytes(h), Mp);
     if (L.total <= (size_t)h->smem_optin) return C;
   }
   return 0;
@@ -279,9 +301,8 @@ int validate(const top_handle *h, const top_problem *pb, const top_result *res) 
   }
   if (pb->B > 0 && (!pb->seg_offset || !pb->waypoints || !pb->start_state || !pb->end_state))
     return TOP_E_INVAL;
-  if (pb->B > 0 && (!res->coeffs || !res->cost || !res->r_primal || !res->r_dual || !res->iters ||
-                    !res->status))
-    return TOP_E_INVAL;
+  if (pb->B > 0 && (!res->cost || !res->r_primal || !res->r_dual || !res->iters || !res->status))
+    return TOP_E_INVAL;  // coeffs is checked once S is known (it may be empty)
   return TOP_OK;
 }
 
@@ -339,6 +360,10 @@ void top_destroy(top_handle *h) {
   cudaFree(h->P);
   cudaFree(h->d_pstage);
   cudaFree(h->d_aux);
+  cudaFree(h->d_ypoly);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+  if (h->join_ev) cudaEventDestroy(h->join_ev);
   cudaFree(h->d_packs);
   cudaFree(h->d_err);
   cudaFree(h->d_stage);
@@ -407,6 +432,7 @@ int top_create(const top_config *cfg, top_handle **out) {
 }
 
 int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void *stream) {
+  Range range("top_solve");
   int rc = validate(h, pb_in, res_in);
   if (rc != TOP_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -430,7 +456,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     if (off[b + 1] < off[b]) return TOP_E_INVAL;
   const int S = off[B];
   if (S > h->cfg.max_segments) return TOP_E_NOMEM;
-  if (S > 0 && !pb_in->durations) return TOP_E_INVAL;
+  if (S > 0 && (!pb_in->durations || !res_in->coeffs)) return TOP_E_INVAL;
   // ---- device views of inputs and outputs ----
   top_problem pb = *pb_in;
   top_result res = *res_in;
@@ -534,6 +560,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   h->ran[0] = h->ran[1] = h->ran[2] = h->ran[3] = false;
   PolyData pdata{nullptr, nullptr, nullptr, nullptr};
   {
+    Range r0("precompute (FP64 local inverses)");
     if (h->profiling) cudaEventRecord(h->ev[0], st);
     int e = 0;
     if (pb.M_poly > 0) {
@@ -575,6 +602,14 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     h->plan_valid = false;  // set once the device copies are enqueued
   }
   const int npack = h->plan_npack, max_nseg = h->plan_max_nseg, max_ntraj = h->plan_max_ntraj;
+  if (h->plan_has_long && npack > 0) {  // fork point for the cluster launches (after the precompute)
+    if (!h->side) {
+      TOP_CUDA(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+      TOP_CUDA(h, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+      TOP_CUDA(h, cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
+    }
+    TOP_CUDA(h, cudaEventRecord(h->fork_ev, st));
+  }
   const bool has_long = h->plan_has_long;
   if (has_long && h->cfg.schedule == TOP_SCHED_RESIDENT) {
     if (d_hist) cudaFree(d_hist);
@@ -596,6 +631,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     ResidentArgs ra{};
     ra.p = dp; ra.r = dr; ra.G = h->G; ra.packs = h->d_packs; ra.traj_list = h->d_tlist; ra.ntp = ntp;
     ra.E = adapt ? h->E : nullptr;
+    Range r1("resident packs");
     if (h->profiling) cudaEventRecord(h->ev[2], st);
     int e = fp64 ? launch_resident_f64(ra, npack, C, L.total, fam, st)
                  : launch_resident_f32(ra, npack, C, L.total, fam, st);
@@ -604,16 +640,21 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   }
   // ---- cluster-resident form for trajectories longer than a CTA but within a cluster ----
   // (closed-form step with the box / ball / velocity-norm families and a fixed rho)
+  // polytope trajectories of any length use the cluster form (a cluster of one CTA
+  // for short ones): the resident packs have no room for their per-axis inverses
   int ccap = 0, cmax = 0;
   size_t csmem = 0;
-  const bool cluster_ok = has_long && cap > 0 && h->cfg.schedule == TOP_SCHED_AUTO &&
-                          (fam & ~(FAM_BOX | FAM_BALL | FAM_VN)) == 0;
+  const bool poly = (fam & FAM_POLY) != 0;
+  const bool cluster_ok = has_long && (cap > 0 || poly) && h->cfg.schedule == TOP_SCHED_AUTO &&
+                          (fam & ~(FAM_BOX | FAM_BALL | FAM_VN | FAM_POLY)) == 0;
+  const int cmin = poly ? 1 : 2;
   if (cluster_ok) {
     ccap = cluster_capacity(h, &pb);
     if (ccap > 0) {
       const int Mb = (fam & FAM_BOX) ? pb.M_box : 0, Mq = (fam & FAM_BALL) ? pb.M_ball : 0,
                 Mv = (fam & FAM_VN) ? pb.M_vn : 0;
-      csmem = res_layout(ccap, kClusterNtp, Mb, Mq, Mv, (int)rbytes(h)).total;
+      const int Mp = poly ? pb.M_poly : 0;
+      csmem = res_layout(ccap, kClusterNtp, Mb, Mq, Mv, (int)rbytes(h), Mp).total;
       if (h->csz_key_C != ccap || h->csz_key_fam != fam || h->csz_key_smem != csmem) {
         h->csz_val = cluster_max_size(ccap, csmem, fam, fp64);
         h->csz_key_C = ccap;
@@ -624,39 +665,56 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     }
   }
   auto cluster_size_for = [&](int nb) -> int {  // smallest power of two of CTAs that holds nb segments
-    if (cmax < 2 || ccap <= 0) return 0;
-    for (int c = 2; c <= cmax; c <<= 1)
+    if (cmax < cmin || ccap <= 0) return 0;
+    for (int c = cmin; c <= cmax; c <<= 1)
       if ((long long)c * ccap >= nb) return c;
     return 0;
   };
   bool any_cluster = false;
-  if (cluster_ok && cmax >= 2) {
+  if (cluster_ok && cmax >= cmin) {
     DevResult drc = dr;
     ClusterArgs ca{};
     ca.p = dp; ca.r = drc; ca.G = h->G; ca.E = adapt ? h->E : nullptr; ca.traj = h->d_ctraj;
+    ca.poly = pdata;
+    if (poly) {
+      const size_t want = rbytes(h) * (size_t)dp.F_poly * dp.M_poly * (size_t)S + 256;
+      cudaError_t ge = grow(&h->d_ypoly, &h->ypoly_bytes, want);
+      if (ge != cudaSuccess) {
+        if (d_hist) cudaFree(d_hist);
+        return ge == cudaErrorMemoryAllocation ? TOP_E_NOMEM : cuda_fail(h, ge);
+      }
+      ca.ypoly = h->d_ypoly;
+    }
     // one launch per cluster size, trajectories listed back to back in d_ctraj
     int nlist = 0;
-    for (int c = 2; c <= cmax; c <<= 1)
+    for (int c = cmin; c <= cmax; c <<= 1)
       for (int b = 0; b < B; ++b) {
         const int nb = off[b + 1] - off[b];
-        if (nb > cap && cluster_size_for(nb) == c) h->h_ctraj[nlist++] = b;
+        if (nb > 0 && (cap == 0 || nb > cap) && cluster_size_for(nb) == c) h->h_ctraj[nlist++] = b;
       }
     if (nlist > 0) {
       any_cluster = true;
-      TOP_CUDA(h, cudaMemcpyAsync(h->d_ctraj, h->h_ctraj, sizeof(int) * nlist, cudaMemcpyHostToDevice, st));
-      if (h->profiling) cudaEventRecord(h->ev[6], st);
+      cudaStream_t cs = (npack > 0 && h->side) ? h->side : st;  // beside the resident packs when there are any
+      if (cs != st) TOP_CUDA(h, cudaStreamWaitEvent(cs, h->fork_ev, 0));
+      TOP_CUDA(h, cudaMemcpyAsync(h->d_ctraj, h->h_ctraj, sizeof(int) * nlist, cudaMemcpyHostToDevice, cs));
+      Range r3("cluster-resident trajectories");
+      if (h->profiling) cudaEventRecord(h->ev[6], cs);
       int at = 0;
-      for (int c = 2; c <= cmax; c <<= 1) {
+      for (int c = cmin; c <= cmax; c <<= 1) {
         int n = 0;
         while (at + n < nlist && cluster_size_for(off[h->h_ctraj[at + n] + 1] - off[h->h_ctraj[at + n]]) == c) ++n;
         if (n == 0) continue;
         ca.traj = h->d_ctraj + at;
-        int e = fp64 ? launch_cluster_f64(ca, n, c, ccap, csmem, fam, st)
-                     : launch_cluster_f32(ca, n, c, ccap, csmem, fam, st);
+        int e = fp64 ? launch_cluster_f64(ca, n, c, ccap, csmem, fam, cs)
+                     : launch_cluster_f32(ca, n, c, ccap, csmem, fam, cs);
         if (e) return cuda_fail(h, (cudaError_t)e);
         at += n;
       }
-      if (h->profiling) { cudaEventRecord(h->ev[7], st); h->ran[3] = true; }
+      if (h->profiling) { cudaEventRecord(h->ev[7], cs); h->ran[3] = true; }
+      if (cs != st) {
+        TOP_CUDA(h, cudaEventRecord(h->join_ev, cs));
+        TOP_CUDA(h, cudaStreamWaitEvent(st, h->join_ev, 0));
+      }
     }
   }
   // ---- streaming form for the remaining long trajectories ----
@@ -729,6 +787,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     sa.rho_t = (double *)(base + o_rho); sa.fac_t = (double *)(base + o_fac);
     sa.kcount = (int *)(base + o_kc); sa.cev = 1;
     sa.E = adapt ? h->E : nullptr;
+    Range r2("streaming trajectories");
     if (h->profiling) cudaEventRecord(h->ev[4], st);
     int e = fp64 ? launch_stream_f64(sa, fam, st) : launch_stream_f32(sa, fam, st);
     if (e) return cuda_fail(h, (cudaError_t)e);
@@ -791,6 +850,7 @@ int top_sync(top_handle *h, void *stream) {
 
 int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *dwaypoints, double *ddurations,
              void *stream) {
+  Range range("top_grad");
   if (!h || !pb_in || !dJ || !dwaypoints || !ddurations) return TOP_E_INVAL;
   top_result fake{};
   fake.coeffs = fake.cost = fake.r_primal = fake.r_dual = ddurations;

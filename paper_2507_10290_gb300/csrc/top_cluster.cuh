@@ -19,7 +19,9 @@
 // (Eq. 21) and publishes the verdict, which every CTA reads back.  All CTAs of
 // a cluster run the same number of cluster barriers (no early exit), and the
 // kernel ends with one, so no CTA leaves while another may still read its
-// shared memory.  With adaptive rho, rank 0 also applies Eq. 22 and every CTA
+// shared memory.  Polytope rows (fixed rho) use the rotated per-axis inverses
+// and their slack state from global memory (L2-resident at these sizes).
+// With adaptive rho, rank 0 also applies Eq. 22 and every CTA
 // rescales its own state and local inverses after a change (step 5 of the
 // resident kernel), followed by a cluster barrier.
 #pragma once
@@ -36,10 +38,11 @@ namespace top {
 namespace cg = cooperative_groups;
 
 template <class R, int F, bool ADAPT>
-__global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
+__global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(const ClusterArgs A) {
   constexpr bool BOX = (F & FAM_BOX) != 0;
   constexpr bool BALL = (F & FAM_BALL) != 0;
   constexpr bool VN = (F & FAM_VN) != 0;
+  constexpr bool POLY = (F & FAM_POLY) != 0;
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
@@ -52,7 +55,8 @@ __global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
   const int C = blockDim.x;
   const int l = threadIdx.x;
   const int Mb = BOX ? p.M_box : 0, Mq = BALL ? p.M_ball : 0, Mv = VN ? p.M_vn : 0;
-  const ResLayout L = res_layout(C, kClusterNtp, Mb, Mq, Mv, (int)sizeof(R));
+  const int Mp = POLY ? p.M_poly : 0, Fp = POLY ? p.F_poly : 0;
+  const ResLayout L = res_layout(C, kClusterNtp, Mb, Mq, Mv, (int)sizeof(R), Mp);
   double *red = (double *)(smem + L.red_rp);   // [C] FP64 cost shares (epilogue)
   R *sh_rp = (R *)(smem + L.red_rp);           // [C] residual shares
   R *sh_rd = (R *)(smem + L.red_rd);
@@ -70,6 +74,7 @@ __global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
   R *tabB = (R *)(smem + L.tabB);
   R *tabQ = (R *)(smem + L.tabQ);
   R *tabV = (R *)(smem + L.tabV);
+  R *tabP = (R *)(smem + L.tabP);
 
   R rho = R(p.rho);  // the trajectory's rho (changes only with adaptive rho)
   const int K = p.max_iters;
@@ -91,6 +96,7 @@ __global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
   if (BOX) fill_sample_table(tabB, Mb, 1, l, C);
   if (BALL) fill_sample_table(tabQ, Mq, 0, l, C);
   if (VN) fill_sample_table(tabV, Mv, 1, l, C);
+  if (POLY) fill_sample_table(tabP, Mp, 0, l, C);
   if (l == 0) {
     sdone[0] = 0;
     part[5] = p.rho;
@@ -111,10 +117,17 @@ __global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
   R Tq = R(1);
   sc.vbox = sc.vnorm = sc.brad = R(0);
   sc.bo[0] = sc.bo[1] = sc.bo[2] = R(0);
+  R *ypoly = POLY ? (R *)A.ypoly + (valid ? g : 0) : nullptr;  // own column, stride S
   if (valid) {
-    const R *Gp = (const R *)A.G;
+    if (!POLY) {  // the polytope family keeps its per-axis inverses in A.poly
+      const R *Gp = (const R *)A.G;
 #pragma unroll
-    for (int q = 0; q < NG; ++q) sc.G[q] = Gp[(size_t)q * p.S + g];
+      for (int q = 0; q < NG; ++q) sc.G[q] = Gp[(size_t)q * p.S + g];
+    } else {
+#pragma unroll
+      for (int q = 0; q < NG; ++q) sc.G[q] = R(0);
+      for (int q = 0; q < Fp * Mp; ++q) ypoly[(size_t)q * p.S] = R(0);
+    }
     Tq = R(p.durations[g]);
     inv_powers(Tq, sc.s);
     if (BOX) sc.vbox = R(p.vbox[b]);
@@ -181,8 +194,19 @@ __global__ void __launch_bounds__(512, 1) cluster_kernel(const ClusterArgs A) {
           wS[a][r] = fs[r] * pS[a * ND + r];
           wE[a][r] = sc.s[r] * mE[a * ND + r];
         }
-      local_step<R, F, true>(sc, wS, wE, rho, k == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq,
-                             Mv, ch);
+      if (POLY) {
+        const R *PN = (const R *)A.poly.N, *PH = (const R *)A.poly.H;
+        R rhs[AX][NC];
+        family_rhs<R, F & 7, true>(sc, wS, wE, rho, k == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV,
+                                   Mb, Mq, Mv, rhs);
+        poly_rhs(PN, PH, (size_t)p.S, (size_t)g, Fp, Mp, rho, ypoly, p.S, tabP, rhs);
+        poly_solve((const R *)A.poly.G, (const R *)A.poly.U, (size_t)p.S, (size_t)g, rhs, ch);
+        family_update<R, F & 7>(sc, k == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq, Mv, ch);
+        poly_update(PN, PH, (size_t)p.S, (size_t)g, Fp, Mp, ypoly, p.S, tabP, ch);
+      } else {
+        local_step<R, F, true>(sc, wS, wE, rho, k == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb,
+                               Mq, Mv, ch);
+      }
       // ---- 2. publish start derivatives ----
 #pragma unroll
       for (int a = 0; a < AX; ++a) {
@@ -407,6 +431,14 @@ __host__ void *cluster_kernel_for_t(int fam) {
     case 5: return (void *)cluster_kernel<R, 5, ADAPT>;
     case 6: return (void *)cluster_kernel<R, 6, ADAPT>;
     case 7: return (void *)cluster_kernel<R, 7, ADAPT>;
+    case 16: return (void *)cluster_kernel<R, 16, false>;
+    case 17: return (void *)cluster_kernel<R, 17, false>;
+    case 18: return (void *)cluster_kernel<R, 18, false>;
+    case 19: return (void *)cluster_kernel<R, 19, false>;
+    case 20: return (void *)cluster_kernel<R, 20, false>;
+    case 21: return (void *)cluster_kernel<R, 21, false>;
+    case 22: return (void *)cluster_kernel<R, 22, false>;
+    case 23: return (void *)cluster_kernel<R, 23, false>;
     default: return nullptr;
   }
 }
@@ -425,7 +457,7 @@ __host__ int cluster_max_size_t(int C, size_t smem, int fam) {
     cudaGetLastError();
     return 0;
   }
-  for (int csz = 16; csz >= 2; csz >>= 1) {
+  for (int csz = 16; csz >= 1; csz >>= 1) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(csz);
     cfg.blockDim = dim3(C);

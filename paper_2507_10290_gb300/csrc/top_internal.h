@@ -82,6 +82,8 @@ struct ClusterArgs {
   const void *G;        // [36][S], element type = iteration type (rewritten on a change of rho)
   const void *E;        // [NE][S] adaptive-rho data, or null
   const int *traj;      // [nclusters] trajectory ids
+  PolyData poly;        // polytope family (FAM_POLY), else null pointers
+  void *ypoly;          // [F_poly M_poly][S] compressed slack / dual of the polytope rows
 };
 constexpr int kClusterNtp = 8;  // res_layout's trajectory slots for the cluster form (room for its shares)
 
@@ -89,7 +91,7 @@ constexpr int kClusterNtp = 8;  // res_layout's trajectory slots for the cluster
 // launch on the host and carves the buffer on the device.
 struct ResLayout {
   size_t red_rp, red_rd, tr_rp, tr_rd;           // double arrays
-  size_t p, m, zP, eS, dz, ybox, qball, qvn, tabB, tabQ, tabV;  // element arrays
+  size_t p, m, zP, eS, dz, ybox, qball, qvn, tabB, tabQ, tabV, tabP;  // element arrays
   size_t off, done, tid, flag;                   // int arrays
   size_t rho, fac;                               // double arrays (per trajectory)
   size_t total;
@@ -97,7 +99,7 @@ struct ResLayout {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, int Mv, int rb) {
+__host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, int Mv, int rb, int Mp = 0) {
   ResLayout L{};
   const size_t J = size_t(C) + size_t(ntp);
   size_t o = 0;
@@ -117,6 +119,7 @@ __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, 
   L.tabB = o;   o += size_t(rb) * 8 * Mb;
   L.tabQ = o;   o += size_t(rb) * 8 * Mq;
   L.tabV = o;   o += size_t(rb) * 8 * Mv;
+  L.tabP = o;   o += size_t(rb) * 8 * Mp;  // polytope sample rows (cluster form)
   o = align_up(o, 16);
   L.off = o;    o += sizeof(int) * (ntp + 1);
   L.done = o;   o += sizeof(int) * ntp;

@@ -129,7 +129,7 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
   if (pb->M_vn > 0) fam |= FAM_VN;
   const int rb = precision == TOP_FP64 ? 8 : 4;
   int cap = 0;
-  for (int C = 512; C >= 32 && cap == 0; C -= 32)
+  for (int C = (precision == TOP_FP64 ? 256 : 512); C >= 32 && cap == 0; C -= 32)  // FP64: 256 threads per CTA
     if (res_layout(C, C / 4, pb->M_box, pb->M_ball, pb->M_vn, rb).total <= (size_t)slot->smem_optin) cap = C;
   if (cap == 0) return TOP_E_LIMIT;
   Pack packs[kMaxBatch];

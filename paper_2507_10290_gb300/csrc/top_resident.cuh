@@ -43,8 +43,9 @@
 
 namespace top {
 
+// FP64 state needs twice the registers: 256 threads per CTA (255 registers each) in FP64
 template <class R, int F, bool ADAPT>
-__global__ void __launch_bounds__(512, 1) resident_kernel(const ResidentArgs A) {
+__global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel(const ResidentArgs A) {
   constexpr bool BOX = (F & FAM_BOX) != 0;
   constexpr bool BALL = (F & FAM_BALL) != 0;
   constexpr bool VN = (F & FAM_VN) != 0;

@@ -96,3 +96,23 @@ def test_unsupported_combinations(T):
     with pytest.raises(T.TopError) as e:
         s.grad(w)
     assert e.value.code == T.TOP_E_NOTSUP
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cluster_and_streaming_forms_agree_on_polytopes(T, precision):
+    """Polytope trajectories run in clusters (one CTA for short ones) by
+    default; the streaming form computes the same iteration."""
+    from test_parity_gpu import _solvers
+    key = ("stream-poly", precision)
+    if key not in _solvers:
+        _solvers[key] = T.Solver(64, 200000, precision=precision, max_samples=16, schedule="stream")
+    w = edge_case("free", M_box=4, vbox=np.full(len(EDGE_NS), 2.5))
+    T.top_set_profiling(solver(T, precision).handle, True)
+    a = to_np(solver(T, precision).solve(w))
+    rc, ms = T.top_kernel_times(solver(T, precision).handle, 4)
+    T.top_set_profiling(solver(T, precision).handle, False)
+    assert ms[3] > 0.0 and ms[2] == 0.0, ms
+    b = to_np(_solvers[key].solve(w))
+    sc = w.durations[:, None, None] ** np.arange(8)
+    tol = 1e-11 if precision == "fp64" else 2e-5
+    assert np.linalg.norm((a["coeffs"] - b["coeffs"]) * sc) <= tol * np.linalg.norm(b["coeffs"] * sc)
