@@ -755,6 +755,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     const size_t o_done = take(sizeof(int) * nl), o_trp = take(sizeof(double) * nl), o_trd = take(sizeof(double) * nl);
     const size_t o_rho = take(sizeof(double) * nl), o_fac = take(sizeof(double) * nl);
     const size_t o_kc = take(sizeof(int) * nl);
+    const size_t o_nw = take(sizeof(int) * (Mg > 0 ? (size_t)total + 1 : 1));
     const size_t o_lt = take(sizeof(int) * (2 * (size_t)nl + 1));
     if (o > h->stream_bytes) {
       cudaFree(h->d_stream);
@@ -786,6 +787,10 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     sa.done = (int *)(base + o_done); sa.tr_rp = (double *)(base + o_trp); sa.tr_rd = (double *)(base + o_trd);
     sa.rho_t = (double *)(base + o_rho); sa.fac_t = (double *)(base + o_fac);
     sa.kcount = (int *)(base + o_kc); sa.cev = 1;
+    // the warp-per-segment numerical step pays in FP64 (4x on active bounds); in FP32 a
+    // thread per segment is as fast and needs no extra launches per iteration
+    sa.nwork = (Mg > 0 && fp64) ? (int *)(base + o_nw) : nullptr;
+    sa.work = (Mg > 0 && fp64) ? (int *)(base + o_nw) + 1 : nullptr;
     sa.E = adapt ? h->E : nullptr;
     Range r2("streaming trajectories");
     if (h->profiling) cudaEventRecord(h->ev[4], st);

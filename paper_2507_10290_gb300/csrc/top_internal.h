@@ -161,6 +161,7 @@ struct StreamArgs {
   double *rho_t, *fac_t;   // [nl] current rho, rescale factor of the last update
   int *kcount;             // [nl] periodic residual evaluations so far (or null)
   int cev;                 // iterations between periodic evaluations
+  int *nwork, *work;       // numerical step: count and compact indices of segments with a violated bound
 };
 
 // A kernel attribute set once per (device, kernel, value): cudaFuncSetAttribute

@@ -435,7 +435,7 @@ __device__ __forceinline__ R dot24(const R (&x)[AX][NC], const R (&y)[AX][NC]) {
 template <class R>
 __device__ int numeric_step(const SegConst<R> &sc, const R (&w)[AX][2][ND], R rho, bool first, bool last, R *yg,
                             int stride, const R *tabV, const R *tabA, int Mg, R vmax, R amax, int mem, int max_it,
-                            R tol, R (&ch)[AX][NC]) {
+                            R tol, R (&ch)[AX][NC], bool defer = false) {
   // start: minimiser of the quadratic part (the closed-form step without constraint rows)
   R rhs[AX][NC];
 #pragma unroll
@@ -474,6 +474,7 @@ __device__ int numeric_step(const SegConst<R> &sc, const R (&w)[AX][2][ND], R rh
       }
     }
     if (!violated) return 0;
+    if (defer) return -1;  // the caller hands the segment to the warp-cooperative solver
   }
   R scale = dot24(rhs, ch);  // rhs^T G rhs: size of the linear term in the G metric
   if (!(scale > R(0))) scale = R(1);
@@ -580,6 +581,234 @@ __device__ int numeric_step(const SegConst<R> &sc, const R (&w)[AX][2][ND], R rh
       if (h > R(0)) yg[(j * 2 + kind) * stride] += rho * h * h;
     }
   }
+  return it;
+}
+
+// ---- the numerical step with one warp per segment ----
+// Lane a * 8 + k (a < 3) holds coefficient k of axis a of every vector of the
+// solve; lanes 24..31 hold zeros.  Sums over lanes are xor butterflies, whose
+// result is bit-identical in every lane, so every branch on a sum is uniform.
+// Same algorithm as numeric_step (start at the minimiser of the quadratic
+// part, L-BFGS with H0 = G, Armijo backtracking, then y += rho g).
+
+template <class R>
+__device__ __forceinline__ R wsum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class R>
+__device__ __forceinline__ R wsum8(R v) {  // over the 8 lanes of an axis
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  return v;
+}
+
+__device__ __forceinline__ int fact_rt(int r) {
+  int f = 1;
+  for (int i = 2; i <= r; ++i) f *= i;
+  return f;
+}
+
+__device__ __forceinline__ int falling_rt(int k, int r) {
+  int f = 1;
+  for (int i = 0; i < r; ++i) f *= (k - i);
+  return f;
+}
+
+// y = G x for this lane's axis (Grow = row k of G)
+template <class R>
+__device__ __forceinline__ R wapply_g(const R (&Grow)[NC], R x) {
+  const int base = (threadIdx.x & 31) & ~7;
+  R y = R(0);
+#pragma unroll
+  for (int l = 0; l < NC; ++l) y += Grow[l] * __shfl_sync(0xffffffffu, x, base + l);
+  return y;
+}
+
+// this lane's integer constants of the basis (k = lane & 7), formed once per segment
+template <class R>
+struct WLane {
+  R q[NC];   // Qh[k][l] (zero unless k, l >= p)
+  R fr[NC];  // F(m, k) = m! / (m - k)!  (zero for m < k)
+  R fc[ND];  // F(k, r)                  (zero for r > k)
+  R fk;      // k!
+};
+
+template <class R>
+__device__ __forceinline__ void wlane_init(WLane<R> &L) {
+  const int k = threadIdx.x & 7;
+#pragma unroll
+  for (int l = 0; l < NC; ++l) {
+    L.q[l] = (k >= PO && l >= PO)
+                 ? R(double(falling_rt(k, PO)) * double(falling_rt(l, PO)) / double(k + l - 2 * PO + 1))
+                 : R(0);
+    L.fr[l] = l >= k ? R(falling_rt(l, k)) : R(0);
+  }
+#pragma unroll
+  for (int r = 0; r < ND; ++r) L.fc[r] = r <= k ? R(falling_rt(k, r)) : R(0);
+  L.fk = R(fact_rt(k));
+}
+
+// the objective of the numerical local step and this lane's gradient entry
+template <class R>
+__device__ R wnum_F(R c, R w0, R w1, const WLane<R> &L, const R (&s)[NC], R rho, bool first, bool last,
+                    const R *yg, int stride, const R *tabV, const R *tabA, int Mg, R vmax, R amax, R &gr) {
+  const int lane = threadIdx.x & 31, k = lane & 7, base = lane & ~7;
+  const bool live = lane < 24;
+  R cax[NC];
+#pragma unroll
+  for (int l = 0; l < NC; ++l) cax[l] = __shfl_sync(0xffffffffu, c, base + l);
+  R Floc = R(0);
+  gr = R(0);
+  if (live) {  // cost c^T Q(T) c = T^-7 ch^T Qh ch (rows k >= p only)
+    R acc = R(0);
+#pragma unroll
+    for (int l = 0; l < NC; ++l) acc += L.q[l] * cax[l];
+    Floc += s[7] * c * acc;
+    gr = R(2) * s[7] * acc;
+  }
+  R dS = R(0), dE = R(0);
+  if (live && k < ND) {  // consensus rows, E-masked at the trajectory's ends
+    R acc = R(0);
+#pragma unroll
+    for (int m = 0; m < NC; ++m) acc += L.fr[m] * cax[m];
+    const R a0 = (first && k >= PO) ? R(0) : L.fk * s[k] * c - w0;
+    const R a1 = (last && k >= PO) ? R(0) : s[k] * acc - w1;
+    Floc += R(0.5) * rho * (a0 * a0 + a1 * a1);
+    dS = s[k] * a0;
+    dE = s[k] * a1;
+  }
+  {
+    R acc = (live && k < ND) ? L.fk * dS : R(0);
+#pragma unroll
+    for (int r = 0; r < ND; ++r) {
+      const R dEr = __shfl_sync(0xffffffffu, dE, base + r);
+      if (live) acc += L.fc[r] * dEr;
+    }
+    gr += rho * acc;
+  }
+  R Fq = R(0);  // terms identical in every lane
+  for (int j = 0; j < Mg; ++j) {
+#pragma unroll
+    for (int kind = 0; kind < 2; ++kind) {
+      const R *tab = kind ? tabA + j * 8 : tabV + j * 8;
+      const R sc_t = kind ? s[2] : s[1];
+      const R gmax = kind ? amax : vmax;
+      const R tk = live ? tab[k] : R(0);
+      const R va = sc_t * wsum8(tk * c);
+      const R v0 = __shfl_sync(0xffffffffu, va, 0), v1 = __shfl_sync(0xffffffffu, va, 8),
+              v2 = __shfl_sync(0xffffffffu, va, 16);
+      const R h = v0 * v0 + v1 * v1 + v2 * v2 - gmax * gmax;
+      if (h > R(0)) {
+        const R g = h * h;
+        const R y = yg[(j * 2 + kind) * stride];
+        Fq += R(0.5) * rho * g * g + y * g;
+        gr += (rho * g + y) * R(4) * h * sc_t * va * tk;
+      }
+    }
+  }
+  return wsum(Floc) + Fq;
+}
+
+template <class R>
+__device__ __forceinline__ R wdot(R x, R y) { return wsum(x * y); }
+
+// the numerical local step of one segment by the calling warp; writes the
+// lane's coefficient to *c_out and returns the L-BFGS iteration count
+template <class R>
+__device__ int numeric_step_warp(const R (&Grow)[NC], const R (&s)[NC], R w0, R w1, R rho, bool first, bool last,
+                                 R *yg, int stride, const R *tabV, const R *tabA, int Mg, R vmax, R amax, int mem,
+                                 int max_it, R tol, R &c_out) {
+  const int lane = threadIdx.x & 31, k = lane & 7, base = lane & ~7;
+  const bool live = lane < 24;
+  WLane<R> L;
+  wlane_init(L);
+  // start: minimiser of the quadratic part, rhs = rho Mh^T E w
+  R oS = (live && k < ND && !(first && k >= PO)) ? s[k] * w0 : R(0);
+  R oE = (live && k < ND && !(last && k >= PO)) ? s[k] * w1 : R(0);
+  R rhs = (live && k < ND) ? L.fk * oS : R(0);
+#pragma unroll
+  for (int r = 0; r < ND; ++r) {
+    const R oEr = __shfl_sync(0xffffffffu, oE, base + r);
+    if (live) rhs += L.fc[r] * oEr;
+  }
+  rhs *= rho;
+  R c = wapply_g(Grow, rhs);
+  R scale = wdot(rhs, c);
+  if (!(scale > R(0))) scale = R(1);
+  R g;
+  R Fv = wnum_F(c, w0, w1, L, s, rho, first, last, yg, stride, tabV, tabA, Mg, vmax, amax, g);
+  R Sh[LBFGS_MAX_MEM], Yh[LBFGS_MAX_MEM], rh[LBFGS_MAX_MEM], al[LBFGS_MAX_MEM];  // [0] = newest pair
+#pragma unroll
+  for (int q = 0; q < LBFGS_MAX_MEM; ++q) { Sh[q] = Yh[q] = rh[q] = al[q] = R(0); }
+  if (mem > LBFGS_MAX_MEM) mem = LBFGS_MAX_MEM;
+  if (mem < 1) mem = 1;
+  int npair = 0, it = 0;
+  for (it = 0; it < max_it; ++it) {
+    R d = wapply_g(Grow, g);
+    if (!(wdot(g, d) > tol * tol * scale)) break;
+    R xn = g;
+#pragma unroll
+    for (int q = 0; q < LBFGS_MAX_MEM; ++q)
+      if (q < npair) {
+        al[q] = rh[q] * wdot(Sh[q], xn);
+        xn -= al[q] * Yh[q];
+      }
+    d = wapply_g(Grow, xn);
+#pragma unroll
+    for (int q = LBFGS_MAX_MEM - 1; q >= 0; --q)
+      if (q < npair) {
+        const R be = rh[q] * wdot(Yh[q], d);
+        d += (al[q] - be) * Sh[q];
+      }
+    d = -d;
+    R gd = wdot(g, d);
+    if (!(gd < R(0))) {  // not a descent direction: restart from the preconditioned gradient
+      d = -wapply_g(Grow, g);
+      gd = wdot(g, d);
+      npair = 0;
+    }
+    R step = R(1), Fn = Fv, gn = g, x = c;
+    bool ok = false;
+    for (int bt = 0; bt < 30; ++bt) {
+      x = c + step * d;
+      Fn = wnum_F(x, w0, w1, L, s, rho, first, last, yg, stride, tabV, tabA, Mg, vmax, amax, gn);
+      if (Fn <= Fv + R(1e-4) * step * gd) { ok = true; break; }
+      step *= R(0.5);
+    }
+    if (!ok) break;
+    const R sn = x - c, yn = gn - g;
+    const R sy = wdot(sn, yn);
+    if (sy > R(0)) {
+#pragma unroll
+      for (int q = LBFGS_MAX_MEM - 1; q > 0; --q) { Sh[q] = Sh[q - 1]; Yh[q] = Yh[q - 1]; rh[q] = rh[q - 1]; }
+      Sh[0] = sn;
+      Yh[0] = yn;
+      rh[0] = R(1) / sy;
+      if (npair < mem) ++npair;
+    }
+    c = x;
+    g = gn;
+    Fv = Fn;
+  }
+  // general-constraint duals (Eq. 17 dual update, y += rho g)
+  for (int j = 0; j < Mg; ++j) {
+#pragma unroll
+    for (int kind = 0; kind < 2; ++kind) {
+      const R *tab = kind ? tabA + j * 8 : tabV + j * 8;
+      const R sc_t = kind ? s[2] : s[1];
+      const R gmax = kind ? amax : vmax;
+      const R va = sc_t * wsum8((live ? tab[k] : R(0)) * c);
+      const R v0 = __shfl_sync(0xffffffffu, va, 0), v1 = __shfl_sync(0xffffffffu, va, 8),
+              v2 = __shfl_sync(0xffffffffu, va, 16);
+      const R h = v0 * v0 + v1 * v1 + v2 * v2 - gmax * gmax;
+      if (h > R(0) && lane == 0) yg[(j * 2 + kind) * stride] += rho * h * h;
+    }
+  }
+  c_out = c;
   return it;
 }
 

@@ -151,9 +151,14 @@ __global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
       }
     R ch[AX][NC];
     if (GEN) {
+      const bool defer = A.nwork != nullptr;
       const int its = numeric_step<R>(sc, w, rho, first, last, (R *)A.ygen + g, A.S, tabGV, tabGA, Mg,
                                       R(p.gen_vmax[b]), R(p.gen_amax[b]), p.lbfgs_mem, p.lbfgs_max_iters,
-                                      R(p.lbfgs_tol), ch);
+                                      R(p.lbfgs_tol), ch, defer);
+      if (its < 0) {  // a violated bound: one warp per such segment solves it (stream_numeric_warp)
+        A.work[atomicAdd(A.nwork, 1)] = x;
+        continue;
+      }
       if (A.inner_iters) A.inner_iters[g] += its;
     } else {
       R wS[AX][ND], wE[AX][ND];
@@ -191,6 +196,73 @@ __global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
 #pragma unroll
       for (int q = 0; q < NC; ++q) chg[(size_t)(a * NC + q) * A.S + g] = ch[a][q];
     }
+  }
+}
+
+// The numerical step for the segments stream_local deferred (a bound violated
+// at the minimiser of the quadratic part): one warp per segment, lanes over
+// (axis, coefficient); writes the coefficients, the end derivatives, the duals y
+// and the L-BFGS iteration count.  The order of the work list does not matter:
+// each segment's result depends only on its own data.
+template <class R>
+__global__ void __launch_bounds__(256) stream_numeric_warp(const StreamArgs A) {
+  const DevProblem &p = A.p;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int Mg = p.M_gen;
+  R *tabGV = (R *)smem, *tabGA = tabGV + 8 * Mg;
+  fill_sample_table(tabGV, Mg, 1, threadIdx.x, blockDim.x);
+  fill_accel_table(tabGA, Mg, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const R *z = (const R *)A.z, *uL = (const R *)A.uL, *uRp = (const R *)A.uRp, *uR0 = (const R *)A.uR0;
+  const R *Gp = (const R *)A.G;
+  R *eS = (R *)A.eS, *eE = (R *)A.eE, *chg = (R *)A.ch;
+  const bool pin = p.mode == 0;
+  const int lane = threadIdx.x & 31, k = lane & 7, a = lane >> 3;
+  const bool live = lane < 24;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int n = *A.nwork;
+  for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < n; item += nwarps) {
+    const int x = A.work[item];
+    int t, b, i, N, g;
+    stream_locate(A, x, t, b, i, N, g);
+    const R rho = R(A.rho_t[t]);
+    const bool first = i == 0, last = i == N - 1;
+    const int jS = g + b, jE = g + b + 1;
+    R s[NC];
+    inv_powers(R(p.durations[g]), s);
+    R Grow[NC];
+#pragma unroll
+    for (int l = 0; l < NC; ++l) Grow[l] = live ? Gp[(size_t)gidx(k, l) * A.S + g] : R(0);
+    R w0 = R(0), w1 = R(0);  // E (z~ - u) at the two ends, row (a, k)
+    if (live && k < ND) {
+      const int r = k;
+      const size_t row = (size_t)(a * ND + r) * A.Jn;
+      R us;
+      if (first) us = (r < PO) ? uR0[(size_t)(a * PO + r) * p.B + b] : R(0);
+      else if (pin && r == 0) us = uRp[(size_t)a * A.Jn + jS];
+      else us = -uL[row + jS];
+      w0 = (first && r >= PO) ? R(0) : z[row + jS] - us;
+      w1 = (last && r >= PO) ? R(0) : z[row + jE] - uL[row + jE];
+    }
+    R c;
+    const int its = numeric_step_warp<R>(Grow, s, w0, w1, rho, first, last, (R *)A.ygen + g, A.S, tabGV, tabGA,
+                                         Mg, R(p.gen_vmax[b]), R(p.gen_amax[b]), p.lbfgs_mem, p.lbfgs_max_iters,
+                                         R(p.lbfgs_tol), c);
+    // outputs: coefficients, end derivatives (rows of M(T) c, Sec. III-D.1)
+    const int base = lane & ~7;
+    R cax[NC];
+#pragma unroll
+    for (int l = 0; l < NC; ++l) cax[l] = __shfl_sync(0xffffffffu, c, base + l);
+    if (live) {
+      chg[(size_t)(a * NC + k) * A.S + g] = c;
+      if (k < ND) {
+        R acc = R(0);
+        for (int m = k; m < NC; ++m) acc += R(falling_rt(m, k)) * cax[m];
+        eS[(size_t)(a * ND + k) * A.S + g] = R(fact_rt(k)) * s[k] * c;
+        eE[(size_t)(a * ND + k) * A.S + g] = s[k] * acc;
+      }
+    }
+    if (lane == 0 && A.inner_iters) A.inner_iters[g] += its;
   }
 }
 
@@ -456,10 +528,15 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
   Ak.cev = cev;
   // one iteration; `first` selects the Init-dependent local step, the
   // final iteration's evaluation names its k unless it is a periodic one
+  const bool gen = (fam & FAM_GEN) != 0 && A.nwork;
+  int wblocks = (A.total + 7) / 8;  // 8 warps per block, one warp per deferred segment
+  if (wblocks > 152 * 16) wblocks = 152 * 16;
   auto iteration = [&](cudaStream_t s, int k, bool first) {
     const bool per = periodic && ((k + 1) % cev == 0);
     const bool check = per || (k == K - 1);
+    if (gen) cudaMemsetAsync(Ak.nwork, 0, sizeof(int), s);
     local<<<blocks, threads, tab_bytes, s>>>(Ak, first ? 0 : 1);
+    if (gen) stream_numeric_warp<R><<<wblocks, 256, sizeof(R) * 16 * (size_t)p.M_gen, s>>>(Ak);
     stream_junction<R><<<blocks, threads, 0, s>>>(Ak, check ? 1 : 0);
     if (check) {
       stream_dual<R><<<blocks, threads, 0, s>>>(Ak);
