@@ -499,6 +499,34 @@ def run_suite(args):
         grad_line(top, oracle)
     if want("general_full"):
         general_full_line(top)
+    if want("shared"):
+        gpu_case("batch with one duration per trajectory (64-trajectory subset for the oracle)",
+                 W.batch(shared_T=True).subset(list(range(64))), precs=("fp32", "fp64"))
+        shared_duration_line(top)
+
+
+def shared_duration_line(top):
+    """The full 4096-trajectory batch with durations shared per trajectory
+    against per-segment durations: the precompute reuses the first interior
+    segment's inverse for every interior segment of the same duration."""
+    line = {"suite": "batch 4096, shared vs per-segment durations (FP32, 300 iterations)"}
+    for kind, w in (("per_segment_T", W.batch()), ("shared_T", W.batch(shared_T=True))):
+        s = top.Solver(max_batch=w.B, max_segments=w.S, precision="fp32")
+        tensors = s.device_inputs(w)
+        out = s.alloc_result(w.B, w.S, w.max_iters)
+        s.solve(w, tensors=tensors, out=out)
+        top.top_set_profiling(s.handle, True)
+        ms, kts = [], []
+        for _ in range(5):
+            ms.append(_timed_solve(s, w, tensors, out))
+            kts.append(top.top_kernel_times(s.handle, 4)[1])
+        top.top_set_profiling(s.handle, False)
+        kt = np.median(np.array(kts), axis=0)
+        line[kind] = {"segments": w.S, "ms": float(np.median(ms)), "precompute_ms": float(kt[0]),
+                      "resident_ms": float(kt[1]), "cluster_ms": float(kt[3]),
+                      "segment_iterations_per_s": w.S * w.max_iters / (float(np.median(ms)) / 1000)}
+        s.close()
+    print(json.dumps(line), flush=True)
 
 
 def speed_bound_comparison(top, oracle):
@@ -702,7 +730,7 @@ def main():
     ap.add_argument("--no-tolerance", action="store_true", help="skip the time-to-tolerance measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep 512 segments per CTA (skip top_autotune)")
     ap.add_argument("--only", default="", help="with --suite: comma-separated subset of single_box, corridor, "
-                    "batch, adaptive, general, polytope, speed, segments, timealloc, grad, general_full")
+                    "batch, adaptive, general, polytope, speed, segments, timealloc, grad, general_full, shared")
     ap.add_argument("--suite", action="store_true",
                     help="one JSON line per benchmark workload (single_box, corridor, batch, grad_batch, general)")
     ap.add_argument("--trajectories", type=int, default=4096,

@@ -42,6 +42,7 @@ struct top_handle {
   size_t pstage_bytes = 0;
   unsigned char *d_aux = nullptr;     // top_sample / top_time_alloc workspace (grow-only)
   size_t aux_bytes = 0;
+  int *d_copy = nullptr;              // [max_segments]: shared-duration reuse map of the precompute
   void *d_ypoly = nullptr;            // polytope slack state of the cluster form (grow-only)
   size_t ypoly_bytes = 0;
   // the cluster-resident launches run on a side stream, concurrently with the
@@ -361,6 +362,7 @@ void top_destroy(top_handle *h) {
   cudaFree(h->d_pstage);
   cudaFree(h->d_aux);
   cudaFree(h->d_ypoly);
+  cudaFree(h->d_copy);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   if (h->join_ev) cudaEventDestroy(h->join_ev);
@@ -404,6 +406,7 @@ int top_create(const top_config *cfg, top_handle **out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->G, (size_t)NG * S * rbytes(h));
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_packs, sizeof(Pack) * std::max(S, B));
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_copy, sizeof(int) * S);
   if (e == cudaSuccess) {
     h->stage_bytes = stage_plan((int)B, (int)S).total;
     e = cudaMalloc((void **)&h->d_stage, h->stage_bytes);
@@ -576,7 +579,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
       pdata = PolyData{pbase, pbase + bG, pbase + bG + bU, pbase + bG + bU + bN};
       e = launch_kinv_poly(dp, pb.rho, fp64, pdata, h->d_err, st);
     } else {
-      e = launch_kinv(dp, pb.rho, fp64 ? nullptr : h->G, fp64 ? h->G : nullptr, h->d_err, st);
+      e = launch_kinv(dp, pb.rho, fp64 ? nullptr : h->G, fp64 ? h->G : nullptr, h->d_err, st, h->d_copy);
     }
     if (e) return cuda_fail(h, (cudaError_t)e);
     if (adapt) {
@@ -639,7 +642,8 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     if (h->profiling) { cudaEventRecord(h->ev[3], st); h->ran[1] = true; }
   }
   // ---- cluster-resident form for trajectories longer than a CTA but within a cluster ----
-  // (closed-form step with the box / ball / velocity-norm families and a fixed rho)
+  // (closed-form step with the box / ball / velocity-norm / polytope families, fixed or
+  // adaptive rho)
   // polytope trajectories of any length use the cluster form (a cluster of one CTA
   // for short ones): the resident packs have no room for their per-axis inverses
   int ccap = 0, cmax = 0;

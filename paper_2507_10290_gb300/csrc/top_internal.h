@@ -189,7 +189,10 @@ inline cudaError_t func_attr_once(const void *kern, cudaFuncAttribute attr, int 
 }
 
 // launchers (defined in the .cu files)
-int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_flag, void *stream);
+// copy (optional, [S] ints of workspace): reuse the inverse of the first interior
+// segment for interior segments of the same duration
+int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_flag, void *stream,
+                int *copy = nullptr);
 int launch_keig(const DevProblem &p, void *E32, void *E64, int *err_flag, void *stream);
 int launch_kinv_poly(const DevProblem &p, double rho, bool fp64, const PolyData &out, int *err_flag, void *stream);
 int launch_fill(double *x, int n, double v, void *stream);

@@ -179,11 +179,24 @@ __device__ __forceinline__ void store_inverse(const double (&A)[NG], const doubl
     }
 }
 
+// Interior segments of a trajectory with the same duration as its first
+// interior segment have the same local matrix (it depends on T, rho, the
+// sample counts and the end masks only): with `copy` non-null they are marked
+// copy[g] = that segment and left to kinv_copy_kernel, so a trajectory whose
+// segments share one duration costs three inversions instead of N.
 template <bool SAMPLES>
 __global__ void __launch_bounds__(128) kinv_kernel(const DevProblem p, double rho, float *__restrict__ G32,
-                                                   double *__restrict__ G64, int *__restrict__ err) {
+                                                   double *__restrict__ G64, int *__restrict__ err,
+                                                   int *__restrict__ copy) {
   const int S = p.S;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < S; g += gridDim.x * blockDim.x) {
+    if (copy) {
+      const int b = find_traj(p.seg_offset, p.B, g);
+      const int g0 = p.seg_offset[b], N = p.seg_offset[b + 1] - g0, i = g - g0;
+      const bool same = i >= 2 && i <= N - 2 && p.durations[g] == p.durations[g0 + 1];
+      copy[g] = same ? g0 + 1 : -1;
+      if (same) continue;
+    }
     bool first, last;
     double s[NC];
     if (!segment_setup(p, g, first, last, s)) {
@@ -452,16 +465,35 @@ int launch_fill(double *x, int n, double v, void *stream) {
   return (int)cudaGetLastError();
 }
 
-int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_flag, void *stream) {
+__global__ void kinv_copy_kernel(const int *__restrict__ copy, int S, float *__restrict__ G32,
+                                 double *__restrict__ G64) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < S; g += gridDim.x * blockDim.x) {
+    const int src = copy[g];
+    if (src < 0) continue;
+#pragma unroll 4
+    for (int q = 0; q < NG; ++q) {
+      if (G64) G64[(size_t)q * S + g] = G64[(size_t)q * S + src];
+      if (G32) G32[(size_t)q * S + g] = G32[(size_t)q * S + src];
+    }
+  }
+}
+
+int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_flag, void *stream, int *copy) {
   if (p.S == 0) return 0;
   const int threads = 128;
   int blocks = (p.S + threads - 1) / threads;
   if (blocks > 152 * 32) blocks = 152 * 32;
   const bool samples = p.inner == 0 && (p.M_box > 0 || p.M_ball > 0 || p.M_vn > 0);
+  cudaStream_t st = (cudaStream_t)stream;
   if (samples)
-    kinv_kernel<true><<<blocks, threads, 0, (cudaStream_t)stream>>>(p, rho, (float *)G32, (double *)G64, err_flag);
+    kinv_kernel<true><<<blocks, threads, 0, st>>>(p, rho, (float *)G32, (double *)G64, err_flag, copy);
   else
-    kinv_kernel<false><<<blocks, threads, 0, (cudaStream_t)stream>>>(p, rho, (float *)G32, (double *)G64, err_flag);
+    kinv_kernel<false><<<blocks, threads, 0, st>>>(p, rho, (float *)G32, (double *)G64, err_flag, copy);
+  if (copy) {
+    int cb = (p.S + 255) / 256;
+    if (cb > 152 * 16) cb = 152 * 16;
+    kinv_copy_kernel<<<cb, 256, 0, st>>>(copy, p.S, (float *)G32, (double *)G64);
+  }
   return (int)cudaGetLastError();
 }
 

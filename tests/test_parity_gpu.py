@@ -109,6 +109,27 @@ def test_batch_subset_300_iterations(T, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_shared_durations(T, precision):
+    """Trajectories whose segments share one duration: the precompute inverts
+    the first interior segment and reuses it for the other interior segments
+    of that duration.  Shared batch, lengths 0..6 around the first/last
+    special cases, one interior duration changed, with and without sample rows."""
+    w = W.batch(B=48, shared_T=True, n_min=8, n_max=64)
+    compare(to_np(solver(T, precision).solve(w)), oracle.solve(w), w, TOL[precision])
+    Ns = [0, 1, 2, 3, 4, 5, 6, 9]
+    e = W.tiny(seed=31, N=Ns, mode="pin")
+    off = e.seg_offset
+    Tn = e.durations.copy()
+    for b in range(len(Ns)):
+        Tn[off[b]:off[b + 1]] = 0.7 + 0.1 * b
+    Tn[off[7] + 4] = 1.3                     # one interior segment differs
+    Tn[off[6] + 1] = 0.9                     # the reference segment itself differs
+    e = e.with_(durations=Tn, max_iters=120)
+    for case in (e, e.with_(mode="free", M_box=8, vbox=np.full(len(Ns), 1.2))):
+        compare(to_np(solver(T, precision).solve(case)), oracle.solve(case), case, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_corridor_box_and_ball(T, precision):
     N = 64 if precision == "fp64" else 128
     w = W.corridor(N=N)
