@@ -42,7 +42,7 @@ struct top_handle {
   size_t pstage_bytes = 0;
   unsigned char *d_aux = nullptr;     // top_sample / top_time_alloc workspace (grow-only)
   size_t aux_bytes = 0;
-  int *d_copy = nullptr;              // [max_segments]: shared-duration reuse map of the precompute
+  int *d_copy = nullptr;              // [2 max_segments + 1]: shared-duration reuse map and inversion list
   void *d_ypoly = nullptr;            // polytope slack state of the cluster form (grow-only)
   size_t ypoly_bytes = 0;
   // the cluster-resident launches run on a side stream, concurrently with the
@@ -406,7 +406,7 @@ int top_create(const top_config *cfg, top_handle **out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->G, (size_t)NG * S * rbytes(h));
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_packs, sizeof(Pack) * std::max(S, B));
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_copy, sizeof(int) * S);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_copy, sizeof(int) * (2 * (size_t)S + 1));
   if (e == cudaSuccess) {
     h->stage_bytes = stage_plan((int)B, (int)S).total;
     e = cudaMalloc((void **)&h->d_stage, h->stage_bytes);

@@ -189,8 +189,8 @@ inline cudaError_t func_attr_once(const void *kern, cudaFuncAttribute attr, int 
 }
 
 // launchers (defined in the .cu files)
-// copy (optional, [S] ints of workspace): reuse the inverse of the first interior
-// segment for interior segments of the same duration
+// copy (optional, [2S + 1] ints of workspace): reuse the inverse of the first
+// interior segment for interior segments of the same duration
 int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_flag, void *stream,
                 int *copy = nullptr);
 int launch_keig(const DevProblem &p, void *E32, void *E64, int *err_flag, void *stream);

@@ -181,22 +181,42 @@ __device__ __forceinline__ void store_inverse(const double (&A)[NG], const doubl
 
 // Interior segments of a trajectory with the same duration as its first
 // interior segment have the same local matrix (it depends on T, rho, the
-// sample counts and the end masks only): with `copy` non-null they are marked
-// copy[g] = that segment and left to kinv_copy_kernel, so a trajectory whose
-// segments share one duration costs three inversions instead of N.
-template <bool SAMPLES>
-__global__ void __launch_bounds__(128) kinv_kernel(const DevProblem p, double rho, float *__restrict__ G32,
-                                                   double *__restrict__ G64, int *__restrict__ err,
-                                                   int *__restrict__ copy) {
-  const int S = p.S;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < S; g += gridDim.x * blockDim.x) {
-    if (copy) {
+// sample counts and the end masks only).  kinv_mark_kernel marks them
+// copy[g] = that segment and lists every other segment in `list` (list[0] =
+// count, warp-aggregated appends, so a warp's entries stay in segment order);
+// kinv_kernel then inverts the listed segments only and kinv_copy_kernel
+// fills in the rest: a trajectory whose segments share one duration costs
+// three inversions instead of N.
+__global__ void kinv_mark_kernel(const DevProblem p, int *__restrict__ copy, int *__restrict__ list) {
+  const int S = p.S, lane = threadIdx.x & 31;
+  for (long long w0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < S;
+       w0 += (long long)gridDim.x * blockDim.x) {
+    const int g = int(w0) + lane;
+    bool rep = false;
+    if (g < S) {
       const int b = find_traj(p.seg_offset, p.B, g);
       const int g0 = p.seg_offset[b], N = p.seg_offset[b + 1] - g0, i = g - g0;
       const bool same = i >= 2 && i <= N - 2 && p.durations[g] == p.durations[g0 + 1];
       copy[g] = same ? g0 + 1 : -1;
-      if (same) continue;
+      rep = !same;
     }
+    const unsigned m = __ballot_sync(0xffffffffu, rep);
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(list, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (rep) list[1 + base + __popc(m & ((1u << lane) - 1u))] = g;
+  }
+}
+
+// one thread per listed segment (every segment when `list` is null)
+template <bool SAMPLES>
+__global__ void __launch_bounds__(128) kinv_kernel(const DevProblem p, double rho, float *__restrict__ G32,
+                                                   double *__restrict__ G64, int *__restrict__ err,
+                                                   const int *__restrict__ list) {
+  const int S = p.S;
+  const int n = list ? list[0] : S;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+    const int g = list ? list[1 + x] : x;
     bool first, last;
     double s[NC];
     if (!segment_setup(p, g, first, last, s)) {
@@ -485,10 +505,18 @@ int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_
   if (blocks > 152 * 32) blocks = 152 * 32;
   const bool samples = p.inner == 0 && (p.M_box > 0 || p.M_ball > 0 || p.M_vn > 0);
   cudaStream_t st = (cudaStream_t)stream;
+  int *list = copy ? copy + p.S : nullptr;
+  if (copy) {
+    cudaError_t e = cudaMemsetAsync(list, 0, sizeof(int), st);
+    if (e != cudaSuccess) return (int)e;
+    int mb = (p.S + 255) / 256;
+    if (mb > 152 * 16) mb = 152 * 16;
+    kinv_mark_kernel<<<mb, 256, 0, st>>>(p, copy, list);
+  }
   if (samples)
-    kinv_kernel<true><<<blocks, threads, 0, st>>>(p, rho, (float *)G32, (double *)G64, err_flag, copy);
+    kinv_kernel<true><<<blocks, threads, 0, st>>>(p, rho, (float *)G32, (double *)G64, err_flag, list);
   else
-    kinv_kernel<false><<<blocks, threads, 0, st>>>(p, rho, (float *)G32, (double *)G64, err_flag, copy);
+    kinv_kernel<false><<<blocks, threads, 0, st>>>(p, rho, (float *)G32, (double *)G64, err_flag, list);
   if (copy) {
     int cb = (p.S + 255) / 256;
     if (cb > 152 * 16) cb = 152 * 16;
