@@ -487,7 +487,7 @@ def run_suite(args):
     if want("general"):
         gpu_case("general (N=1000, numerical step)", W.general(N=1000), tol_eps=1e-4)
     if want("polytope"):
-        gpu_case("polytope corridor (N=1024, F=8 faces at M=8, box rows at M=16; streaming)",
+        gpu_case("polytope corridor (N=1024, F=8 faces at M=8, box rows at M=16; cluster-resident)",
                  W.polytope_corridor(), tol_eps=1e-4)
     if want("speed"):
         speed_bound_comparison(top, oracle)

@@ -93,6 +93,42 @@ def test_directional_derivatives_full_size(T):
             assert abs(ad - fd) <= 1e-3 * max(abs(fd), 1e-12), (b, ad, fd)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp32", 1e-3)])
+def test_converged_gradient_equals_the_centralized_qp_gradient(T, precision, tol):
+    """Six PIN segments, rho = 10, K = 1000: the iteration has reached its
+    fixed point (the unrolled cost equals the centralized optimum to 1e-12),
+    so the adjoint must equal the gradient of the optimal value J*(P, T) of
+    the centralized QP, here central differences (h = 1e-5, FP64) of its
+    direct solve (the C^6 spline of the optimality conditions)."""
+    from oracle import centralized as C
+    w0 = W.tiny(seed=4, N=[6], mode="pin", T_range=(1.6, 2.4), step=2.0)
+    w = w0.with_(durations=1.4 * w0.durations, max_iters=1000, rho=10.0)
+
+    def Jstar(P, Td):
+        return C.segment_cost(C.pin_spline(P, Td, w.start_state[0], w.end_state[0]), Td)
+
+    assert abs(oracle.solve(w)["cost"][0] / Jstar(w.waypoints, w.durations) - 1) < 1e-10
+    h = 1e-5
+    gP = np.zeros_like(w.waypoints)
+    gT = np.zeros_like(w.durations)
+    for idx in np.ndindex(*w.waypoints.shape):
+        Pp, Pm = w.waypoints.copy(), w.waypoints.copy()
+        Pp[idx] += h
+        Pm[idx] -= h
+        gP[idx] = (Jstar(Pp, w.durations) - Jstar(Pm, w.durations)) / (2 * h)
+    for i in range(w.S):
+        Tp, Tm = w.durations.copy(), w.durations.copy()
+        Tp[i] += h
+        Tm[i] -= h
+        gT[i] = (Jstar(w.waypoints, Tp) - Jstar(w.waypoints, Tm)) / (2 * h)
+    s = T.Solver(max_batch=1, max_segments=w.S, precision=precision)
+    dw, dT = s.grad(w)
+    s.close()
+    dw, dT = dw.cpu().numpy(), dT.cpu().numpy()
+    assert rel(dT, gT) < tol, (rel(dT, gT), dT, gT)
+    assert rel(dw, gP) < tol, rel(dw, gP)
+
+
 def test_autograd_function_matches_top_grad(T):
     import torch
     from paper_2507_10290_gb300.autograd import TopCost
