@@ -560,7 +560,9 @@ def speed_bound_comparison(top, oracle):
     N, eps, cap = 256, 1e-4, 20000
     line = {"suite": "speed bound: projection (Eq. 14, 18f-g) vs numerical step (Eq. 15-17)",
             "workload": f"speed_limit N={N}, M=16, FREE, v_max = 1.6 x end-to-end mean speed; numerical "
-                        "step with the library's L-BFGS defaults (50 iterations, tol 1e-6 FP32 / 1e-12 FP64)",
+                        "step with the library's L-BFGS defaults (50 iterations, tol 1e-6 FP32 / 1e-12 FP64); "
+                        "numerical step one warp per segment in FP64, one thread per segment in FP32 "
+                        "(fp32_warp: the warp form in FP32)",
             "segments": N, "to_tolerance": {"eps": eps, "cap": cap}}
     sols = {}
     for inner in ("closed", "numeric"):
@@ -569,8 +571,9 @@ def speed_bound_comparison(top, oracle):
         t0 = time.perf_counter()
         oracle.solve(w.with_(max_iters=20), lbfgs_tol=1e-12, lbfgs_max_iters=50)
         entry = {"oracle_ms_per_iteration_1_core": 1000 * (time.perf_counter() - t0) / 20}
-        for prec in ("fp32", "fp64"):
-            s = top.Solver(max_batch=1, max_segments=N, precision=prec, max_samples=16)
+        forms = [("fp32", "auto"), ("fp64", "auto")] + ([("fp32", "warp")] if inner == "numeric" else [])
+        for prec, form in forms:
+            s = top.Solver(max_batch=1, max_segments=N, precision=prec, max_samples=16, numeric_form=form)
             tensors = s.device_inputs(w)
             out = s.alloc_result(1, N, w.max_iters)
             s.solve(w, tensors=tensors, out=out, max_iters=5)
@@ -581,11 +584,12 @@ def speed_bound_comparison(top, oracle):
             out2 = s.alloc_result(1, N, cap_here)
             mt = _timed_solve(s, wt, tensors, out2)
             g = {k: v.cpu().numpy() for k, v in out2.items()}
-            entry[prec] = {"us_per_iteration": 1000 * ms / w.max_iters, "cap": cap_here,
+            entry[prec if form == "auto" else f"{prec}_{form}"] = {"us_per_iteration": 1000 * ms / w.max_iters, "cap": cap_here,
                            "to_tolerance_ms": mt, "iterations": int(g["iters"][0]), "status": int(g["status"][0]),
                            "cost": float(g["cost"][0]),
                            "max_speed_excess": max_speed_excess(g["coeffs"], w.durations, 16, vmax)}
-            sols[(inner, prec)] = g["coeffs"]
+            if form == "auto":
+                sols[(inner, prec)] = g["coeffs"]
             s.close()
         line[inner] = entry
     sc = W.speed_limit(N=N).durations[:, None, None] ** np.arange(8)

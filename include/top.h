@@ -70,6 +70,7 @@ enum top_mode      { TOP_PIN = 0, TOP_FREE = 1 };      /* interior waypoints pin
 enum top_inner     { TOP_CLOSED_FORM = 0, TOP_NUMERIC = 1 };
 enum top_memory    { TOP_MEM_DEVICE = 0, TOP_MEM_HOST = 1 };
 enum top_schedule  { TOP_SCHED_AUTO = 0, TOP_SCHED_RESIDENT = 1, TOP_SCHED_STREAM = 2 };
+enum top_numeric_form { TOP_NUMERIC_AUTO = 0, TOP_NUMERIC_WARP = 1, TOP_NUMERIC_THREAD = 2 };
 
 typedef struct top_handle top_handle;
 
@@ -87,7 +88,14 @@ typedef struct top_config {
                              TOP_SCHED_STREAM: streaming only */
   int32_t segs_per_cta;   /* resident-form capacity per CTA; 0 = chosen from shared-memory size */
   int32_t ckpt_interval;  /* adjoint checkpoint interval in iterations (0 = 10) */
-  int32_t reserved[9];    /* must be zero */
+  int32_t numeric_form;   /* how the numerical local step (Sec. III-C.3) runs, enum top_numeric_form:
+                             TOP_NUMERIC_WARP: a segment whose general bound is violated at the minimiser
+                             of the quadratic part is solved by one warp (lanes over axis x coefficient and
+                             over the (sample, bound) pairs), at the price of one more launch per iteration;
+                             TOP_NUMERIC_THREAD: one thread per segment, no extra launch;
+                             TOP_NUMERIC_AUTO: WARP in FP64, THREAD in FP32.  Results agree within the
+                             L-BFGS tolerance, not bit for bit. */
+  int32_t reserved[8];    /* must be zero */
 } top_config;
 
 /* One batch.  Pointers are device pointers for TOP_MEM_DEVICE and host

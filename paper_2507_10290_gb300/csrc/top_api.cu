@@ -392,7 +392,8 @@ int top_create(const top_config *cfg, top_handle **out) {
   if (cfg->max_batch <= 0 || cfg->max_segments <= 0 || cfg->max_samples < 0) return TOP_E_INVAL;
   if (cfg->precision != TOP_FP32 && cfg->precision != TOP_FP64) return TOP_E_INVAL;
   if (cfg->schedule < TOP_SCHED_AUTO || cfg->schedule > TOP_SCHED_STREAM) return TOP_E_INVAL;
-  for (int q = 0; q < 9; ++q)
+  if (cfg->numeric_form < TOP_NUMERIC_AUTO || cfg->numeric_form > TOP_NUMERIC_THREAD) return TOP_E_INVAL;
+  for (int q = 0; q < 8; ++q)
     if (cfg->reserved[q] != 0) return TOP_E_INVAL;
   top_handle *h = new (std::nothrow) top_handle;
   if (!h) return TOP_E_NOMEM;
@@ -791,10 +792,12 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     sa.done = (int *)(base + o_done); sa.tr_rp = (double *)(base + o_trp); sa.tr_rd = (double *)(base + o_trd);
     sa.rho_t = (double *)(base + o_rho); sa.fac_t = (double *)(base + o_fac);
     sa.kcount = (int *)(base + o_kc); sa.cev = 1;
-    // the warp-per-segment numerical step pays in FP64 (4x on active bounds); in FP32 a
-    // thread per segment is as fast and needs no extra launches per iteration
-    sa.nwork = (Mg > 0 && fp64) ? (int *)(base + o_nw) : nullptr;
-    sa.work = (Mg > 0 && fp64) ? (int *)(base + o_nw) + 1 : nullptr;
+    // segments with a violated general bound: one warp each (an extra launch per
+    // iteration, which only pays where bounds are active), or one thread each
+    const bool warp_num = Mg > 0 && (h->cfg.numeric_form == TOP_NUMERIC_WARP ||
+                                     (h->cfg.numeric_form == TOP_NUMERIC_AUTO && fp64));
+    sa.nwork = warp_num ? (int *)(base + o_nw) : nullptr;
+    sa.work = warp_num ? (int *)(base + o_nw) + 1 : nullptr;
     sa.E = adapt ? h->E : nullptr;
     Range r2("streaming trajectories");
     if (h->profiling) cudaEventRecord(h->ev[4], st);

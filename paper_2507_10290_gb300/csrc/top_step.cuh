@@ -652,15 +652,25 @@ __device__ __forceinline__ void wlane_init(WLane<R> &L) {
   L.fk = R(fact_rt(k));
 }
 
-// the objective of the numerical local step and this lane's gradient entry
+// the objective of the numerical local step and this lane's gradient entry.
+// The general-bound terms take one (sample, kind) pair per lane: lanes 0-15
+// the velocity rows of samples j0 .. j0+15, lanes 16-31 their acceleration
+// rows; each lane reduces its row's gradient weight to three per-axis values
+// in the warp's scratch wsc[3][32], from which lane (axis, coefficient) sums
+// its gradient entry.
 template <class R>
 __device__ R wnum_F(R c, R w0, R w1, const WLane<R> &L, const R (&s)[NC], R rho, bool first, bool last,
-                    const R *yg, int stride, const R *tabV, const R *tabA, int Mg, R vmax, R amax, R &gr) {
+                    const R *yg, int stride, const R *tabV, const R *tabA, int Mg, R vmax, R amax, R *wsc, R &gr) {
   const int lane = threadIdx.x & 31, k = lane & 7, base = lane & ~7;
   const bool live = lane < 24;
-  R cax[NC];
+  R call[AX][NC];  // every coefficient of the segment in every lane
 #pragma unroll
-  for (int l = 0; l < NC; ++l) cax[l] = __shfl_sync(0xffffffffu, c, base + l);
+  for (int a = 0; a < AX; ++a)
+#pragma unroll
+    for (int l = 0; l < NC; ++l) call[a][l] = __shfl_sync(0xffffffffu, c, a * NC + l);
+  R cax[NC];  // this lane's axis
+#pragma unroll
+  for (int l = 0; l < NC; ++l) cax[l] = base == 0 ? call[0][l] : (base == 8 ? call[1][l] : call[2][l]);
   R Floc = R(0);
   gr = R(0);
   if (live) {  // cost c^T Q(T) c = T^-7 ch^T Qh ch (rows k >= p only)
@@ -690,27 +700,48 @@ __device__ R wnum_F(R c, R w0, R w1, const WLane<R> &L, const R (&s)[NC], R rho,
     }
     gr += rho * acc;
   }
-  R Fq = R(0);  // terms identical in every lane
-  for (int j = 0; j < Mg; ++j) {
+  const int kind = lane >> 4;
+  const R sc_t = kind ? s[2] : s[1];
+  const R gmax = kind ? amax : vmax;
+  for (int j0 = 0; j0 < Mg; j0 += 16) {
+    const int jj = j0 + (lane & 15);
+    const bool on = jj < Mg;
+    const R *tab = (kind ? tabA : tabV) + jj * 8;
+    R va[AX] = {R(0), R(0), R(0)};
+    if (on) {
 #pragma unroll
-    for (int kind = 0; kind < 2; ++kind) {
-      const R *tab = kind ? tabA + j * 8 : tabV + j * 8;
-      const R sc_t = kind ? s[2] : s[1];
-      const R gmax = kind ? amax : vmax;
-      const R tk = live ? tab[k] : R(0);
-      const R va = sc_t * wsum8(tk * c);
-      const R v0 = __shfl_sync(0xffffffffu, va, 0), v1 = __shfl_sync(0xffffffffu, va, 8),
-              v2 = __shfl_sync(0xffffffffu, va, 16);
-      const R h = v0 * v0 + v1 * v1 + v2 * v2 - gmax * gmax;
-      if (h > R(0)) {
-        const R g = h * h;
-        const R y = yg[(j * 2 + kind) * stride];
-        Fq += R(0.5) * rho * g * g + y * g;
-        gr += (rho * g + y) * R(4) * h * sc_t * va * tk;
+      for (int q = 0; q < NC; ++q) {
+        const R tq = tab[q];
+#pragma unroll
+        for (int a = 0; a < AX; ++a) va[a] += tq * call[a][q];
       }
+#pragma unroll
+      for (int a = 0; a < AX; ++a) va[a] *= sc_t;
     }
+    const R h = va[0] * va[0] + va[1] * va[1] + va[2] * va[2] - gmax * gmax;
+    R wgt = R(0);
+    if (on && h > R(0)) {
+      const R g = h * h;
+      const R y = yg[(jj * 2 + kind) * stride];
+      Floc += R(0.5) * rho * g * g + y * g;
+      wgt = (rho * g + y) * R(4) * h * sc_t;
+    }
+#pragma unroll
+    for (int a = 0; a < AX; ++a) wsc[a * 32 + lane] = wgt * va[a];
+    __syncwarp();
+    if (live) {
+      const int a = lane >> 3;
+      R acc = R(0);
+#pragma unroll
+      for (int p = 0; p < 32; ++p) {
+        const int jp = j0 + (p & 15);
+        if (jp < Mg) acc += wsc[a * 32 + p] * ((p >> 4) ? tabA : tabV)[jp * 8 + k];
+      }
+      gr += acc;
+    }
+    __syncwarp();  // the scratch is rewritten by the next block of samples
   }
-  return wsum(Floc) + Fq;
+  return wsum(Floc);
 }
 
 template <class R>
@@ -721,7 +752,7 @@ __device__ __forceinline__ R wdot(R x, R y) { return wsum(x * y); }
 template <class R>
 __device__ int numeric_step_warp(const R (&Grow)[NC], const R (&s)[NC], R w0, R w1, R rho, bool first, bool last,
                                  R *yg, int stride, const R *tabV, const R *tabA, int Mg, R vmax, R amax, int mem,
-                                 int max_it, R tol, R &c_out) {
+                                 int max_it, R tol, R *wsc, R &c_out) {
   const int lane = threadIdx.x & 31, k = lane & 7, base = lane & ~7;
   const bool live = lane < 24;
   WLane<R> L;
@@ -740,7 +771,7 @@ __device__ int numeric_step_warp(const R (&Grow)[NC], const R (&s)[NC], R w0, R 
   R scale = wdot(rhs, c);
   if (!(scale > R(0))) scale = R(1);
   R g;
-  R Fv = wnum_F(c, w0, w1, L, s, rho, first, last, yg, stride, tabV, tabA, Mg, vmax, amax, g);
+  R Fv = wnum_F(c, w0, w1, L, s, rho, first, last, yg, stride, tabV, tabA, Mg, vmax, amax, wsc, g);
   R Sh[LBFGS_MAX_MEM], Yh[LBFGS_MAX_MEM], rh[LBFGS_MAX_MEM], al[LBFGS_MAX_MEM];  // [0] = newest pair
 #pragma unroll
   for (int q = 0; q < LBFGS_MAX_MEM; ++q) { Sh[q] = Yh[q] = rh[q] = al[q] = R(0); }
@@ -775,7 +806,7 @@ __device__ int numeric_step_warp(const R (&Grow)[NC], const R (&s)[NC], R w0, R 
     bool ok = false;
     for (int bt = 0; bt < 30; ++bt) {
       x = c + step * d;
-      Fn = wnum_F(x, w0, w1, L, s, rho, first, last, yg, stride, tabV, tabA, Mg, vmax, amax, gn);
+      Fn = wnum_F(x, w0, w1, L, s, rho, first, last, yg, stride, tabV, tabA, Mg, vmax, amax, wsc, gn);
       if (Fn <= Fv + R(1e-4) * step * gd) { ok = true; break; }
       step *= R(0.5);
     }

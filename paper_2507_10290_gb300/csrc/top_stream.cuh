@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(256) stream_numeric_warp(const StreamArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int Mg = p.M_gen;
   R *tabGV = (R *)smem, *tabGA = tabGV + 8 * Mg;
+  R *wsc = tabGA + 8 * Mg + (threadIdx.x >> 5) * 96;  // this warp's [3][32] gradient scratch
   fill_sample_table(tabGV, Mg, 1, threadIdx.x, blockDim.x);
   fill_accel_table(tabGA, Mg, threadIdx.x, blockDim.x);
   __syncthreads();
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(256) stream_numeric_warp(const StreamArgs A) {
     R c;
     const int its = numeric_step_warp<R>(Grow, s, w0, w1, rho, first, last, (R *)A.ygen + g, A.S, tabGV, tabGA,
                                          Mg, R(p.gen_vmax[b]), R(p.gen_amax[b]), p.lbfgs_mem, p.lbfgs_max_iters,
-                                         R(p.lbfgs_tol), c);
+                                         R(p.lbfgs_tol), wsc, c);
     // outputs: coefficients, end derivatives (rows of M(T) c, Sec. III-D.1)
     const int base = lane & ~7;
     R cax[NC];
@@ -536,7 +537,7 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
     const bool check = per || (k == K - 1);
     if (gen) cudaMemsetAsync(Ak.nwork, 0, sizeof(int), s);
     local<<<blocks, threads, tab_bytes, s>>>(Ak, first ? 0 : 1);
-    if (gen) stream_numeric_warp<R><<<wblocks, 256, sizeof(R) * 16 * (size_t)p.M_gen, s>>>(Ak);
+    if (gen) stream_numeric_warp<R><<<wblocks, 256, sizeof(R) * (16 * (size_t)p.M_gen + 8 * 96), s>>>(Ak);
     stream_junction<R><<<blocks, threads, 0, s>>>(Ak, check ? 1 : 0);
     if (check) {
       stream_dual<R><<<blocks, threads, 0, s>>>(Ak);

@@ -52,12 +52,13 @@ TOP_PIN, TOP_FREE = 0, 1
 TOP_CLOSED_FORM, TOP_NUMERIC = 0, 1
 TOP_MEM_DEVICE, TOP_MEM_HOST = 0, 1
 TOP_SCHED_AUTO, TOP_SCHED_RESIDENT, TOP_SCHED_STREAM = 0, 1, 2
+TOP_NUMERIC_AUTO, TOP_NUMERIC_WARP, TOP_NUMERIC_THREAD = 0, 1, 2
 
 
 class top_config(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_batch", C.c_int32), ("max_segments", C.c_int32),
                 ("max_samples", C.c_int32), ("schedule", C.c_int32), ("segs_per_cta", C.c_int32),
-                ("ckpt_interval", C.c_int32), ("reserved", C.c_int32 * 9)]
+                ("ckpt_interval", C.c_int32), ("numeric_form", C.c_int32), ("reserved", C.c_int32 * 8)]
 
 
 class top_problem(C.Structure):
@@ -218,7 +219,8 @@ class Solver:
     """
 
     def __init__(self, max_batch: int, max_segments: int, precision: str = "fp32", max_samples: int = 16,
-                 schedule: str = "auto", segs_per_cta: int = 0, ckpt_interval: int = 10):
+                 schedule: str = "auto", segs_per_cta: int = 0, ckpt_interval: int = 10,
+                 numeric_form: str = "auto"):
         import torch  # device memory and streams only
         self.torch = torch
         cfg = top_config()
@@ -229,6 +231,8 @@ class Solver:
         cfg.schedule = {"auto": TOP_SCHED_AUTO, "resident": TOP_SCHED_RESIDENT, "stream": TOP_SCHED_STREAM}[schedule]
         cfg.segs_per_cta = int(segs_per_cta)
         cfg.ckpt_interval = int(ckpt_interval)
+        cfg.numeric_form = {"auto": TOP_NUMERIC_AUTO, "warp": TOP_NUMERIC_WARP,
+                            "thread": TOP_NUMERIC_THREAD}[numeric_form]
         self.precision = precision
         rc, h = top_create(cfg)
         if rc != TOP_OK:

@@ -30,3 +30,22 @@ def test_each_path_against_the_oracle(T, precision, inner):
         assert (o["inner_iters"] > 0).sum() >= 3, "the bound must be active on several segments"
     g = to_np(solver(T, precision).solve(w))
     compare(g, o, w, TOL[precision])
+
+
+@pytest.mark.parametrize("precision,form", [("fp32", "warp"), ("fp64", "thread")])
+def test_numerical_step_in_the_other_form(T, precision, form):
+    """The warp-per-segment and thread-per-segment forms of the numerical
+    step (TOP_NUMERIC_WARP / TOP_NUMERIC_THREAD) in the precision whose default
+    is the other one, held to the oracle like the default forms."""
+    from test_parity_gpu import _solvers
+    key = ("numeric-form", precision, form)
+    if key not in _solvers:
+        _solvers[key] = T.Solver(64, 4096, precision=precision, max_samples=16, numeric_form=form)
+    g0 = W.speed_limit(seed=3, N=32, M=8)
+    chord = np.linalg.norm(np.diff(g0.waypoints, axis=0), axis=1) / g0.durations
+    w = W.speed_limit(seed=3, N=32, M=8, inner="numeric", max_iters=40, vmax=0.8 * float(np.median(chord)))
+    w = w.with_(lbfgs_tol=1e-12 if precision == "fp64" else 1e-6, lbfgs_max_iters=5000)
+    o = oracle.solve(w, state=True, lbfgs_tol=1e-12, lbfgs_max_iters=5000)
+    assert (o["inner_iters"] > 0).sum() >= 3
+    g = to_np(_solvers[key].solve(w))
+    compare(g, o, w, TOL[precision])
