@@ -28,6 +28,7 @@ struct Range {
 
 struct top_handle {
   top_config cfg{};
+  long long launches = 0;  // kernels launched by top_solve (top_launch_count)
   int device = 0;
   int sm_count = 0;
   int smem_optin = 0;
@@ -328,6 +329,8 @@ const char *top_strerror(int code) {
 
 int top_last_cuda_error(const top_handle *h) { return h ? h->last_cuda : 0; }
 
+int64_t top_launch_count(const top_handle *h) { return h ? (int64_t)h->launches : -1; }
+
 int top_set_profiling(top_handle *h, int enable) {
   if (!h) return TOP_E_INVAL;
   if (enable && !h->ev[0]) {
@@ -541,6 +544,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   TOP_CUDA(h, cudaMemsetAsync(dr.status, 0, sizeof(int32_t) * B, st));
   if (dr.rho) {
     int e = launch_fill(dr.rho, B, pb.rho, st);
+    h->launches += 1;
     if (e) return cuda_fail(h, (cudaError_t)e);
   }
   // ---- adaptive-rho data: grow-only workspace ----
@@ -579,12 +583,15 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
       unsigned char *pbase = (unsigned char *)h->P;
       pdata = PolyData{pbase, pbase + bG, pbase + bG + bU, pbase + bG + bU + bN};
       e = launch_kinv_poly(dp, pb.rho, fp64, pdata, h->d_err, st);
+      h->launches += S > 0 ? 1 : 0;
     } else {
       e = launch_kinv(dp, pb.rho, fp64 ? nullptr : h->G, fp64 ? h->G : nullptr, h->d_err, st, h->d_copy);
+      h->launches += S > 0 ? 3 : 0;  // mark, invert, copy
     }
     if (e) return cuda_fail(h, (cudaError_t)e);
     if (adapt) {
       e = launch_keig(dp, fp64 ? nullptr : h->E, fp64 ? h->E : nullptr, h->d_err, st);
+      h->launches += S > 0 ? 1 : 0;
       if (e) return cuda_fail(h, (cudaError_t)e);
     }
     if (h->profiling) { cudaEventRecord(h->ev[1], st); h->ran[0] = true; }
@@ -639,6 +646,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     if (h->profiling) cudaEventRecord(h->ev[2], st);
     int e = fp64 ? launch_resident_f64(ra, npack, C, L.total, fam, st)
                  : launch_resident_f32(ra, npack, C, L.total, fam, st);
+    h->launches += 1;
     if (e) return cuda_fail(h, (cudaError_t)e);
     if (h->profiling) { cudaEventRecord(h->ev[3], st); h->ran[1] = true; }
   }
@@ -712,6 +720,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
         ca.traj = h->d_ctraj + at;
         int e = fp64 ? launch_cluster_f64(ca, n, c, ccap, csmem, fam, cs)
                      : launch_cluster_f32(ca, n, c, ccap, csmem, fam, cs);
+        h->launches += 1;
         if (e) return cuda_fail(h, (cudaError_t)e);
         at += n;
       }
@@ -799,6 +808,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     sa.nwork = warp_num ? (int *)(base + o_nw) : nullptr;
     sa.work = warp_num ? (int *)(base + o_nw) + 1 : nullptr;
     sa.E = adapt ? h->E : nullptr;
+    sa.launches = &h->launches;
     Range r2("streaming trajectories");
     if (h->profiling) cudaEventRecord(h->ev[4], st);
     int e = fp64 ? launch_stream_f64(sa, fam, st) : launch_stream_f32(sa, fam, st);

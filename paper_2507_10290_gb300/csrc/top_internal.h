@@ -162,6 +162,7 @@ struct StreamArgs {
   int *kcount;             // [nl] periodic residual evaluations so far (or null)
   int cev;                 // iterations between periodic evaluations
   int *nwork, *work;       // numerical step: count and compact indices of segments with a violated bound
+  long long *launches;     // host counter of kernel launches (or null); never read on the device
 };
 
 // A kernel attribute set once per (device, kernel, value): cudaFuncSetAttribute

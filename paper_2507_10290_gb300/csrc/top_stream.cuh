@@ -521,6 +521,7 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
     default: return (int)cudaErrorInvalidValue;
   }
   init<<<blocks, threads, 0, st>>>(A);
+  long long nl = 1;  // kernel launches, for the handle's count
   const int K = p.max_iters;
   const bool adapt = p.adaptive && A.E;
   const int cev = adapt ? 1 : (p.check_every > 0 ? p.check_every : 1);
@@ -539,11 +540,16 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
     local<<<blocks, threads, tab_bytes, s>>>(Ak, first ? 0 : 1);
     if (gen) stream_numeric_warp<R><<<wblocks, 256, sizeof(R) * (16 * (size_t)p.M_gen + 8 * 96), s>>>(Ak);
     stream_junction<R><<<blocks, threads, 0, s>>>(Ak, check ? 1 : 0);
+    nl += gen ? 3 : 2;
     if (check) {
       stream_dual<R><<<blocks, threads, 0, s>>>(Ak);
       stream_reduce<R><<<Ak.nl, 256, 0, s>>>(Ak, per ? -1 : k);
+      nl += 2;
     }
-    if (adapt && k + 1 < K) rescale<<<blocks, threads, 0, s>>>(Ak);
+    if (adapt && k + 1 < K) {
+      rescale<<<blocks, threads, 0, s>>>(Ak);
+      nl += 1;
+    }
   };
   int k = 0;
   if (K > 0) iteration(st, k++, true);
@@ -560,14 +566,20 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
     cudaGraphExec_t exec = nullptr;
     bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    const long long before = nl;
     if (ok) {
       for (int j = 0; j < G; ++j) iteration(cs, 1 + j, false);
       ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && graph != nullptr;
     }
+    const long long per_replay = nl - before;  // recorded, not launched
+    nl = before;
     if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
     bool launched = true;
     if (ok) {
-      for (int q = 0; launched && q < nblk; ++q) launched = cudaGraphLaunch(exec, st) == cudaSuccess;
+      for (int q = 0; launched && q < nblk; ++q) {
+        launched = cudaGraphLaunch(exec, st) == cudaSuccess;
+        if (launched) nl += per_replay;
+      }
       k = 1 + nblk * G;
     }
     if (exec) cudaGraphExecDestroy(exec);
@@ -579,6 +591,7 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
   for (; k < K; ++k) iteration(st, k, false);
   stream_output<R><<<blocks, threads, 0, st>>>(A);
   stream_finish<R><<<A.nl, 256, 0, st>>>(A, K);
+  if (A.launches) *A.launches += nl + 2;
   return (int)cudaGetLastError();
 }
 

@@ -90,6 +90,8 @@ _lib.top_solve.restype = C.c_int
 _lib.top_grad.argtypes = [C.c_void_p, C.POINTER(top_problem), C.c_void_p, C.c_void_p, C.c_void_p,
                           C.c_void_p]
 _lib.top_grad.restype = C.c_int
+_lib.top_launch_count.argtypes = [C.c_void_p]
+_lib.top_launch_count.restype = C.c_int64
 _lib.top_destroy.argtypes = [C.c_void_p]
 _lib.top_destroy.restype = None
 _lib.top_strerror.argtypes = [C.c_int]
@@ -186,6 +188,11 @@ def top_set_layout(handle, B: int, host_seg_offset) -> int:
 def top_sync(handle, stream: int = 0) -> int:
     """int top_sync(top_handle*, void* stream): error flag of the last capture-safe top_solve."""
     return _lib.top_sync(handle, C.c_void_p(stream))
+
+
+def top_launch_count(handle) -> int:
+    """int64_t top_launch_count(const top_handle*): kernels launched by top_solve so far."""
+    return int(_lib.top_launch_count(handle))
 
 
 def top_set_profiling(handle, enable: bool) -> int:
