@@ -450,10 +450,31 @@ def run_suite(args):
         dt = time.perf_counter() - t0
         return r, dt
 
+    def rel_max(a, b):
+        return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+    def pin_spline_coeffs(w):
+        """The converged PIN fixed point (the centralized C^6 spline through the
+        waypoints) of every trajectory, or None where the problem has other rows."""
+        from oracle import centralized as C
+        if w.mode != "pin" or any(getattr(w, f, 0) for f in ("M_box", "M_ball", "M_vn", "M_gen", "M_poly")):
+            return None
+        off = np.asarray(w.seg_offset)
+        out = np.zeros((w.S, 3, 8))
+        for b in range(w.B):
+            g0, g1 = int(off[b]), int(off[b + 1])
+            if g1 > g0:
+                out[g0:g1] = C.pin_spline(w.waypoints[g0 + b:g1 + b + 1], w.durations[g0:g1],
+                                          w.start_state[b], w.end_state[b])
+        return out
+
     def gpu_case(name, w, precs=("fp32", "fp64"), extra=None, tol_eps=None, tol_cap=20000):
         line = {"suite": name, "workload": w.name, "segments": int(w.S), "trajectories": int(w.B),
                 "iterations": int(w.max_iters)}
         o, odt = oracle_rate(w)
+        spline = pin_spline_coeffs(w)
+        if spline is not None:
+            line["oracle_distance_to_converged_pin_spline"] = scaled_err(o["coeffs"], spline, w.durations)
         line["oracle"] = {"seconds": odt, "cores": 1, "segment_iterations_per_s": w.S * w.max_iters / odt}
         for prec in precs:
             s = top.Solver(max_batch=w.B, max_segments=w.S, precision=prec, max_samples=16)
@@ -469,7 +490,11 @@ def run_suite(args):
                      "kernel_ms": {"precompute": kt[0], "resident": kt[1], "streaming": kt[2], "cluster": kt[3]},
                      "segment_iterations_per_s": w.S * w.max_iters / (float(np.median(ms)) / 1000),
                      "coeff_rel_err_vs_oracle": scaled_err(g["coeffs"], o["coeffs"], w.durations),
-                     "cost_rel_err_vs_oracle": float(np.max(np.abs(g["cost"] - o["cost"]) / np.abs(o["cost"])))}
+                     "cost_rel_err_vs_oracle": float(np.max(np.abs(g["cost"] - o["cost"]) / np.abs(o["cost"]))),
+                     "r_primal_rel_err_vs_oracle": rel_max(g["r_primal"], o["r_primal"]),
+                     "r_dual_rel_err_vs_oracle": rel_max(g["r_dual"], o["r_dual"])}
+            if spline is not None:
+                entry["distance_to_converged_pin_spline"] = scaled_err(g["coeffs"], spline, w.durations)
             if getattr(w, "adaptive_rho", False):
                 entry["final_rho_equal_to_oracle"] = float(np.mean(g["rho"] == o["rho_final"]))
             if tol_eps:
