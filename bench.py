@@ -39,7 +39,9 @@ from paper_2507_10290_gb300 import workloads as W  # noqa: E402
 
 METRIC = "CADMM segment-iterations/s (4096-trajectory batch, 300 iterations, to fixed iteration count)"
 UNIT = "segment-iterations/s"
-FLOP_PER_SEG_IT = 1190        # algorithmic FP32 FLOPs of one segment-iteration
+# algorithmic FP32 FLOPs of one segment-iteration without inequality rows (multiply-add = 2):
+# targets 3x28, consensus right-hand side 3x93, G rhs 3x128, end derivatives 3x91, junction 21x8
+FLOP_PER_SEG_IT = 1190
 L2_BYTES = 129 * 1024 * 1024
 
 

@@ -16,7 +16,7 @@
 // The CTA barriers of the resident kernel become cluster barriers.  On check
 // iterations every CTA reduces its share of ||r_p||^2, ||r_d||^2 in a fixed
 // order, rank 0 adds the shares in rank order, applies the stopping test
-// (Eq. 21) and publishes the verdict, which every CTA reads back.  All CTAs of
+// (Eq. 21) and publishes the stop decision, which every CTA reads back.  All CTAs of
 // a cluster run the same number of cluster barriers (no early exit), and the
 // kernel ends with one, so no CTA leaves while another may still read its
 // shared memory.  Polytope rows (fixed rho) use the rotated per-axis inverses
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
   R *sh_rd = (R *)(smem + L.red_rd);
   double *part = (double *)(smem + L.tr_rp);   // [8]: shares ||r_p||^2, ||r_d||^2, rank 0's norms, cost share,
                                                //      rank 0's rho and rho_old / rho_new (Eq. 22)
-  int *sdone = (int *)(smem + L.done);         // rank 0: the verdict
+  int *sdone = (int *)(smem + L.done);         // rank 0: the stop decision
   R *sp = (R *)(smem + L.p);
   R *sm = (R *)(smem + L.m);
   R *szP = (R *)(smem + L.zP);
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
 
   const int cev = p.check_every > 0 ? p.check_every : 1;
   const bool periodic = p.eps > 0.0 || res.history != nullptr;
-  int done = 0;     // the verdict, identical in every CTA of the cluster
+  int done = 0;     // the stop decision, identical in every CTA of the cluster
   double rp_last = 0.0, rd_last = 0.0;
   const int warp = l >> 5, lane = l & 31;
   for (int k = 0; k < K; ++k) {
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
         if (lane == 0) { part[0] = double(a1); part[1] = double(a2); }
       }
       cl.sync();
-      if (rank == 0 && l == 0 && !done) {  // shares in rank order, the verdict
+      if (rank == 0 && l == 0 && !done) {  // shares in rank order, the stop decision
         double s1 = 0.0, s2 = 0.0;
         for (int q = 0; q < csz; ++q) {
           const double *pq = cl.map_shared_rank(part, q);
@@ -336,8 +336,8 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
         rho_new = p0[5];
       }
       if (rank == 0) { rp_last = part[2]; rd_last = part[3]; }
-      cl.sync();  // the verdict is read everywhere before rank 0 may write the next shares
-      if (done) break;  // the same verdict in every CTA: a uniform exit from the loop
+      cl.sync();  // the decision is read everywhere before rank 0 may write the next shares
+      if (done) break;  // the same decision in every CTA: a uniform exit from the loop
       // ---- 5. after a change of rho (adaptive rho): keep the unscaled duals, new local inverse ----
       if (ADAPT && fac != 1.0 && k + 1 < K) {  // the same fac in every CTA
         if (valid) {
