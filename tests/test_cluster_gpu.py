@@ -148,3 +148,25 @@ def test_graph_capture_replays_top_solve(T):
     compare(to_np(out), o, w, TOL["fp32"])
     assert T.top_set_layout(s.handle, 0, None) == T.TOP_OK
     s.close()
+
+
+def test_launch_count(T):
+    """top_launch_count: a fixed-rho solve whose trajectories all fit one CTA
+    launches fill (the final rho), mark, invert, copy and resident; a long one
+    adds one cluster launch; the streaming form launches at least its two
+    kernels (local step, junction) per iteration plus set-up and output."""
+    s = small_cta_solver(T, "fp32")
+    w = W.tiny(seed=2, N=[5, 9, 40], mode="pin").with_(max_iters=30)
+    c0 = T.top_launch_count(s.handle)
+    s.solve(w)
+    assert T.top_launch_count(s.handle) - c0 == 5
+    w2 = W.tiny(seed=2, N=[5, 200], mode="pin").with_(max_iters=30)  # 200 > 64 per CTA: a cluster
+    c0 = T.top_launch_count(s.handle)
+    g, ms = solve_profiled(T, s, w2)
+    assert ms[3] > 0.0
+    assert T.top_launch_count(s.handle) - c0 == 6
+    st = small_cta_solver(T, "fp32", schedule="stream")
+    c0 = T.top_launch_count(st.handle)
+    st.solve(w.with_(max_iters=100))
+    assert T.top_launch_count(st.handle) - c0 >= 2 * 100 + 3
+    assert T.top_launch_count(None) == -1
