@@ -343,9 +343,14 @@ def run_ours(args):
     clocks = clk.summary()
     sm_max = peaks.get("sm_max_mhz") or 2070.0
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FFMA pipe at the maximum SM clock
+    if args.precision == "fp64":  # 2 DFMA per clock per SM (1/64 of the FP32 lanes)
+        fp32_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12
+    rt = "float" if args.precision == "fp32" else "double"
     # the iteration kernels: resident packs, plus clusters for trajectories longer
-    # than the chosen capacity (same work per segment-iteration, run one after the other)
-    res_ms = kern["resident_ms"] + kern["cluster_ms"]
+    # than the chosen capacity (same work per segment-iteration)
+    res_ms = kern["resident_ms"]
+    if kern["cluster_ms"] > 0:  # clusters run beside the resident packs: the iteration phase's wall time
+        res_ms = max(kern["resident_ms"], kern["cluster_ms"], ms_step - kern["kinv_ms"])
     achieved = FLOP_PER_SEG_IT * S * iters / (res_ms / 1000.0) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -358,10 +363,13 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "trajectories_per_s": world * B / (ms_step / 1000.0),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": resident_traffic(S),
-                     "kernel": "resident_kernel<float,0>" + (" + cluster_kernel<float,0>" if kern["cluster_ms"] > 0 else ""),
+                     "frac": achieved / fp32_peak,
+                     "traffic": resident_traffic(S) if args.precision == "fp32" else None,
+                     "kernel": f"resident_kernel<{rt},0>" + (f" + cluster_kernel<{rt},0>" if kern["cluster_ms"] > 0 else ""),
                      "kernel_ms": res_ms,
-                     "peak_source": f"FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x {sm_max:.0f} MHz (max SM clock)",
+                     "peak_source": (f"FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x {sm_max:.0f} MHz (max SM clock)"
+                                     if args.precision == "fp32" else
+                                     f"FP64 pipe: 152 SMs x 2 DFMA x 2 FLOP x {sm_max:.0f} MHz (max SM clock)"),
                      "flop_per_segment_iteration": FLOP_PER_SEG_IT},
         "kinv_ms": kern["kinv_ms"],
         "cuda_graph_ms_per_step": graph_ms,
