@@ -54,7 +54,9 @@ extern "C" {
 #define TOP_E_NOTSUP   -5  /* a valid but unsupported combination (e.g. numeric step with box rows) */
 #define TOP_E_STATE    -6  /* call out of order (e.g. top_grad without a matching top_solve) */
 #define TOP_E_NUMERIC  -7  /* a local KKT matrix was not positive definite in FP64 */
-#define TOP_E_LIMIT    -8  /* the problem exceeds the fixed scratch of top_solve_noalloc */
+#define TOP_E_LIMIT    -8  /* the problem exceeds the fixed scratch of top_solve_noalloc, or 32-bit
+                               indexing of per-segment state (S x rows per segment >= 2^31, rows =
+                               max(108, 6 M_box, 3 M_ball, 3 M_vn, 2 M_gen, F_poly M_poly)) */
 
 /* fixed limits of top_solve_noalloc */
 #define TOP_NOALLOC_MAX_SEGMENTS 16384

@@ -438,6 +438,19 @@ int top_create(const top_config *cfg, top_handle **out) {
   return TOP_OK;
 }
 
+// The streaming form indexes its per-segment state as row * S + g in 32-bit
+// integers (row < 6 M_box, 3 M_ball, 3 M_vn, 2 M_gen, F M_poly, or the 108
+// values of the polytope inverses): such products must stay below 2^31.
+static bool index_fits(const top_problem *pb, int S) {
+  long long rows = 108;
+  rows = std::max(rows, 6LL * pb->M_box);
+  rows = std::max(rows, 3LL * pb->M_ball);
+  rows = std::max(rows, 3LL * pb->M_vn);
+  rows = std::max(rows, 2LL * pb->M_gen);
+  rows = std::max(rows, (long long)pb->F_poly * pb->M_poly);
+  return rows * (long long)S < (1LL << 31);
+}
+
 int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void *stream) {
   Range range("top_solve");
   int rc = validate(h, pb_in, res_in);
@@ -464,6 +477,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   const int S = off[B];
   if (S > h->cfg.max_segments) return TOP_E_NOMEM;
   if (S > 0 && (!pb_in->durations || !res_in->coeffs)) return TOP_E_INVAL;
+  if (!index_fits(pb_in, S)) return TOP_E_LIMIT;
   // ---- device views of inputs and outputs ----
   top_problem pb = *pb_in;
   top_result res = *res_in;
