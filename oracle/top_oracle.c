@@ -53,6 +53,12 @@
  *       scaled dual is multiplied by rho_old / rho_new) and each segment's
  *       local matrix is assembled and factorised again for the new rho.
  *
+ * Parity unpinned: the iterate path of the L-BFGS numerical step.  Only its
+ * result is pinned (stationarity of an independently coded objective, and
+ * equality with the closed form where no bound is active), so GPU/oracle
+ * parity of that step holds where every local solve reaches its tolerance
+ * before its iteration cap.
+ *
  * Compile-time type: OR_REAL (default double; the oracle's own rounding is
  * bounded by re-running it with OR_REAL = long double).
  */
