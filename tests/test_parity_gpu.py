@@ -256,3 +256,15 @@ def test_general_bounds_long_trajectory(T, precision):
     o = oracle.solve(w)
     g = to_np(solver(T, precision).solve(w))
     compare(g, o, w, TOL[precision])
+
+
+def test_large_host_memory_results_equal_device_results(T):
+    """138,519 segments (26.6 MB of coefficients staged back to the host): the
+    host-buffer call returns exactly what the device-buffer call does."""
+    w = W.batch(B=512).with_(max_iters=10)
+    s = solver(T, "fp32")
+    gd = to_np(s.solve(w))
+    gh = s.solve_host(w)
+    assert gd["coeffs"].nbytes > (16 << 20)
+    for k in ("coeffs", "cost", "r_primal", "r_dual", "iters", "status"):
+        assert np.array_equal(gd[k], gh[k]), k
