@@ -255,7 +255,8 @@ int top_autotune(top_handle *h, const top_problem *pb, int32_t iters, int32_t *o
 int top_set_profiling(top_handle *h, int enable);
 int top_kernel_times(const top_handle *h, float *ms, int n);
 
-/* Kernels this handle's top_solve calls have launched so far (a host-side
+/* Kernels this handle's top_solve calls have launched so far (instrumentation
+ * with no counterpart in the paper; a host-side
  * count: each launch the library issues, and each kernel node of a CUDA graph
  * it replays, counts once; library copies and memsets do not count).  The
  * difference across a region is the number of the library's kernels that ran
