@@ -268,3 +268,19 @@ def test_large_host_memory_results_equal_device_results(T):
     assert gd["coeffs"].nbytes > (16 << 20)
     for k in ("coeffs", "cost", "r_primal", "r_dual", "iters", "status"):
         assert np.array_equal(gd[k], gh[k]), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_pin_with_box_rows_does_not_converge(T, precision):
+    """The single-box workload with PIN waypoints: pinned positions plus the
+    velocity box leave (almost) no feasible trajectory, and the iteration does
+    not reach eps = 1e-4 in 3000 iterations, on the oracle as on the GPU.  The
+    status says so (TOP_NOT_CONVERGED), the results of the last iteration are
+    written and finite, and they match the oracle's after the same iterations."""
+    w = W.single_box().with_(mode="pin", eps=1e-4, max_iters=3000)
+    o = oracle.solve(w)
+    assert o["status"][0] == T.TOP_NOT_CONVERGED
+    g = to_np(solver(T, precision).solve(w))
+    assert g["status"][0] == T.TOP_NOT_CONVERGED and g["iters"][0] == 3000
+    assert np.all(np.isfinite(g["coeffs"])) and g["r_primal"][0] > 1.0
+    compare(g, o, w, TOL[precision])
