@@ -15,6 +15,12 @@ of the oracle can be checked against them:
                   KKT system of the whole QP (numpy.linalg.solve).
   active_set_qp   brute force over the active sets of a tiny box-constrained
                   problem: the exact constrained optimum.
+  norm_ball_qp    a tiny problem with sampled norm bounds ||sigma^(r)(t_ij) - o_i||
+                  <= rad_i (ball corridor: r = 0; velocity norm: r = 1, o = 0),
+                  solved through its Lagrange dual (maximised over the
+                  multipliers mu >= 0, each dual evaluation one equality-
+                  constrained linear KKT solve), then polished by Newton's
+                  method on the multipliers of the binding samples.
 
 Coefficients are returned in the raw monomial basis of each segment,
 shape [N, 3, 8]:  sigma_i(t) = sum_k c[i, a, k] (t - t_{i-1})^k.
@@ -259,3 +265,83 @@ def active_set_qp(P, T, start, end, mode, M, vmax, tol=1e-9):
         c_all[cols] = found[0]
         act_all += found[1]
     return c_all.reshape(N, 3, NC), sorted(act_all)
+
+
+def norm_ball_qp(P, T, start, end, mode, M, order, centres, radii):
+    """Exact optimum of min sum c^T Qt c under the equalities of Eq. 2 and the
+    sampled norm bounds ||sigma_i^{(order)}(t_ij) - centres[i]|| <= radii[i],
+    t_ij = j T_i / M, j = 1..M.
+
+    The problem is a convex QCQP with a strictly feasible point, so strong
+    duality holds: for multipliers mu >= 0 the Lagrangian is a quadratic in c
+    whose equality-constrained minimiser c(mu) is one linear KKT solve, and
+    the dual function d(mu) = L(c(mu), mu) is concave with gradient
+    ||G_j c(mu) - o_j||^2 - rad_j^2.  d is maximised by L-BFGS-B over mu >= 0;
+    the multipliers of the binding samples are then refined by Newton's
+    method on ||G_j c(mu) - o_j||^2 = rad_j^2.  Returns (c [N,3,8], mu [N*M],
+    g [N*M] = ||G_j c - o_j|| - rad_j).
+    """
+    import scipy.optimize as so
+
+    A, b = _equalities(P, T, start, end, mode)
+    H = _hessian(T)
+    N = len(T)
+    n = N * 3 * NC
+    # time-normalised unknowns and unit-norm equality rows (conditioning only)
+    D = np.concatenate([[T[i] ** -k for a in range(3) for k in range(NC)] for i in range(N)])
+    Hs = D[:, None] * H * D[None, :]
+    As = A * D[None, :]
+    rs = 1.0 / np.linalg.norm(As, axis=1)
+    As = As * rs[:, None]
+    bs = b * rs
+    m = As.shape[0]
+    Gs, os_, rad = [], [], []
+    for i in range(N):
+        for j in range(1, M + 1):
+            row = deriv_row(order, j * T[i] / M)
+            G = np.zeros((3, n))
+            for a in range(3):
+                o = i * 3 * NC + a * NC
+                G[a, o:o + NC] = row
+            Gs.append(G * D[None, :])
+            os_.append(np.asarray(centres[i], dtype=float))
+            rad.append(float(radii[i]))
+    J = len(Gs)
+
+    def c_of(mu):
+        K = Hs.copy()
+        rhs = np.zeros(n)
+        for G, o, mj in zip(Gs, os_, mu):
+            K += 2.0 * mj * G.T @ G
+            rhs += 2.0 * mj * G.T @ o
+        KKT = np.zeros((n + m, n + m))
+        KKT[:n, :n] = K
+        KKT[:n, n:] = As.T
+        KKT[n:, :n] = As
+        return np.linalg.solve(KKT, np.concatenate([rhs, bs]))[:n]
+
+    def gaps(x):
+        return np.array([np.sum((G @ x - o) ** 2) - r * r for G, o, r in zip(Gs, os_, rad)])
+
+    def neg_dual(mu):
+        x = c_of(mu)
+        g = gaps(x)
+        return -(0.5 * x @ Hs @ x + mu @ g), -g
+
+    res = so.minimize(neg_dual, np.zeros(J), jac=True, method="L-BFGS-B", bounds=[(0.0, None)] * J,
+                      options=dict(ftol=0.0, gtol=1e-14, maxiter=20000))
+    mu = np.array(res.x)
+    act = np.where(mu > 1e-9 * max(1.0, mu.max()))[0]
+    if len(act):
+        def f(ma):
+            full = np.zeros(J)
+            full[act] = ma
+            return gaps(c_of(full))[act]
+        sol = so.root(f, mu[act], method="hybr", options=dict(xtol=1e-15))
+        # hybr may report "no further improvement" at full precision: judge by the residual
+        if np.all(sol.x >= 0) and np.abs(f(sol.x)).max() <= np.abs(f(mu[act])).max():
+            mu = np.zeros(J)
+            mu[act] = sol.x
+    x = c_of(mu)
+    g = np.array([np.linalg.norm(G @ x - o) - r for G, o, r in zip(Gs, os_, rad)])
+    return (D * x).reshape(N, 3, NC), mu, g

@@ -600,3 +600,185 @@ def test_inactive_polytopes_keep_the_free_fixed_point():
     r = oracle.solve(w)
     ref = CZ.free_polynomial(w.durations, w.start_state[0], w.end_state[0])
     assert scaled_relerr(r["coeffs"], ref, w.durations) < 1e-9
+
+
+# ------------------------------- quadratic rows inside the iteration (Eq. 18f-g) --
+
+def _ball_instance():
+    """Tiny FREE instance with a ball corridor per segment (Sec. III-C.2 with the
+    centre shift of reading R8): centre at the chord midpoint of the unconstrained
+    optimum, radius 85 % of its farthest sample (the trajectory's fixed end stays
+    strictly inside), so that some samples bind; rho = 10 converges to ~1e-8."""
+    w = W.tiny(seed=5, N=3, mode="free", T_range=(0.9, 1.3), step=2.0)
+    free = CZ.free_polynomial(w.durations, w.start_state[0], w.end_state[0])
+    N, M = len(w.durations), 2
+    cen, rad = np.zeros((N, 3)), np.zeros(N)
+    for i in range(N):
+        T = w.durations[i]
+        pts = np.array([[free[i, a] @ CZ.deriv_row(0, (j + 1) * T / M) for a in range(3)] for j in range(M)])
+        start = np.array([free[i, a] @ CZ.deriv_row(0, 0.0) for a in range(3)])
+        cen[i] = 0.5 * (start + pts[-1])
+        rad[i] = 0.85 * np.linalg.norm(pts - cen[i], axis=1).max()
+    rad[-1] = max(rad[-1], 1.05 * np.linalg.norm(w.waypoints[-1] - cen[-1]))
+    return w.with_(M_ball=M, ball_c=cen, ball_r=rad, rho=10.0, max_iters=200000)
+
+
+def _vn_instance():
+    """Tiny FREE instance whose speed bound ||v(t_ij)|| <= v_max (projection
+    family, Eq. 18f-g with the centre at 0) is 85 % of the unconstrained peak
+    sampled speed; rho = 10 converges to ~1e-9."""
+    w = W.tiny(seed=5, N=3, mode="free", T_range=(0.9, 1.3), step=2.0)
+    free = CZ.free_polynomial(w.durations, w.start_state[0], w.end_state[0])
+    N, M = len(w.durations), 3
+    peak = max(np.linalg.norm([free[i, a] @ CZ.deriv_row(1, (j + 1) * w.durations[i] / M) for a in range(3)])
+               for i in range(N) for j in range(M))
+    return w.with_(M_vn=M, vnorm=np.array([0.85 * peak]), rho=10.0, max_iters=100000)
+
+
+def quadratic_row_errors(kind, lib=None):
+    """The converged oracle on a ball-corridor ("ball") or velocity-norm ("vn")
+    instance against (i) the exact optimum of the same QCQP from its Lagrange
+    dual (`centralized.norm_ball_qp`, nothing shared with the oracle), and
+    (ii) the KKT certificate of Eq. 18 at the fixed point, every matrix rebuilt
+    here from the basis:
+      stationarity  2 Qt c + rho Mt^T (E u) + rho sum_j A_j^T w_j = 0
+                    (A_j = I_3 (x) beta^{(r)}(t_j)^T, r = 0 ball, 1 velocity;
+                    nu_j = rho w_j is the multiplier of sample j),
+      nu_j along the outward normal at phi_j: w_j = lam_j (phi_j - o), lam_j >= 0,
+      complementarity: lam_j > 0 only where ||phi_j - o|| = rad,
+      the split holds: A_j c = phi_j, and A_j c is feasible.
+    Returns (relative distance to the QCQP optimum, worst certificate violations,
+    number of binding samples)."""
+    w = _ball_instance() if kind == "ball" else _vn_instance()
+    r = oracle.solve(w, state=True, **({} if lib is None else {"real": lib}))
+    T, rho = w.durations, w.rho
+    N = len(T)
+    if kind == "ball":
+        M, order, cen, rad = w.M_ball, 0, w.ball_c, w.ball_r
+        phi, wd = r["phi_b"], r["w_b"]
+    else:
+        M, order, cen, rad = w.M_vn, 1, np.zeros((N, 3)), np.full(N, float(w.vnorm[0]))
+        phi, wd = r["phi_v"], r["w_v"]
+    c_ref, mu, g = CZ.norm_ball_qp(w.waypoints, T, w.start_state[0], w.end_state[0], "free", M, order, cen, rad)
+    dist = scaled_relerr(r["coeffs"], c_ref, T)
+    worst = {"stat": 0.0, "normal": 0.0, "compl": 0.0, "split": 0.0, "feas": 0.0}
+    binding = 0
+    for i in range(N):
+        Mt, E = _consensus_rows(T[i], i == 0, i == N - 1)
+        Qt = np.zeros((24, 24))
+        for a in range(3):
+            Qt[a * 8:(a + 1) * 8, a * 8:(a + 1) * 8] = CZ.snap_gram(T[i])
+        ci = r["coeffs"][i].reshape(24)
+        scale = np.abs(2 * Qt @ ci).max()
+        stat = 2 * Qt @ ci + rho * Mt.T @ (E * r["u"][i])
+        for j in range(M):
+            A = np.kron(np.eye(3), CZ.deriv_row(order, (j + 1) * T[i] / M)[None, :])
+            stat += rho * A.T @ wd[i, j]
+            d = phi[i, j] - cen[i]
+            nw = np.linalg.norm(wd[i, j])
+            worst["split"] = max(worst["split"], np.abs(A @ ci - phi[i, j]).max() / max(1.0, np.abs(phi[i, j]).max()))
+            worst["feas"] = max(worst["feas"], np.linalg.norm(A @ ci - cen[i]) - rad[i])
+            if nw > 1e-8 * max(1.0, np.abs(wd).max()):
+                binding += 1
+                cosang = float(wd[i, j] @ d) / (nw * np.linalg.norm(d))
+                worst["normal"] = max(worst["normal"], 1.0 - cosang)
+                worst["compl"] = max(worst["compl"], abs(np.linalg.norm(d) - rad[i]) / rad[i])
+        worst["stat"] = max(worst["stat"], np.abs(stat).max() / scale)
+    return dist, worst, binding, r
+
+
+def _quadratic_rows_ok(kind, lib=None):
+    dist, worst, binding, r = quadratic_row_errors(kind, lib)
+    return (binding >= 1 and dist < 1e-6 and worst["stat"] < 1e-6 and worst["normal"] < 1e-9
+            and worst["compl"] < 1e-7 and worst["split"] < 1e-7 and worst["feas"] < 1e-7)
+
+
+@pytest.mark.parametrize("kind", ["ball", "vn"])
+def test_quadratic_rows_reach_the_qcqp_optimum_with_a_kkt_certificate(kind):
+    dist, worst, binding, r = quadratic_row_errors(kind)
+    assert binding >= 1, "the instance must have binding samples"
+    assert dist < 1e-6, dist
+    assert worst["stat"] < 1e-6 and worst["normal"] < 1e-9 and worst["compl"] < 1e-7, worst
+    assert worst["split"] < 1e-7 and worst["feas"] < 1e-7, worst
+
+
+# ------------------------------------------- residual values (Eq. 19-20) --
+
+def residual_errors(lib=None, K=23):
+    """||r_p|| and ||r_d|| reported after iteration K+1 (and in the history),
+    recomputed here from the returned coefficients and junction states with
+    matrices built from the basis:
+      r_p^2 = sum over interior junctions, axes and orders 0..6 of
+              (sigma_j^{(r)}(T_j) - sigma_{j+1}^{(r)}(0))^2            (Eq. 19)
+      r_d^2 = sum_i || rho Mt_i^T E_i (zt_i^{K+1} - zt_i^K) ||^2          (Eq. 20, R10)
+    on a batch of one PIN and one FREE trajectory with rho != 1 and box rows.
+    Returns the largest relative error."""
+    kw = {} if lib is None else {"real": lib}
+    w = W.tiny(seed=12, N=[4, 6], mode="pin", T_range=(0.6, 1.4)).with_(rho=3.7)
+    w = w.with_(M_box=3, vbox=np.array([2.0, 2.0]))
+    worst = 0.0
+    for mode in ("pin", "free"):
+        wm = w.with_(mode=mode)
+        a = oracle.solve(wm.with_(max_iters=K), state=True, **kw)
+        b = oracle.solve(wm.with_(max_iters=K + 1), state=True, history=True, **kw)
+        off = wm.seg_offset
+        for t in range(wm.B):
+            s0, s1 = int(off[t]), int(off[t + 1])
+            N = s1 - s0
+            T = wm.durations[s0:s1]
+            c = b["coeffs"][s0:s1]
+            rp2 = 0.0
+            for j in range(1, N):
+                for ax in range(3):
+                    for rr in range(7):
+                        gap = c[j - 1, ax] @ CZ.deriv_row(rr, T[j - 1]) - c[j, ax] @ CZ.deriv_row(rr, 0.0)
+                        rp2 += gap * gap
+            rd2 = 0.0
+            za, zb = a["z"][s0 + t:s1 + t + 1], b["z"][s0 + t:s1 + t + 1]
+            for i in range(N):
+                Mt, E = _consensus_rows(T[i], i == 0, i == N - 1)
+                dz = np.concatenate([np.concatenate([zb[i + side, ax] - za[i + side, ax] for side in (0, 1)])
+                                     for ax in range(3)])
+                v = wm.rho * Mt.T @ (E * dz)
+                rd2 += v @ v
+            for got, ref in ((b["r_primal"][t], np.sqrt(rp2)), (b["r_dual"][t], np.sqrt(rd2)),
+                             (b["history"][K, t, 0], np.sqrt(rp2)), (b["history"][K, t, 1], np.sqrt(rd2))):
+                worst = max(worst, abs(got - ref) / max(ref, 1e-300))
+            if rd2 == 0.0 or rp2 == 0.0:
+                worst = np.inf  # the instance must exercise both residuals
+    return worst
+
+
+def test_residuals_equal_their_definition():
+    assert residual_errors() < 1e-10
+
+
+# ------------------------------------------- numerical-step dual (Eq. 17) --
+
+def numeric_dual_error(lib=None, K=20):
+    """y^{K+1} - y^K = rho g(c^{K+1}) per sample and bound (Eq. 17 with the dual
+    update of Eq. 7c, reading R9), g = max(0, ||sigma^{(r)}(t_j)||^2 - g_max^2)^2,
+    recomputed here from the returned coefficients; rho = 1e4, so that a
+    missing factor rho is visible.  Returns the largest relative error."""
+    kw = {} if lib is None else {"real": lib}
+    w = W.tiny(seed=9, N=4, mode="pin", step=4.0, T_range=(0.8, 1.0)).with_(
+        inner="numeric", M_gen=4, gen_vmax=np.array([4.0]), gen_amax=np.array([8.0]), rho=1e4)
+    a = oracle.solve(w.with_(max_iters=K), state=True, **kw)
+    b = oracle.solve(w.with_(max_iters=K + 1), state=True, **kw)
+    worst, active = 0.0, 0
+    for i in range(w.S):
+        T = w.durations[i]
+        for j in range(w.M_gen):
+            t = (j + 1) * T / w.M_gen
+            for col, order, gmax in ((0, 1, 4.0), (1, 2, 8.0)):
+                vec = np.array([b["coeffs"][i, ax] @ CZ.deriv_row(order, t) for ax in range(3)])
+                g = max(0.0, vec @ vec - gmax ** 2) ** 2
+                inc = b["y_gen"][i, j, col] - a["y_gen"][i, j, col]
+                ref = w.rho * g
+                active += ref > 0
+                worst = max(worst, abs(inc - ref) / max(abs(ref), 1e-12 * abs(b["y_gen"]).max(), 1e-300))
+    return worst if active else np.inf
+
+
+def test_numeric_dual_step_is_rho_times_g():
+    assert numeric_dual_error() < 1e-9

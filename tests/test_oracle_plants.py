@@ -15,9 +15,9 @@ from oracle import capi
 from oracle import centralized as CZ
 from paper_2507_10290_gb300 import workloads as W
 
-from test_oracle_pins import (_box_instance, _numpy_F, adaptive_dual_continuity_error, adaptive_kkt_error,
-                              adaptive_rule_violations, polytope_kkt_errors, polytope_rotation_error, read_golden,
-                              scaled_relerr)
+from test_oracle_pins import (_box_instance, _numpy_F, _quadratic_rows_ok, adaptive_dual_continuity_error,
+                              adaptive_kkt_error, adaptive_rule_violations, numeric_dual_error, polytope_kkt_errors,
+                              polytope_rotation_error, read_golden, residual_errors, scaled_relerr)
 
 
 def pin_closed_form(lib):
@@ -132,9 +132,26 @@ def pin_polytope_rotation(lib):
     return polytope_rotation_error(lib) < 1e-11
 
 
-ALL_PINS = [pin_projection, pin_closed_form, pin_numeric_stationary, pin_free_fixed_point,
-            pin_active_set, pin_pin_fixed_point, pin_adaptive_rule, pin_adaptive_dual, pin_adaptive_kkt,
-            pin_polytope_rotation, pin_polytope_kkt]
+def pin_residuals(lib):
+    return residual_errors(lib) < 1e-10
+
+
+def pin_numeric_dual(lib):
+    return numeric_dual_error(lib) < 1e-9
+
+
+def pin_ball_corridor(lib):
+    return _quadratic_rows_ok("ball", lib)
+
+
+def pin_velocity_norm(lib):
+    return _quadratic_rows_ok("vn", lib)
+
+
+# cheap pins first: a planted mistake stops at the first pin that rejects it
+ALL_PINS = [pin_projection, pin_residuals, pin_closed_form, pin_numeric_dual, pin_numeric_stationary,
+            pin_free_fixed_point, pin_active_set, pin_velocity_norm, pin_ball_corridor, pin_pin_fixed_point,
+            pin_adaptive_rule, pin_adaptive_dual, pin_adaptive_kkt, pin_polytope_rotation, pin_polytope_kkt]
 
 PLANTS = {
     "rhs without rho": ("for (int l = 0; l < NL; ++l) rhs[l] *= rho;\n        chol_solve",
@@ -164,6 +181,30 @@ PLANTS = {
                                   "sd->Ao[row * NL + a * NC + k] = (real)nf[a] * beta_rk(1, k, t);"),
     "polytope offset sign": ("sd->b[row] = pb->poly_h[(size_t)gi * pb->F_poly + f];",
                              "sd->b[row] = -pb->poly_h[(size_t)gi * pb->F_poly + f];"),
+    # quadratic rows inside the iteration (Eq. 18a, 18f-g)
+    "ball rhs with +w": ("d3[a] = phb[((size_t)i * Mq + j) * 3 + a] - wb[((size_t)i * Mq + j) * 3 + a];",
+                         "d3[a] = phb[((size_t)i * Mq + j) * 3 + a] + wb[((size_t)i * Mq + j) * 3 + a];"),
+    "velocity-norm rhs with +w": ("d3[a] = phv[((size_t)i * Mv + j) * 3 + a] - wv[((size_t)i * Mv + j) * 3 + a];",
+                                  "d3[a] = phv[((size_t)i * Mv + j) * 3 + a] + wv[((size_t)i * Mv + j) * 3 + a];"),
+    "velocity-norm rows on position": ("sample_matrix(1, t, sd->Av + (size_t)j * 3 * NL);",
+                                       "sample_matrix(0, t, sd->Av + (size_t)j * 3 * NL);"),
+    "ball rows missing from K": ("sample_matrix(0, t, sd->Ab + (size_t)j * 3 * NL);\n      add_AtA(sd->K, sd->Ab + (size_t)j * 3 * NL, 3, rho);",
+                                 "sample_matrix(0, t, sd->Ab + (size_t)j * 3 * NL);"),
+    "velocity-norm rows missing from K": ("sample_matrix(1, t, sd->Av + (size_t)j * 3 * NL);\n      add_AtA(sd->K, sd->Av + (size_t)j * 3 * NL, 3, rho);",
+                                          "sample_matrix(1, t, sd->Av + (size_t)j * 3 * NL);"),
+    "ball dual forgets its past": ("wb[((size_t)i * Mq + j) * 3 + a] = qv[a] - ph[a];",
+                                   "wb[((size_t)i * Mq + j) * 3 + a] = w3[a] - ph[a];"),
+    # residuals (Eq. 19-20)
+    "r_d without rho": ("matvec_t_add(sd[i].Mt, NR, dz, rho, rdv);", "matvec_t_add(sd[i].Mt, NR, dz, 1, rdv);"),
+    "r_d without M^T": ("matvec_t_add(sd[i].Mt, NR, dz, rho, rdv);\n      rd2 += dotn(rdv, rdv, NL);",
+                        "for (int q = 0; q < NR; ++q) rd2 += rho * rho * dz[q] * dz[q];"),
+    "r_d from the end side only": ("dz[q] = sd[i].E[q] * (z[zi] - zo[zi]);",
+                                   "dz[q] = side ? sd[i].E[q] * (z[zi] - zo[zi]) : 0;"),
+    "r_p over orders < p only": ("rp2 += gap * gap;                                       /* Eq. 19 */",
+                                 "if (r < PO) rp2 += gap * gap;"),
+    # numerical-step dual (Eq. 17)
+    "numeric dual without rho": ("yg[((size_t)i * Mg + j) * 2 + g2] += rho * g;",
+                                 "yg[((size_t)i * Mg + j) * 2 + g2] += g;"),
 }
 
 
