@@ -150,7 +150,8 @@ typedef struct top_problem {
    * couple the axes; the library factorises each segment's local matrix in
    * the eigenbasis of sum_f n_f n_f^T, where it is block diagonal.  Closed-form
    * step only, fixed rho (adaptive_rho: TOP_E_NOTSUP); such problems run in the
-   * streaming form.  M_poly = 0: no polytopes. */
+   * cluster-resident form (one thread-block cluster per trajectory, up to 16 CTAs;
+   * longer trajectories stream).  M_poly = 0: no polytopes. */
   int32_t M_poly;
   int32_t F_poly;             /* faces per segment (>= 1 when M_poly > 0) */
   const double *poly_n;       /* [S][F_poly][3] face normals (any length; rows scale with it) */
@@ -277,8 +278,10 @@ int64_t top_launch_count(const top_handle *h);
  * trajectory short enough for one CTA of the resident kernel; otherwise
  * TOP_E_LIMIT.  The first call on a device looks up the array's device
  * address (once, with that device current): make it before any stream
- * capture.  All calls share the array; calls whose GPU work overlaps race on
- * it and must be serialised by the caller.  Synchronises `stream` like
+ * capture.  The address is kept for the life of the device's primary
+ * context: do not call it on a device after cudaDeviceReset.  All calls share
+ * the array; calls whose GPU work overlaps race on it and must be serialised
+ * by the caller.  Synchronises `stream` like
  * top_solve.  Errors: TOP_E_INVAL, TOP_E_NOTSUP, TOP_E_LIMIT, TOP_E_NUMERIC,
  * TOP_E_CUDA. */
 int top_solve_noalloc(const top_problem *pb, top_result *res, int precision, void *stream);

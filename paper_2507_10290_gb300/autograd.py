@@ -25,13 +25,15 @@ class TopCost(torch.autograd.Function):
         ctx.solver = solver
         ctx.workload = workload
         ctx.tensors = tensors
+        ctx.like = ((waypoints.device, waypoints.dtype), (durations.device, durations.dtype))
         return out["cost"].clone()
 
     @staticmethod
     def backward(ctx, gcost):
         dw, dT = ctx.solver.grad(ctx.workload, dJ=gcost.detach().to(torch.float64).contiguous(),
                                  tensors=ctx.tensors)
-        return dw, dT, None, None
+        (dev_w, dt_w), (dev_T, dt_T) = ctx.like  # gradients live where their inputs do
+        return dw.to(device=dev_w, dtype=dt_w), dT.to(device=dev_T, dtype=dt_T), None, None
 
 
 def top_cost(waypoints, durations, solver: "_top.Solver", workload):

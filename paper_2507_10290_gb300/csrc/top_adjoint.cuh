@@ -250,7 +250,7 @@ int run_adjoint_t(const StreamArgs &Fw, AdjArgs A, int ckpt, void *const *ck_bas
   cudaStream_t st = (cudaStream_t)stream;
   const int threads = 256;
   int blocks = (Fw.total + threads - 1) / threads;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > sm_count() * 8) blocks = sm_count() * 8;
   void *work[4] = {Fw.z, Fw.uL, Fw.uRp, Fw.uR0};
   const int K = Fw.p.max_iters;
   stream_init<R, 0><<<blocks, threads, 0, st>>>(Fw);

@@ -286,15 +286,15 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
       sh_rp[l] = rp2;
       sh_rd[l] = rd2;
       __syncthreads();
-      if (warp == 0) {  // this CTA's shares in a fixed order
-        R a1 = R(0), a2 = R(0);
-        for (int x = lane; x < C; x += 32) { a1 += sh_rp[x]; a2 += sh_rd[x]; }
+      if (warp == 0) {  // this CTA's shares, accumulated in FP64 in a fixed order
+        double a1 = 0.0, a2 = 0.0;
+        for (int x = lane; x < C; x += 32) { a1 += double(sh_rp[x]); a2 += double(sh_rd[x]); }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           a1 += __shfl_xor_sync(0xffffffffu, a1, o);
           a2 += __shfl_xor_sync(0xffffffffu, a2, o);
         }
-        if (lane == 0) { part[0] = double(a1); part[1] = double(a2); }
+        if (lane == 0) { part[0] = a1; part[1] = a2; }
       }
       cl.sync();
       if (rank == 0 && l == 0 && !done) {  // shares in rank order, the stop decision

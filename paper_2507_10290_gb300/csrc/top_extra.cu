@@ -67,11 +67,11 @@ int launch_sample(const int32_t *off, const double *T, int B, int M, int order, 
   cudaStream_t st = (cudaStream_t)stream;
   if (B <= 0) return 0;
   int bt = (B + 127) / 128;
-  if (bt > 152 * 8) bt = 152 * 8;
+  if (bt > sm_count() * 8) bt = sm_count() * 8;
   traj_times_kernel<<<bt, 128, 0, st>>>(off, T, B, tstart, ttot);
   const long long n = (long long)B * M;
   long long bs = (n + 255) / 256;
-  if (bs > 152 * 16) bs = 152 * 16;
+  if (bs > sm_count() * 16) bs = sm_count() * 16;
   sample_kernel<<<(int)bs, 256, 0, st>>>(off, tstart, ttot, coeffs, B, M, order, out);
   return (int)cudaGetLastError();
 }
@@ -79,7 +79,7 @@ int launch_sample(const int32_t *off, const double *T, int B, int M, int order, 
 int launch_time_step(double *T, const double *dT, int S, double kT, double lr, void *stream) {
   if (S <= 0) return 0;
   int blocks = (S + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > sm_count() * 8) blocks = sm_count() * 8;
   time_step_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(T, dT, S, kT, lr);
   return (int)cudaGetLastError();
 }

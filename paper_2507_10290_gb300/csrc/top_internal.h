@@ -189,6 +189,20 @@ inline cudaError_t func_attr_once(const void *kern, cudaFuncAttribute attr, int 
   return cudaSuccess;
 }
 
+// Streaming multiprocessors of the current device (grid-stride kernels cap
+// their grids at a multiple of it); queried once per device.
+inline int sm_count() {
+  static int counts[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 128;  // any count > 0 is correct
+  if (counts[dev] <= 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 128;
+    counts[dev] = n;
+  }
+  return counts[dev];
+}
+
 // launchers (defined in the .cu files)
 // copy (optional, [2S + 1] ints of workspace): reuse the inverse of the first
 // interior segment for interior segments of the same duration

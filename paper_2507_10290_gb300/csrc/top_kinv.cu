@@ -445,7 +445,7 @@ int launch_kinv_poly(const DevProblem &p, double rho, bool fp64, const PolyData 
   if (p.S == 0) return 0;
   const int threads = 128;
   int blocks = (p.S + threads - 1) / threads;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > sm_count() * 32) blocks = sm_count() * 32;
   cudaStream_t st = (cudaStream_t)stream;
   const bool samples = p.inner == 0 && (p.M_box > 0 || p.M_ball > 0 || p.M_vn > 0);
 #define TOP_KP(SMP, R)                                                                                   \
@@ -464,7 +464,7 @@ int launch_keig(const DevProblem &p, void *E32, void *E64, int *err_flag, void *
   if (p.S == 0) return 0;
   const int threads = 128;
   int blocks = (p.S + threads - 1) / threads;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > sm_count() * 32) blocks = sm_count() * 32;
   const bool samples = p.inner == 0 && (p.M_box > 0 || p.M_ball > 0 || p.M_vn > 0);
   if (samples)
     keig_kernel<true><<<blocks, threads, 0, (cudaStream_t)stream>>>(p, (float *)E32, (double *)E64, err_flag);
@@ -480,7 +480,7 @@ __global__ void fill_kernel(double *x, int n, double v) {
 int launch_fill(double *x, int n, double v, void *stream) {
   if (n <= 0) return 0;
   int blocks = (n + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > sm_count() * 8) blocks = sm_count() * 8;
   fill_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(x, n, v);
   return (int)cudaGetLastError();
 }
@@ -502,7 +502,7 @@ int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_
   if (p.S == 0) return 0;
   const int threads = 128;
   int blocks = (p.S + threads - 1) / threads;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > sm_count() * 32) blocks = sm_count() * 32;
   const bool samples = p.inner == 0 && (p.M_box > 0 || p.M_ball > 0 || p.M_vn > 0);
   cudaStream_t st = (cudaStream_t)stream;
   int *list = copy ? copy + p.S : nullptr;
@@ -510,7 +510,7 @@ int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_
     cudaError_t e = cudaMemsetAsync(list, 0, sizeof(int), st);
     if (e != cudaSuccess) return (int)e;
     int mb = (p.S + 255) / 256;
-    if (mb > 152 * 16) mb = 152 * 16;
+    if (mb > sm_count() * 16) mb = sm_count() * 16;
     kinv_mark_kernel<<<mb, 256, 0, st>>>(p, copy, list);
   }
   if (samples)
@@ -519,7 +519,7 @@ int launch_kinv(const DevProblem &p, double rho, void *G32, void *G64, int *err_
     kinv_kernel<false><<<blocks, threads, 0, st>>>(p, rho, (float *)G32, (double *)G64, err_flag, list);
   if (copy) {
     int cb = (p.S + 255) / 256;
-    if (cb > 152 * 16) cb = 152 * 16;
+    if (cb > sm_count() * 16) cb = sm_count() * 16;
     kinv_copy_kernel<<<cb, 256, 0, st>>>(copy, p.S, (float *)G32, (double *)G64);
   }
   return (int)cudaGetLastError();

@@ -23,8 +23,11 @@
 // Host code never uses the array's name as a device address (in host code it
 // is only a stand-in symbol): the first call on each device, with that device
 // current, looks the address up once with cudaGetSymbolAddress and keeps it;
-// make that first call before any stream capture.  No cudaMalloc, cudaFree
-// or allocating library routine is called here.
+// make that first call before any stream capture.  The kept address belongs
+// to the device's primary context: it stays valid while that context lives,
+// which is the whole process unless the caller resets the device
+// (cudaDeviceReset), after which no call may be made on that device.  No
+// cudaMalloc, cudaFree or allocating library routine is called here.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -93,6 +96,7 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
       !(pb->eps >= 0.0))
     return TOP_E_INVAL;
   if (pb->mode != TOP_PIN && pb->mode != TOP_FREE) return TOP_E_INVAL;
+  if (pb->inner != TOP_CLOSED_FORM && pb->inner != TOP_NUMERIC) return TOP_E_INVAL;  // as top_solve
   if (pb->inner != TOP_CLOSED_FORM || pb->M_gen != 0) return TOP_E_NOTSUP;
   if (pb->adaptive_rho != 0) return TOP_E_NOTSUP;  // the fixed scratch has no room for the adaptive-rho data
   if (pb->M_poly != 0) return TOP_E_NOTSUP;        // nor for the polytope family's per-axis inverses

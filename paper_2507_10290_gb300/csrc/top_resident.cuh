@@ -24,9 +24,9 @@
 //   2. publish the start derivatives; barrier
 //   3. junction i+1 (owned by thread i): consensus update, primal-residual
 //      share (Eq. 19) on check iterations; barrier
-//   4. on check iterations: dual residual (Eq. 20), per-trajectory
-//      reductions in a fixed order, stopping test (Eq. 21), and with adaptive
-//      rho the update of Eq. 22; barrier
+//   4. on check iterations: dual residual (Eq. 20), per-trajectory FP64
+//      reductions of the segments' shares in a fixed order, stopping test
+//      (Eq. 21), and with adaptive rho the update of Eq. 22; barrier
 //   5. after a change of rho (adaptive rho only): the thread's own junction
 //      targets, slack duals and projection states rescaled, its local inverse
 //      rebuilt for the new rho; barrier
@@ -289,15 +289,16 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
       const int warp = l >> 5, lane = l & 31, nw = C >> 5;
       for (int t = warp; t < pk.ntraj; t += nw) {
         if (sdone[t]) continue;
-        R a1 = R(0), a2 = R(0);  // fixed order: lane-strided, then a butterfly
-        for (int x = soff[t] + lane; x < soff[t + 1]; x += 32) { a1 += sh_rp[x]; a2 += sh_rd[x]; }
+        // FP64 accumulation of the shares in a fixed order: lane-strided, then a butterfly
+        double a1 = 0.0, a2 = 0.0;
+        for (int x = soff[t] + lane; x < soff[t + 1]; x += 32) { a1 += double(sh_rp[x]); a2 += double(sh_rd[x]); }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           a1 += __shfl_xor_sync(0xffffffffu, a1, o);
           a2 += __shfl_xor_sync(0xffffffffu, a2, o);
         }
         if (lane == 0) {
-          const double rp = sqrt(double(a1)), rd = sqrt(double(a2));
+          const double rp = sqrt(a1), rd = sqrt(a2);
           tr_rp[t] = rp;
           tr_rd[t] = rd;
           const int bb = stid[t];

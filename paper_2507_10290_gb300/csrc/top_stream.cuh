@@ -500,7 +500,7 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
   if (A.total == 0) return 0;
   const int threads = 256;
   int blocks = (A.total + threads - 1) / threads;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > sm_count() * 8) blocks = sm_count() * 8;
   const DevProblem &p = A.p;
   const int Mb = (fam & FAM_BOX) ? p.M_box : 0, Mq = (fam & FAM_BALL) ? p.M_ball : 0,
             Mv = (fam & FAM_VN) ? p.M_vn : 0;
@@ -532,7 +532,7 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
   // final iteration's evaluation names its k unless it is a periodic one
   const bool gen = (fam & FAM_GEN) != 0 && A.nwork;
   int wblocks = (A.total + 7) / 8;  // 8 warps per block, one warp per deferred segment
-  if (wblocks > 152 * 16) wblocks = 152 * 16;
+  if (wblocks > sm_count() * 16) wblocks = sm_count() * 16;
   auto iteration = [&](cudaStream_t s, int k, bool first) {
     const bool per = periodic && ((k + 1) % cev == 0);
     const bool check = per || (k == K - 1);

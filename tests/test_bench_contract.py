@@ -5,13 +5,16 @@ import json
 import os
 import subprocess
 import sys
+import time
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_paired_json_line():
-    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+    t0 = time.perf_counter()
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "0",
                           "--ref-seconds", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    wall = time.perf_counter() - t0
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -23,6 +26,8 @@ def test_reference_arm_prints_one_paired_json_line():
     assert d["config"]["workload"].startswith("batch of 4096 trajectories")
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    # the step fields describe what ran: the timed samples fit in the process's own run time
+    assert d["steps"] == 2 and d["steps"] * d["ms_per_step"] / 1000.0 <= wall
 
     import bench
     assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT

@@ -5,13 +5,16 @@ real-time loop that must not call cudaMalloc, a process with a fixed memory
 budget) cannot create a handle, because top_create allocates a workspace.
 top_solve_noalloc keeps its scratch in one fixed-size device array instead.
 This test calls it through the C ABI and checks it against the handle-based
-top_solve on the same inputs, twice in a row (the second call reuses the
-array the first one left behind), and checks that a problem beyond the fixed
-limit is rejected with TOP_E_LIMIT.  The file is named to run last.
+top_solve and against the CPU oracle on the same inputs, twice in a row (the
+second call reuses the array the first one left behind; around it the free
+device memory and torch's reserved memory must not change), and checks that a
+problem beyond the fixed limit is rejected with TOP_E_LIMIT.  The file is
+named to run last.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_2507_10290_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -29,7 +32,10 @@ def T():
     return top
 
 
-def noalloc_solve(T, w, precision):
+def noalloc_solve(T, w, precision, memory=None):
+    """One call of top_solve_noalloc on freshly allocated inputs and outputs;
+    with `memory` (a list), appends the (free device bytes, torch reserved
+    bytes) seen just before and just after the call."""
     import torch
     s = T.Solver.__new__(T.Solver)  # marshalling helpers only; no handle is created
     s.torch = torch
@@ -38,7 +44,13 @@ def noalloc_solve(T, w, precision):
     pb = s.make_problem(w, tensors, T.TOP_MEM_DEVICE)
     r = T.Solver.result_struct(out)
     prec = T.TOP_FP64 if precision == "fp64" else T.TOP_FP32
+    torch.cuda.synchronize()
+    before = (torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved())
     rc = T.top_solve_noalloc(pb, r, prec, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    after = (torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved())
+    if memory is not None:
+        memory.append((before, after))
     return rc, {k: v.cpu().numpy() for k, v in out.items()}
 
 
@@ -56,14 +68,20 @@ def test_noalloc_matches_top_solve_twice(T, precision):
         ref_solver = T.Solver(max_batch=w.B, max_segments=w.S, precision=precision, max_samples=16)
         ref = {k: v.cpu().numpy() for k, v in ref_solver.solve(w).items()}
         ref_solver.close()
+        orc = oracle.solve(w)
+        memory = []
         for call in range(2):
-            rc, got = noalloc_solve(T, w, precision)
+            rc, got = noalloc_solve(T, w, precision, memory)
             assert rc == T.TOP_OK, (call, T.top_strerror(rc))
-            err = np.linalg.norm(scaled(got["coeffs"] - ref["coeffs"], w.durations)) / \
-                np.linalg.norm(scaled(ref["coeffs"], w.durations))
-            assert err <= TOL[precision], (call, err)
-            assert np.max(np.abs(got["cost"] - ref["cost"])) <= TOL[precision] * np.max(np.abs(ref["cost"]))
-            assert np.array_equal(got["iters"], ref["iters"]) and np.array_equal(got["status"], ref["status"])
+            for other in (ref, orc):  # the handle-based solve and the CPU oracle
+                err = np.linalg.norm(scaled(got["coeffs"] - other["coeffs"], w.durations)) / \
+                    np.linalg.norm(scaled(other["coeffs"], w.durations))
+                assert err <= TOL[precision], (call, err)
+                assert np.max(np.abs(got["cost"] - other["cost"])) <= TOL[precision] * np.max(np.abs(other["cost"]))
+                assert np.array_equal(got["iters"], other["iters"]) and np.array_equal(got["status"], other["status"])
+        # the second call finds its array resident and allocates nothing
+        before, after = memory[1]
+        assert before == after, (before, after)
 
 
 def test_noalloc_rejects_problems_beyond_its_limit(T):
