@@ -141,7 +141,7 @@ int resident_capacity(const top_handle *h, const top_problem *pb) {
   const int tmax = max_cta_threads(h);
   int cap = h->cfg.segs_per_cta > 0 ? std::min(tmax, h->cfg.segs_per_cta / 32 * 32) : tmax;
   for (int C = cap; C >= 32; C -= 32) {
-    ResLayout L = res_layout(C, C / 4, Mb, Mq, Mv, (int)rbytes(h));
+    ResLayout L = res_layout_resident(C, C / 4, Mb, Mq, Mv, (int)rbytes(h));
     if (L.total <= (size_t)h->smem_optin) return C;
   }
   return 0;
@@ -652,7 +652,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     const int ntp = std::max(1, max_ntraj);
     const int Mb = (fam & FAM_BOX) ? pb.M_box : 0, Mq = (fam & FAM_BALL) ? pb.M_ball : 0,
               Mv = (fam & FAM_VN) ? pb.M_vn : 0;
-    const ResLayout L = res_layout(C, ntp, Mb, Mq, Mv, (int)rbytes(h));
+    const ResLayout L = res_layout_resident(C, ntp, Mb, Mq, Mv, (int)rbytes(h));
     ResidentArgs ra{};
     ra.p = dp; ra.r = dr; ra.G = h->G; ra.packs = h->d_packs; ra.traj_list = h->d_tlist; ra.ntp = ntp;
     ra.E = adapt ? h->E : nullptr;

@@ -91,7 +91,7 @@ constexpr int kClusterNtp = 8;  // res_layout's trajectory slots for the cluster
 // launch on the host and carves the buffer on the device.
 struct ResLayout {
   size_t red_rp, red_rd, tr_rp, tr_rd;           // double arrays
-  size_t p, m, zP, eS, dz, ybox, qball, qvn, tabB, tabQ, tabV, tabP;  // element arrays
+  size_t p, m, zP, eS, dz, ybox, qball, qvn, tabB, tabQ, tabV, tabP, ch;  // element arrays
   size_t off, done, tid, flag;                   // int arrays
   size_t rho, fac;                               // double arrays (per trajectory)
   size_t total;
@@ -99,7 +99,12 @@ struct ResLayout {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, int Mv, int rb, int Mp = 0) {
+// mreg (the resident kernel): the end-side targets of a segment's end slot
+// live in its thread's registers, so m holds only the start slots of the
+// pack's trajectories ([trajectory][21]); the coefficients of check
+// iterations are kept in ch ([24][C]) for the output.
+__host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, int Mv, int rb, int Mp = 0,
+                                                bool mreg = false) {
   ResLayout L{};
   const size_t J = size_t(C) + size_t(ntp);
   size_t o = 0;
@@ -109,7 +114,7 @@ __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, 
   L.tr_rd = o;  o += sizeof(double) * ntp;
   o = align_up(o, 16);
   L.p = o;      o += size_t(rb) * 21 * J;  // [slot][21] start-side targets
-  L.m = o;      o += size_t(rb) * 21 * J;  // [slot][21] end-side targets
+  L.m = o;      o += size_t(rb) * 21 * (mreg ? size_t(ntp) : J);  // [slot][21] end-side targets
   L.zP = o;     o += size_t(rb) * 3 * J;   // [slot][3] pinned positions
   L.eS = o;     o += size_t(rb) * 21 * C;  // [segment][21] published start derivatives
   L.dz = o;     o += size_t(rb) * 21 * J;  // [slot][21] consensus change (check iterations)
@@ -120,6 +125,7 @@ __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, 
   L.tabQ = o;   o += size_t(rb) * 8 * Mq;
   L.tabV = o;   o += size_t(rb) * 8 * Mv;
   L.tabP = o;   o += size_t(rb) * 8 * Mp;  // polytope sample rows (cluster form)
+  L.ch = o;     o += mreg ? size_t(rb) * 24 * C : 0;
   o = align_up(o, 16);
   L.off = o;    o += sizeof(int) * (ntp + 1);
   L.done = o;   o += sizeof(int) * ntp;
@@ -130,6 +136,11 @@ __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, 
   L.fac = o;    o += sizeof(double) * ntp;
   L.total = align_up(o, 16);
   return L;
+}
+
+// the layout of the resident kernel (top_resident.cuh)
+__host__ __device__ inline ResLayout res_layout_resident(int C, int ntp, int Mb, int Mq, int Mv, int rb) {
+  return res_layout(C, ntp, Mb, Mq, Mv, rb, 0, true);
 }
 
 // Streaming form (trajectories longer than a resident CTA): state in global
@@ -237,6 +248,43 @@ struct AdjArgs {
   double *Pbar;              // [Jn][3]
   const double *dJ;          // [B]
 };
+// Resident adjoint (top_adjres.cuh): packs of whole trajectories, fixed rho,
+// closed-form step without inequality rows.
+struct AdjResArgs {
+  DevProblem p;
+  const void *G;          // [36][S] packed local inverses (iteration type)
+  const Pack *packs;
+  const int *traj_list;
+  int ntp;                // trajectory slots per pack
+  int ckpt;               // checkpoint interval in iterations
+  int Jn;                 // global junction slots, S + B
+  void *ck;               // [ceil(K / ckpt)][2][21][Jn] checkpoints of the slot state (p, m)
+  void *tape;             // [ckpt][2][21][Jn] the slot state entering each iteration of a block
+  const double *dJ;       // [B] cost seeds
+  double *dw;             // [Jn][3] dJ/d(waypoints) (interior junctions written, others left)
+  double *dT;             // [S] dJ/d(durations)
+};
+struct AdjResLayout {
+  size_t p, m, pb, mb, zP, eS, off, tid, total;
+};
+__host__ __device__ inline AdjResLayout adjres_layout(int C, int ntp, int rb) {
+  AdjResLayout L{};
+  const size_t J = size_t(C) + size_t(ntp);
+  size_t o = 0;
+  L.p = o;   o += size_t(rb) * 21 * J;   // [slot][21] forward targets p, m and their adjoints
+  L.m = o;   o += size_t(rb) * 21 * J;
+  L.pb = o;  o += size_t(rb) * 21 * J;
+  L.mb = o;  o += size_t(rb) * 21 * J;
+  L.zP = o;  o += size_t(rb) * 3 * J;
+  L.eS = o;  o += size_t(rb) * 21 * size_t(C);
+  o = align_up(o, 16);
+  L.off = o; o += sizeof(int) * (ntp + 1);
+  L.tid = o; o += sizeof(int) * ntp;
+  L.total = align_up(o, 16);
+  return L;
+}
+int launch_adjres_f32(const AdjResArgs &a, int nblocks, int C, size_t smem, void *stream);
+int launch_adjres_f64(const AdjResArgs &a, int nblocks, int C, size_t smem, void *stream);
 int launch_adjoint_f32(const StreamArgs &f, const AdjArgs &a, int ckpt, void *const *ck, void *const *tape,
                        const size_t *bytes, double *dw, double *dT, void *stream);
 int launch_adjoint_f64(const StreamArgs &f, const AdjArgs &a, int ckpt, void *const *ck, void *const *tape,

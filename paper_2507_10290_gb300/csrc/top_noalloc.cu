@@ -134,7 +134,7 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
   const int rb = precision == TOP_FP64 ? 8 : 4;
   int cap = 0;
   for (int C = (precision == TOP_FP64 ? 256 : 512); C >= 32 && cap == 0; C -= 32)  // FP64: 256 threads per CTA
-    if (res_layout(C, C / 4, pb->M_box, pb->M_ball, pb->M_vn, rb).total <= (size_t)slot->smem_optin) cap = C;
+    if (res_layout_resident(C, C / 4, pb->M_box, pb->M_ball, pb->M_vn, rb).total <= (size_t)slot->smem_optin) cap = C;
   if (cap == 0) return TOP_E_LIMIT;
   Pack packs[kMaxBatch];
   int npack = 0, max_nseg = 0, max_ntraj = 0;
@@ -189,7 +189,7 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
     return TOP_E_CUDA;
   const int C = std::max(32, (max_nseg + 31) / 32 * 32);
   const int ntp = std::max(1, max_ntraj);
-  const ResLayout L = res_layout(C, ntp, (fam & FAM_BOX) ? pb->M_box : 0, (fam & FAM_BALL) ? pb->M_ball : 0,
+  const ResLayout L = res_layout_resident(C, ntp, (fam & FAM_BOX) ? pb->M_box : 0, (fam & FAM_BALL) ? pb->M_ball : 0,
                                  (fam & FAM_VN) ? pb->M_vn : 0, rb);
   ResidentArgs ra{};
   ra.p = dp; ra.r = dr; ra.G = G; ra.packs = d_packs; ra.traj_list = d_list; ra.ntp = ntp;

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   const int ntp = A.ntp;
   const int J = C + ntp;
   const int Mb = BOX ? p.M_box : 0, Mq = BALL ? p.M_ball : 0, Mv = VN ? p.M_vn : 0;
-  const ResLayout L = res_layout(C, ntp, Mb, Mq, Mv, (int)sizeof(R));
+  const ResLayout L = res_layout_resident(C, ntp, Mb, Mq, Mv, (int)sizeof(R));
   double *red_rp = (double *)(smem + L.red_rp);  // FP64 cost shares (epilogue)
   R *sh_rp = (R *)(smem + L.red_rp);              // residual shares (check iterations)
   R *sh_rd = (R *)(smem + L.red_rd);
@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   R *tabB = (R *)(smem + L.tabB);
   R *tabQ = (R *)(smem + L.tabQ);
   R *tabV = (R *)(smem + L.tabV);
+  R *sch = (R *)(smem + L.ch);  // [24][C] coefficients of the last check iteration (the output)
   int *soff = (int *)(smem + L.off);
   int *sdone = (int *)(smem + L.done);
   int *stid = (int *)(smem + L.tid);
@@ -100,7 +101,9 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   }
   for (int t = l; t < ntp; t += C) { tr_rp[t] = 0.0; tr_rd[t] = 0.0; srho[t] = p.rho; sfac[t] = 1.0; }
   if (l == 0) *sflag = 0;
-  for (int q = l; q < NJ * J; q += C) { sdz[q] = R(0); sp[q] = R(0); sm[q] = R(0); }
+  for (int q = l; q < NJ * J; q += C) { sdz[q] = R(0); sp[q] = R(0); }
+  for (int q = l; q < NJ * ntp; q += C) sm[q] = R(0);
+  for (int q = l; q < 24 * C; q += C) sch[q] = R(0);
   for (int q = l; q < 3 * J; q += C) szP[q] = R(0);
   if (BOX) for (int q = l; q < 6 * Mb * C; q += C) sybox[q] = R(0);
   if (BALL) for (int q = l; q < 3 * Mq * C; q += C) sqball[q] = R(0);
@@ -128,8 +131,13 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   const int b = stid[tb];
   const int g = p.seg_offset[b] + i;        // global segment
   const int jS = l + tb, jE = l + tb + 1;   // junction slots in shared memory
-  R *pS = sp + jS * NJ, *mS = sm + jS * NJ;  // start slot
-  R *pE = sp + jE * NJ, *mE = sm + jE * NJ;  // end slot (owned by this thread)
+  R *pS = sp + jS * NJ, *mS = sm + tb * NJ;  // start slot (m only at a trajectory's start: [trajectory][21])
+  R *pE = sp + jE * NJ;                      // end slot (owned by this thread)
+  // m at the end slot is read and written by this thread alone (its local step
+  // and its junction update): it lives in registers, not in shared memory
+  R mE[NJ];
+#pragma unroll
+  for (int q = 0; q < NJ; ++q) mE[q] = R(0);
   const R *eSnext = seS + (l + 1) * NJ;
 
   SegConst<R> sc;
@@ -150,7 +158,9 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
     }
     // Init of Algorithm 1: z position rows from the path, other orders zero,
     // the trajectory's two ends from the boundary states, every u zero
+#pragma unroll
     for (int a = 0; a < AX; ++a)
+#pragma unroll
       for (int r = 0; r < ND; ++r) {
         const int row = a * ND + r;
         if (!last) {
@@ -180,11 +190,6 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
 #pragma unroll
   for (int r = 0; r < ND; ++r) fs[r] = R(fact(r)) * sc.s[r];
 
-  R ch[AX][NC];
-#pragma unroll
-  for (int a = 0; a < AX; ++a)
-#pragma unroll
-    for (int k = 0; k < NC; ++k) ch[a][k] = R(0);
 
   const int cev = p.check_every > 0 ? p.check_every : 1;
   const bool periodic = p.eps > 0.0 || res.history != nullptr;
@@ -195,6 +200,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
     R eE[AX][ND];
     R eSv[AX][ND];
     if (act) {
+      R ch[AX][NC];
       // ---- 1. local step (Eq. 18a, 18d-g) ----
       R wS[AX][ND], wE[AX][ND];
 #pragma unroll
@@ -212,6 +218,13 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
         end_derivs_f(ch[a], sc.s, fs, eSv[a], eE[a]);
 #pragma unroll
         for (int r = 0; r < ND; ++r) seS[l * NJ + a * ND + r] = eSv[a][r];
+      }
+      // a check iteration may be a trajectory's last: keep its coefficients
+      if (check) {
+#pragma unroll
+        for (int a = 0; a < AX; ++a)
+#pragma unroll
+          for (int q = 0; q < NC; ++q) sch[(a * NC + q) * C + l] = ch[a][q];
       }
     }
     __syncthreads();
@@ -368,6 +381,11 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   // ---- outputs: coefficients in the paper's basis, FP64 cost per trajectory ----
   double Ji = 0.0;
   if (valid) {
+    R ch[AX][NC];
+#pragma unroll
+    for (int a = 0; a < AX; ++a)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) ch[a][q] = sch[(a * NC + q) * C + l];
     const double T = p.durations[g];
     double sd[NC];
     sd[0] = 1.0;
