@@ -400,11 +400,58 @@ def run_ours(args):
     }
     if args.precision == "fp32" and not args.no_fp64:
         line["fp64_same_workload"] = fp64_same_workload(top, w, world, flush)
+    if args.precision == "fp32" and not args.no_adjoint:
+        line["adjoint"] = adjoint_batch(top, world, flush, fp32_peak)
     if not args.no_tolerance:
         line["to_tolerance"] = time_to_tolerance(top, B, rank, world)
     if cpu is not None:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)
+
+
+# algorithmic FLOPs of one segment-iteration of the adjoint (top_grad, no
+# inequality rows): the forward iteration (1392, see above) plus its
+# transpose, which re-forms the local solve (1392) and applies the transposed
+# maps to the adjoints (1392); the checkpoint recomputation is not counted
+ADJ_FLOP_PER_SEG_IT = 3 * FLOP_PER_SEG_IT
+
+
+def adjoint_batch(top, world, flush, fp32_peak, steps=5):
+    """top_grad on the differentiation workload (256 trajectories x 256
+    segments, gradient of the cost after 100 iterations w.r.t. every waypoint
+    and duration, checkpoints every 10 iterations), FP32; CUDA events around
+    the whole call and the library's own events around the adjoint kernel."""
+    import torch
+    w = W.grad_batch()
+    s = top.Solver(max_batch=w.B, max_segments=w.S, precision="fp32", max_samples=0)
+    tensors = s.device_inputs(w)
+    s.grad(w, tensors=tensors)  # warm-up: workspace, plan
+    top.top_set_profiling(s.handle, True)
+    st = torch.cuda.current_stream()
+    ms, kms = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        s.grad(w, tensors=tensors, stream=st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        kt = top.top_kernel_times(s.handle)[1]
+        kms.append(kt[1] if kt[1] > 0 else kt[2])
+    top.top_set_profiling(s.handle, False)
+    s.close()
+    m, km = float(np.mean(ms)), float(np.mean(kms))
+    seg_it = w.S * w.max_iters
+    achieved = ADJ_FLOP_PER_SEG_IT * seg_it / (km / 1000.0) / 1e12
+    return {"workload": f"gradient of the cost after {w.max_iters} iterations w.r.t. waypoints and durations, "
+                        f"{w.B} trajectories x 256 segments, PIN, rho=1, checkpoints every 10 iterations",
+            "ms_per_gradient": m, "kernel_ms": km, "segment_iterations_per_s": world * seg_it / (m / 1000.0),
+            "dtype": "f32",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "kernel": "adjoint_resident_kernel<float>",
+                         "flop_per_segment_iteration": ADJ_FLOP_PER_SEG_IT}}
 
 
 def fp64_same_workload(top, w, world, flush, steps=3):
@@ -829,6 +876,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tolerance", action="store_true", help="skip the time-to-tolerance measurement")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 run of the same workload")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the top_grad measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep 512 segments per CTA (skip top_autotune)")
     ap.add_argument("--only", default="", help="with --suite: comma-separated subset of single_box, corridor, "
                     "batch, adaptive, general, polytope, speed, segments, timealloc, grad, general_full, shared")

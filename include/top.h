@@ -183,13 +183,19 @@ int top_create(const top_config *cfg, top_handle **out);
 int top_solve(top_handle *h, const top_problem *pb, top_result *res, void *stream);
 
 /* Gradient of sum_b dJ[b] * J_b, J_b the cost of trajectory b after exactly
- * pb->max_iters iterations of the closed-form iteration without inequality
- * constraints (eps ignored), with respect to the waypoints and the
- * durations, by a hand-written adjoint through the unrolled iterations with
- * checkpoints every ckpt_interval iterations.  dJ: [B]; dwaypoints: [S+B][3];
- * ddurations: [S] (same memory kind as the problem; outputs are
- * overwritten).  The paper has no gradient; this is an extension.
- * Errors: as top_solve; TOP_E_NOTSUP with inequality families or the numerical step. */
+ * pb->max_iters iterations of the closed-form iteration (Eq. 18a-g, eps
+ * ignored, fixed rho), with respect to the waypoints and the durations, by a
+ * hand-written adjoint through the unrolled iterations with checkpoints every
+ * ckpt_interval iterations.  The box, ball and velocity-norm rows are
+ * differentiated through their slack / projection steps (Eq. 18d-g); at a
+ * kink (a slack exactly 0, a projected point exactly on its sphere) the
+ * inactive branch is taken.  Without rows, trajectories of up to 256
+ * segments (FP32; fewer in FP64) run the whole sweep resident in one launch.
+ * dJ: [B]; dwaypoints: [S+B][3]; ddurations: [S] (same memory kind as the
+ * problem; outputs are overwritten; a trajectory's first and last waypoint
+ * get 0, they enter only through the boundary states).  The paper has no
+ * gradient; this is an extension.
+ * Errors: as top_solve; TOP_E_NOTSUP with polytope rows, the numerical step or adaptive rho. */
 int top_grad(top_handle *h, const top_problem *pb, const double *dJ, double *dwaypoints,
              double *ddurations, void *stream);
 
@@ -214,7 +220,7 @@ int top_sample(top_handle *h, const top_problem *pb, const double *coeffs, int32
  * dF/dT_i = dJ/dT_i + k_T from top_grad.  durations_io: [S] initial durations
  * in, final durations out; pb->durations is not read.  res (may be NULL) gets
  * a top_solve with the final durations.  Same restrictions as top_grad
- * (closed-form step, no inequality families, fixed rho).  Memory kind of pb.
+ * (closed-form step, box / ball / velocity-norm rows, fixed rho).  Memory kind of pb.
  * Errors: as top_grad; TOP_E_INVAL for k_T < 0, lr <= 0 or steps < 0. */
 int top_time_alloc(top_handle *h, const top_problem *pb, double k_T, double lr, int32_t steps,
                    double *durations_io, top_result *res, void *stream);
@@ -251,7 +257,8 @@ int top_autotune(top_handle *h, const top_problem *pb, int32_t iters, int32_t *o
  * returns, for the last top_solve, ms[0] = local-matrix precompute, ms[1] =
  * resident iteration kernel, ms[2] = streaming iteration kernels, ms[3] =
  * cluster-resident kernels (0 for a kernel that did not run), for up to n
- * entries.  Returns the number of entries written, or TOP_E_INVAL /
+ * entries.  After top_grad: ms[0] = precompute, ms[1] = resident adjoint,
+ * ms[2] = streaming adjoint (forward, recomputation and reverse sweep).  Returns the number of entries written, or TOP_E_INVAL /
  * TOP_E_STATE (profiling off). */
 int top_set_profiling(top_handle *h, int enable);
 int top_kernel_times(const top_handle *h, float *ms, int n);

@@ -893,8 +893,9 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
   fake.iters = fake.status = (int32_t *)ddurations;
   int rc = validate(h, pb_in, &fake);
   if (rc != TOP_OK) return rc;
-  if (pb_in->M_box || pb_in->M_ball || pb_in->M_vn || pb_in->M_gen || pb_in->M_poly) return TOP_E_NOTSUP;
+  if (pb_in->inner != TOP_CLOSED_FORM || pb_in->M_gen || pb_in->M_poly) return TOP_E_NOTSUP;
   if (pb_in->adaptive_rho) return TOP_E_NOTSUP;
+  const int fam = families(pb_in) & (FAM_BOX | FAM_BALL | FAM_VN);
   cudaStream_t st = (cudaStream_t)stream;
   TOP_CUDA(h, cudaSetDevice(h->device));
   const int B = pb_in->B;
@@ -937,8 +938,15 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
   const size_t o_done = take(sizeof(int) * nl), o_trp = take(sizeof(double) * nl), o_trd = take(sizeof(double) * nl);
   const size_t o_rho = take(sizeof(double) * nl), o_fac = take(sizeof(double) * nl);
   const size_t o_lt = take(sizeof(int) * (2 * (size_t)nl + 1));
-  const size_t o_ck = take((bz * 2 + buRp + buR0 + 4 * 256) * (size_t)nblk);
-  const size_t o_tape = take((bz * 2 + buRp + buR0 + 4 * 256) * (size_t)ckpt);
+  // the rows' states (box slack/dual, ball and velocity-norm projections) and their adjoints
+  const int Mb = (fam & FAM_BOX) ? pb_in->M_box : 0, Mq = (fam & FAM_BALL) ? pb_in->M_ball : 0,
+            Mv = (fam & FAM_VN) ? pb_in->M_vn : 0;
+  const size_t byb = rb * 6 * Mb * (size_t)S, bqb = rb * 3 * Mq * (size_t)S, bqv = rb * 3 * Mv * (size_t)S;
+  const size_t o_yb = take(byb), o_qb = take(bqb), o_qv = take(bqv);
+  const size_t o_ybb = take(byb), o_qbb = take(bqb), o_qvb = take(bqv);
+  const size_t one_state = bz * 2 + buRp + buR0 + byb + bqb + bqv + 7 * 256;
+  const size_t o_ck = take(one_state * (size_t)nblk);
+  const size_t o_tape = take(one_state * (size_t)ckpt);
   const size_t o_zb = take(bz), o_uLb = take(bz), o_uRb = take(bz), o_uR0b = take(buR0);
   const size_t o_eSb = take(rb * 21 * (size_t)S), o_eEb = take(rb * 21 * (size_t)S);
   const size_t o_wbS = take(rb * 21 * (size_t)S), o_wbE = take(rb * 21 * (size_t)S);
@@ -968,12 +976,22 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
     TOP_CUDA(h, cudaMemcpyAsync(sb + SP.off_T, pb_in->durations, sizeof(double) * S, cudaMemcpyHostToDevice, st));
     TOP_CUDA(h, cudaMemcpyAsync(sb + SP.off_s0, pb_in->start_state, sizeof(double) * 12 * B, cudaMemcpyHostToDevice, st));
     TOP_CUDA(h, cudaMemcpyAsync(sb + SP.off_s1, pb_in->end_state, sizeof(double) * 12 * B, cudaMemcpyHostToDevice, st));
+    if (Mb) TOP_CUDA(h, cudaMemcpyAsync(sb + SP.off_vbox, pb_in->vbox, sizeof(double) * B, cudaMemcpyHostToDevice, st));
+    if (Mq) {
+      TOP_CUDA(h, cudaMemcpyAsync(sb + SP.off_bc, pb_in->ball_c, sizeof(double) * 3 * S, cudaMemcpyHostToDevice, st));
+      TOP_CUDA(h, cudaMemcpyAsync(sb + SP.off_br, pb_in->ball_r, sizeof(double) * S, cudaMemcpyHostToDevice, st));
+    }
+    if (Mv) TOP_CUDA(h, cudaMemcpyAsync(sb + SP.off_vn, pb_in->vnorm, sizeof(double) * B, cudaMemcpyHostToDevice, st));
     TOP_CUDA(h, cudaMemcpyAsync(base + o_dJ, dJ, sizeof(double) * B, cudaMemcpyHostToDevice, st));
     pb.seg_offset = (const int32_t *)(sb + SP.off_seg);
     pb.waypoints = (const double *)(sb + SP.off_wp);
     pb.durations = (const double *)(sb + SP.off_T);
     pb.start_state = (const double *)(sb + SP.off_s0);
     pb.end_state = (const double *)(sb + SP.off_s1);
+    pb.vbox = Mb ? (const double *)(sb + SP.off_vbox) : nullptr;
+    pb.ball_c = Mq ? (const double *)(sb + SP.off_bc) : nullptr;
+    pb.ball_r = Mq ? (const double *)(sb + SP.off_br) : nullptr;
+    pb.vnorm = Mv ? (const double *)(sb + SP.off_vn) : nullptr;
     d_dJ = (const double *)(base + o_dJ);
     d_dw = (double *)(base + o_dw);
     d_dT = (double *)(base + o_dT);
@@ -984,16 +1002,78 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
   dp.start_state = pb.start_state; dp.end_state = pb.end_state;
   dp.mode = pb.mode; dp.inner = TOP_CLOSED_FORM; dp.rho = pb.rho; dp.eps = 0.0;
   dp.max_iters = K; dp.check_every = 1;
+  dp.M_box = Mb; dp.vbox = pb.vbox;
+  dp.M_ball = Mq; dp.ball_c = pb.ball_c; dp.ball_r = pb.ball_r;
+  dp.M_vn = Mv; dp.vnorm = pb.vnorm;
   DevResult dr{};
   TOP_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
   const bool fp64 = h->cfg.precision == TOP_FP64;
+  h->ran[0] = h->ran[1] = h->ran[2] = h->ran[3] = false;
   {
+    if (h->profiling) cudaEventRecord(h->ev[0], st);
     int e = launch_kinv(dp, pb.rho, fp64 ? nullptr : h->G, fp64 ? h->G : nullptr, h->d_err, st);
     if (e) return cuda_fail(h, (cudaError_t)e);
+    if (h->profiling) { cudaEventRecord(h->ev[1], st); h->ran[0] = true; }
   }
   TOP_CUDA(h, cudaMemsetAsync(d_dw, 0, sizeof(double) * 3 * Jn, st));
   TOP_CUDA(h, cudaMemsetAsync(d_dT, 0, sizeof(double) * S, st));
-  if (nl > 0 && K > 0) {
+  // resident adjoint when every trajectory fits one CTA (the whole reverse
+  // sweep in one launch, state in shared memory); the streaming form otherwise
+  int maxN = 0;
+  for (int b = 0; b < B; ++b) maxN = std::max(maxN, off[b + 1] - off[b]);
+  int rcap = 0;
+  if (h->cfg.schedule != TOP_SCHED_STREAM)
+    for (int C = 256; C >= 32 && rcap == 0; C -= 32)
+      if (adjres_layout(C, C / 4, (int)rb).total <= (size_t)h->smem_optin) rcap = C;
+  if (nl > 0 && K > 0 && maxN <= rcap && fam == 0) {
+    int npack = 0, max_nseg = 0, max_ntraj = 0;
+    bool has_long = false;
+    plan_packs(off, B, rcap, std::max(1, rcap / 4), h->h_packs, h->h_tlist, npack, max_nseg, max_ntraj, has_long);
+    h->plan_valid = false;  // the pack buffers now hold this plan
+    const size_t st_bytes = rb * 2 * 21 * Jn;  // one saved slot state
+    size_t o2 = o_dT + align_up(sizeof(double) * S, 256);
+    const size_t o_rck = o2;
+    o2 = align_up(o2 + st_bytes * nblk, 256);
+    const size_t o_rtape = o2;
+    o2 = align_up(o2 + st_bytes * ckpt, 256);
+    if (o2 > h->stream_bytes) {
+      cudaFree(h->d_stream);
+      h->d_stream = nullptr;
+      h->stream_bytes = 0;
+      cudaError_t e = cudaMalloc((void **)&h->d_stream, o2);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? TOP_E_NOMEM : cuda_fail(h, e);
+      }
+      h->stream_bytes = o2;
+      base = h->d_stream;
+      if (host) {  // the staged seeds and outputs live in this buffer
+        TOP_CUDA(h, cudaMemcpyAsync(base + o_dJ, dJ, sizeof(double) * B, cudaMemcpyHostToDevice, st));
+        d_dJ = (const double *)(base + o_dJ);
+        d_dw = (double *)(base + o_dw);
+        d_dT = (double *)(base + o_dT);
+        TOP_CUDA(h, cudaMemsetAsync(d_dw, 0, sizeof(double) * 3 * Jn, st));
+        TOP_CUDA(h, cudaMemsetAsync(d_dT, 0, sizeof(double) * S, st));
+      }
+    }
+    TOP_CUDA(h, cudaMemcpyAsync(h->d_packs, h->h_packs, sizeof(Pack) * npack, cudaMemcpyHostToDevice, st));
+    int ntl = 0;
+    for (int q = 0; q < npack; ++q) ntl += h->h_packs[q].ntraj;
+    TOP_CUDA(h, cudaMemcpyAsync(h->d_tlist, h->h_tlist, sizeof(int) * ntl, cudaMemcpyHostToDevice, st));
+    const int C = std::max(32, (max_nseg + 31) / 32 * 32);
+    const int ntp = std::max(1, max_ntraj);
+    AdjResArgs ra{};
+    ra.p = dp; ra.G = h->G; ra.packs = h->d_packs; ra.traj_list = h->d_tlist; ra.ntp = ntp;
+    ra.ckpt = ckpt; ra.Jn = (int)Jn; ra.ck = base + o_rck; ra.tape = base + o_rtape;
+    ra.dJ = d_dJ; ra.dw = d_dw; ra.dT = d_dT;
+    const size_t smem = adjres_layout(C, ntp, (int)rb).total;
+    Range r1("resident adjoint");
+    if (h->profiling) cudaEventRecord(h->ev[2], st);
+    int e = fp64 ? launch_adjres_f64(ra, npack, C, smem, st) : launch_adjres_f32(ra, npack, C, smem, st);
+    h->launches += 1;
+    if (e) return cuda_fail(h, (cudaError_t)e);
+    if (h->profiling) { cudaEventRecord(h->ev[3], st); h->ran[1] = true; }
+  } else if (nl > 0 && K > 0) {
     TOP_CUDA(h, cudaMemcpyAsync(base + o_lt, lt_b, sizeof(int) * nl, cudaMemcpyHostToDevice, st));
     TOP_CUDA(h, cudaMemcpyAsync(base + o_lt + sizeof(int) * nl, lt_pre, sizeof(int) * (nl + 1),
                                 cudaMemcpyHostToDevice, st));
@@ -1004,7 +1084,8 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
     sa.nl = nl; sa.total = total; sa.S = S; sa.Jn = (int)Jn;
     sa.z = base + o_z; sa.uL = base + o_uL; sa.dz = base + o_dz; sa.uRp = base + o_uRp; sa.uR0 = base + o_uR0;
     sa.eS = base + o_eS; sa.eE = base + o_eE; sa.ch = base + o_ch;
-    sa.ybox = sa.qball = sa.qvn = sa.ygen = nullptr;
+    sa.ybox = base + o_yb; sa.qball = base + o_qb; sa.qvn = base + o_qv;
+    sa.ygen = nullptr;
     sa.inner_iters = nullptr;
     sa.rp2 = (double *)(base + o_rp); sa.rd2 = (double *)(base + o_rd);
     sa.done = (int *)(base + o_done); sa.tr_rp = (double *)(base + o_trp); sa.tr_rd = (double *)(base + o_trd);
@@ -1015,19 +1096,23 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
     aa.zb = base + o_zb; aa.uLb = base + o_uLb; aa.uRb = base + o_uRb; aa.uR0b = base + o_uR0b;
     aa.eSb = base + o_eSb; aa.eEb = base + o_eEb; aa.wbS = base + o_wbS; aa.wbE = base + o_wbE;
     aa.Tbar = (double *)(base + o_Tb); aa.Pbar = (double *)(base + o_Pb); aa.dJ = d_dJ;
+    aa.ybb = base + o_ybb; aa.qbb = base + o_qbb; aa.qvb = base + o_qvb;
     TOP_CUDA(h, cudaMemsetAsync(base + o_zb, 0, o_eSb - o_zb, st));        // zb, uLb, uRb, uR0b
     TOP_CUDA(h, cudaMemsetAsync(base + o_wbS, 0, o_Tb - o_wbS, st));       // wbS, wbE
     TOP_CUDA(h, cudaMemsetAsync(base + o_Tb, 0, o_dJ - o_Tb, st));         // Tbar, Pbar
-    const size_t bytes[4] = {bz, bz, buRp, buR0};
-    std::vector<void *> ck((size_t)nblk * 4), tape((size_t)ckpt * 4);
+    TOP_CUDA(h, cudaMemsetAsync(base + o_ybb, 0, o_ck - o_ybb, st));       // the rows' adjoints
+    const size_t bytes[7] = {bz, bz, buRp, buR0, byb, bqb, bqv};
+    std::vector<void *> ck((size_t)nblk * 7), tape((size_t)ckpt * 7);
     size_t oc = o_ck, ot = o_tape;
     for (int c = 0; c < nblk; ++c)
-      for (int q = 0; q < 4; ++q) { ck[(size_t)c * 4 + q] = base + oc; oc = align_up(oc + bytes[q], 256); }
+      for (int q = 0; q < 7; ++q) { ck[(size_t)c * 7 + q] = base + oc; oc = align_up(oc + bytes[q], 256); }
     for (int c = 0; c < ckpt; ++c)
-      for (int q = 0; q < 4; ++q) { tape[(size_t)c * 4 + q] = base + ot; ot = align_up(ot + bytes[q], 256); }
-    int e = fp64 ? launch_adjoint_f64(sa, aa, ckpt, ck.data(), tape.data(), bytes, d_dw, d_dT, st)
-                 : launch_adjoint_f32(sa, aa, ckpt, ck.data(), tape.data(), bytes, d_dw, d_dT, st);
+      for (int q = 0; q < 7; ++q) { tape[(size_t)c * 7 + q] = base + ot; ot = align_up(ot + bytes[q], 256); }
+    if (h->profiling) cudaEventRecord(h->ev[4], st);
+    int e = fp64 ? launch_adjoint_f64(sa, aa, fam, ckpt, ck.data(), tape.data(), bytes, d_dw, d_dT, st)
+                 : launch_adjoint_f32(sa, aa, fam, ckpt, ck.data(), tape.data(), bytes, d_dw, d_dT, st);
     if (e) return cuda_fail(h, (cudaError_t)e);
+    if (h->profiling) { cudaEventRecord(h->ev[5], st); h->ran[2] = true; }
   }
   if (host) {
     TOP_CUDA(h, cudaMemcpyAsync(dwaypoints, d_dw, sizeof(double) * 3 * Jn, cudaMemcpyDeviceToHost, st));
@@ -1169,9 +1254,7 @@ int top_time_alloc(top_handle *h, const top_problem *pb_in, double k_T, double l
                    double *durations_io, top_result *res, void *stream) {
   if (!h || !pb_in || !durations_io) return TOP_E_INVAL;
   if (!(k_T >= 0.0) || !(lr > 0.0) || steps < 0) return TOP_E_INVAL;
-  if (pb_in->M_box || pb_in->M_ball || pb_in->M_vn || pb_in->M_gen || pb_in->M_poly || pb_in->adaptive_rho ||
-      pb_in->inner != TOP_CLOSED_FORM)
-    return TOP_E_NOTSUP;
+  if (pb_in->M_gen || pb_in->M_poly || pb_in->adaptive_rho || pb_in->inner != TOP_CLOSED_FORM) return TOP_E_NOTSUP;
   if (pb_in->B < 0 || pb_in->B > h->cfg.max_batch) return pb_in->B < 0 ? TOP_E_INVAL : TOP_E_NOMEM;
   const int B = pb_in->B;
   if (B == 0) return TOP_OK;
@@ -1197,7 +1280,9 @@ int top_time_alloc(top_handle *h, const top_problem *pb_in, double k_T, double l
   const size_t bS = align_up(sizeof(double) * (size_t)S + 8, 256), bB = align_up(sizeof(double) * B, 256);
   const size_t bW = align_up(sizeof(double) * 3 * Jn, 256), bOff = align_up(sizeof(int32_t) * (B + 1), 256);
   const size_t bSt = align_up(sizeof(double) * 12 * B, 256);
-  const size_t want = 2 * bS + bB + bW + (host ? bOff + bW + 2 * bSt : 0);
+  // the rows' parameters of a host problem: vbox [B], ball_c [S][3], ball_r [S], vnorm [B]
+  const size_t bRows = host ? 2 * bB + align_up(sizeof(double) * 3 * (size_t)S + 8, 256) + bS : 0;
+  const size_t want = 2 * bS + bB + bW + (host ? bOff + bW + 2 * bSt + bRows : 0);
   cudaError_t ge = grow((void **)&h->d_aux, &h->aux_bytes, want);
   if (ge != cudaSuccess) return ge == cudaErrorMemoryAllocation ? TOP_E_NOMEM : cuda_fail(h, ge);
   unsigned char *p = h->d_aux;
@@ -1216,6 +1301,26 @@ int top_time_alloc(top_handle *h, const top_problem *pb_in, double k_T, double l
     pbd.start_state = (const double *)p; p += bSt;
     TOP_CUDA(h, cudaMemcpyAsync(p, pb_in->end_state, sizeof(double) * 12 * B, cudaMemcpyHostToDevice, st));
     pbd.end_state = (const double *)p; p += bSt;
+    if (pb_in->M_box > 0) {
+      TOP_CUDA(h, cudaMemcpyAsync(p, pb_in->vbox, sizeof(double) * B, cudaMemcpyHostToDevice, st));
+      pbd.vbox = (const double *)p;
+    }
+    p += bB;
+    if (pb_in->M_vn > 0) {
+      TOP_CUDA(h, cudaMemcpyAsync(p, pb_in->vnorm, sizeof(double) * B, cudaMemcpyHostToDevice, st));
+      pbd.vnorm = (const double *)p;
+    }
+    p += bB;
+    if (pb_in->M_ball > 0) {
+      TOP_CUDA(h, cudaMemcpyAsync(p, pb_in->ball_c, sizeof(double) * 3 * S, cudaMemcpyHostToDevice, st));
+      pbd.ball_c = (const double *)p;
+    }
+    p += align_up(sizeof(double) * 3 * (size_t)S + 8, 256);
+    if (pb_in->M_ball > 0) {
+      TOP_CUDA(h, cudaMemcpyAsync(p, pb_in->ball_r, sizeof(double) * S, cudaMemcpyHostToDevice, st));
+      pbd.ball_r = (const double *)p;
+    }
+    p += bS;
   }
   if (S > 0)
     TOP_CUDA(h, cudaMemcpyAsync(dT_cur, durations_io, sizeof(double) * S,

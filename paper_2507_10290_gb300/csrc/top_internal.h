@@ -240,6 +240,8 @@ int launch_stream_f64(const StreamArgs &a, int fam, void *stream);
 struct AdjArgs {
   StreamArgs f;              // forward views (segment list, problem, G)
   const void *tz, *tuL, *tuRp, *tuR0;  // x^k from the tape
+  const void *tyb, *tqb, *tqv;         // x^k from the tape: box / ball / velocity-norm states ([rows][S])
+  void *ybb, *qbb, *qvb;               // their adjoints ([rows][S])
   void *zb, *uLb, *uRb;      // [21][Jn] adjoint of the junction state
   void *uR0b;                // [12][B]
   void *eSb, *eEb;           // [21][S] adjoint of the end derivatives
@@ -285,9 +287,12 @@ __host__ __device__ inline AdjResLayout adjres_layout(int C, int ntp, int rb) {
 }
 int launch_adjres_f32(const AdjResArgs &a, int nblocks, int C, size_t smem, void *stream);
 int launch_adjres_f64(const AdjResArgs &a, int nblocks, int C, size_t smem, void *stream);
-int launch_adjoint_f32(const StreamArgs &f, const AdjArgs &a, int ckpt, void *const *ck, void *const *tape,
+// the streaming adjoint; fam: FAM_BOX / FAM_BALL / FAM_VN bits (closed-form step);
+// ck[c * 7 + q], tape[l * 7 + q]: copies of the arrays (z, uL, uRp, uR0, ybox,
+// qball, qvn) of bytes[q] bytes (0 for an absent family)
+int launch_adjoint_f32(const StreamArgs &f, const AdjArgs &a, int fam, int ckpt, void *const *ck, void *const *tape,
                        const size_t *bytes, double *dw, double *dT, void *stream);
-int launch_adjoint_f64(const StreamArgs &f, const AdjArgs &a, int ckpt, void *const *ck, void *const *tape,
+int launch_adjoint_f64(const StreamArgs &f, const AdjArgs &a, int fam, int ckpt, void *const *ck, void *const *tape,
                        const size_t *bytes, double *dw, double *dT, void *stream);
 
 }  // namespace top
