@@ -570,7 +570,58 @@ def run_suite(args):
                                           w.start_state[b], w.end_state[b])
         return out
 
-    def gpu_case(name, w, precs=("fp32", "fp64"), extra=None, tol_eps=None, tol_cap=20000):
+    def handoff(w, o_solve, eps, cap, cev=10):
+        """Time to eps: FP32 until its residuals stop falling, then FP64 from the
+        FP32 state (top_resume), against FP64 alone; residuals every `cev`
+        iterations in both.  The switch point K1 is the iteration of the FP32
+        run's smallest residual (max of ||r_p||, ||r_d|| over N eps), read from
+        an untimed FP32 run with history."""
+        wt = w.with_(eps=eps, max_iters=cap)
+        s32 = top.Solver(max_batch=w.B, max_segments=w.S, precision="fp32", max_samples=16)
+        s64 = top.Solver(max_batch=w.B, max_segments=w.S, precision="fp64", max_samples=16)
+        t32, t64 = s32.device_inputs(w), s64.device_inputs(w)
+        h = s32.solve(wt, tensors=t32, history=True, check_every=cev)["history"].cpu().numpy()[:, 0, :]
+        tol = np.diff(w.seg_offset)[0] * eps
+        ratio = np.max(h, axis=1) / tol
+        ok = np.isfinite(ratio)
+        K1 = int(cev * (np.argmin(np.where(ok, ratio, np.inf)) // cev + 1)) if ok.any() else cap
+        st = torch.cuda.current_stream()
+
+        def timed(fn):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            r = fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            return r, e0.elapsed_time(e1)
+
+        s32.resume(wt, tensors=t32, max_iters=5)  # warm-up of both handles
+        s64.resume(wt, tensors=t64, max_iters=5, save=False)
+        (a, state), ms32 = timed(lambda: s32.resume(wt, tensors=t32, eps=eps, max_iters=K1, check_every=cev))
+        it32 = int(a["iters"][0])
+        done32 = int(a["status"][0]) == 0
+        ms64, it64, status = 0.0, 0, int(a["status"][0])
+        if not done32:
+            (b, _), ms64 = timed(lambda: s64.resume(wt, start=state, tensors=t64, eps=eps, max_iters=cap - it32,
+                                                    check_every=cev, save=False))
+            it64, status = int(b["iters"][0]), int(b["status"][0])
+        c, ms_alone = timed(lambda: s64.solve(wt, tensors=t64, eps=eps, max_iters=cap, check_every=cev))
+        res = {"eps": eps, "cap": cap, "check_every": cev, "switch_iteration": K1,
+               "fp32_ms": ms32, "fp32_iterations": it32, "fp64_ms": ms64, "fp64_iterations": it64,
+               "total_ms": ms32 + ms64, "status": status,
+               "fp64_alone_ms": ms_alone, "fp64_alone_iterations": int(c["iters"][0]),
+               "fp64_alone_status": int(c["status"][0])}
+        if w.S * it32 <= 400000:  # parity of the FP32 phase with the oracle at the switch point
+            o1 = o_solve(w.with_(max_iters=it32))
+            g = s32.solve(w, tensors=t32, max_iters=it32)
+            res["fp32_at_switch_coeff_rel_err_vs_oracle"] = scaled_err(g["coeffs"].cpu().numpy(), o1["coeffs"],
+                                                                        w.durations)
+        s32.close()
+        s64.close()
+        return res
+
+    def gpu_case(name, w, precs=("fp32", "fp64"), extra=None, tol_eps=None, tol_cap=20000, fp32_then_fp64=False):
         line = {"suite": name, "workload": w.name, "segments": int(w.S), "trajectories": int(w.B),
                 "iterations": int(w.max_iters)}
         o, odt = oracle_rate(w)
@@ -608,6 +659,8 @@ def run_suite(args):
                                          "status": out2["status"].cpu().numpy().tolist()}
             line[prec] = entry
             s.close()
+        if fp32_then_fp64 and tol_eps:
+            line["fp32_then_fp64"] = handoff(w, oracle.solve, tol_eps, tol_cap)
         if extra:
             line.update(extra(o))
         print(json.dumps(line), flush=True)
@@ -618,9 +671,9 @@ def run_suite(args):
         return only is None or name in only
 
     if want("single_box"):
-        gpu_case("single_box", W.single_box(), tol_eps=1e-4)
+        gpu_case("single_box", W.single_box(), tol_eps=1e-4, fp32_then_fp64=True)
     if want("corridor"):
-        gpu_case("corridor", W.corridor(), tol_eps=1e-4)
+        gpu_case("corridor", W.corridor(), tol_eps=1e-4, fp32_then_fp64=True)
     sub = W.batch().subset(list(range(64)))
     if want("batch"):
         gpu_case("batch (64-trajectory subset for the oracle)", sub, precs=("fp32", "fp64"))

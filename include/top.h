@@ -293,6 +293,49 @@ int64_t top_launch_count(const top_handle *h);
  * TOP_E_CUDA. */
 int top_solve_noalloc(const top_problem *pb, top_result *res, int precision, void *stream);
 
+/* Iteration state of a batch (an extension for warm starts and resumption;
+ * the paper has none), in the memory kind of the problem, FP64 whatever the
+ * handle's precision.  For junction j of trajectory b (row seg_offset[b] + b + j
+ * of the [S+B] arrays, as the waypoints) and derivative row (axis a, order r)
+ * at index a * 7 + r:
+ *   p  the consensus target z_j - u (Eq. 18b-c) that the local step of the
+ *      segment starting at j reads (its start side)
+ *   m  the target that the segment ending at j reads (its end side)
+ * At the trajectory's first junction m holds the fixed start state (orders
+ * < 4) and p the first segment's target; at its last junction p holds the
+ * fixed end state and m the last segment's target; rows of order >= 4 there
+ * are 0 (they are dropped from the consensus).  On free interior rows
+ * z = (p + m) / 2 and the two scaled duals are -(p - z) and -(m - z).
+ *   ybox   [S][6 M_box]   box rows in the compressed form y = A c - b + v of
+ *                         Eq. 18d-e (s = max(0, -y), v = max(0, y)), row
+ *                         order (sample, axis, sign)
+ *   qball  [S][M_ball][3] ball rows q = A c + w of Eq. 18f-g (phi = P(q), w = q - P(q))
+ *   qvn    [S][M_vn][3]   velocity-norm rows, likewise
+ *   iters  [B]            iterations run so far
+ * Pointers of absent families may be NULL. */
+typedef struct top_state {
+  double *p;
+  double *m;
+  double *ybox;
+  double *qball;
+  double *qvn;
+  int32_t *iters;
+} top_state;
+
+/* top_solve from a saved state instead of Init, and/or saving the state
+ * after the last iteration: `from` (may be NULL: Init) is read before the
+ * first iteration, `to` (may be NULL) written after the last; pb->max_iters
+ * more iterations run, and res->iters counts these.  A run of K1 iterations
+ * saved and resumed for K2 more gives the coefficients, costs and state of one
+ * run of K1 + K2 iterations bit for bit (the states are exact in FP64 for
+ * either precision; the stopping rule of Eq. 21 is applied per call), so a
+ * state saved by an FP32 handle can continue on an FP64 handle.  Fixed rho, the
+ * closed-form step with box / ball / velocity-norm rows, and trajectories that
+ * run resident or in a thread-block cluster (not the streaming form).
+ * Errors: as top_solve; TOP_E_NOTSUP outside that set. */
+int top_resume(top_handle *h, const top_problem *pb, const top_state *from, top_result *res, top_state *to,
+               void *stream);
+
 /* Free the workspace and the handle (NULL is a no-op). */
 void top_destroy(top_handle *h);
 

@@ -79,6 +79,9 @@ struct top_handle {
   int *h_ctraj = nullptr, *d_ctraj = nullptr;  // [max_batch]
   int csz_key_C = -1, csz_key_fam = -1, csz_val = 0;
   size_t csz_key_smem = 0;
+  // top_resume with host memory: device copies of the states (grow-only)
+  unsigned char *d_ws = nullptr;
+  size_t ws_bytes = 0;
   // capture-safe mode (top_set_layout): host copy of the batch layout
   int layout_B = 0;
   int32_t *layout_off = nullptr;  // [max_batch + 1]
@@ -383,6 +386,7 @@ void top_destroy(top_handle *h) {
   cudaFreeHost(h->h_ctraj);
   std::free(h->layout_off);
   cudaFree(h->d_ctraj);
+  cudaFree(h->d_ws);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
   cudaSetDevice(prev);
@@ -451,7 +455,14 @@ static bool index_fits(const top_problem *pb, int S) {
   return rows * (long long)S < (1LL << 31);
 }
 
-int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// top_solve and top_resume: `from` / `to` (may be null) are the state to start
+// from and to save, in the problem's memory kind
+int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, const top_state *from, top_state *to,
+               void *stream) {
   Range range("top_solve");
   int rc = validate(h, pb_in, res_in);
   if (rc != TOP_OK) return rc;
@@ -478,6 +489,18 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   if (S > h->cfg.max_segments) return TOP_E_NOMEM;
   if (S > 0 && (!pb_in->durations || !res_in->coeffs)) return TOP_E_INVAL;
   if (!index_fits(pb_in, S)) return TOP_E_LIMIT;
+  const bool resume = from || to;
+  if (resume) {
+    if (pb_in->adaptive_rho || pb_in->inner != TOP_CLOSED_FORM || pb_in->M_poly > 0 ||
+        h->cfg.schedule == TOP_SCHED_STREAM)
+      return TOP_E_NOTSUP;
+    for (const top_state *x : {from, (const top_state *)to}) {
+      if (!x) continue;
+      if (!x->p || !x->m || !x->iters || (pb_in->M_box && !x->ybox) || (pb_in->M_ball && !x->qball) ||
+          (pb_in->M_vn && !x->qvn))
+        return TOP_E_INVAL;
+    }
+  }
   // ---- device views of inputs and outputs ----
   top_problem pb = *pb_in;
   top_result res = *res_in;
@@ -627,6 +650,75 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     h->plan_valid = false;  // set once the device copies are enqueued
   }
   const int npack = h->plan_npack, max_nseg = h->plan_max_nseg, max_ntraj = h->plan_max_ntraj;
+  // a resumable run keeps its state resident or in clusters: every long
+  // trajectory must fit a cluster (the streaming form has no state export)
+  if (resume && h->plan_has_long) {
+    const int Mb = (fam & FAM_BOX) ? pb.M_box : 0, Mq = (fam & FAM_BALL) ? pb.M_ball : 0,
+              Mv = (fam & FAM_VN) ? pb.M_vn : 0;
+    const bool ok = h->cfg.schedule == TOP_SCHED_AUTO && cap > 0 && (fam & ~(FAM_BOX | FAM_BALL | FAM_VN)) == 0;
+    const int cc = ok ? cluster_capacity(h, &pb) : 0;
+    const int cm = cc > 0 ? cluster_max_size(cc, res_layout(cc, kClusterNtp, Mb, Mq, Mv, (int)rbytes(h)).total, fam, fp64)
+                          : 0;
+    for (int b = 0; b < B; ++b) {
+      const int nb = off[b + 1] - off[b];
+      if (nb > cap && !(cm >= 2 && (long long)nb <= (long long)cm * cc)) {
+        if (d_hist) cudaFree(d_hist);
+        return TOP_E_NOTSUP;
+      }
+    }
+  }
+  StateView fromv{}, tov{};
+  if (resume) {
+    const size_t np = sizeof(double) * 21 * (size_t)(S + B), nyb = sizeof(double) * 6 * pb.M_box * (size_t)S,
+                 nqb = sizeof(double) * 3 * pb.M_ball * (size_t)S, nqv = sizeof(double) * 3 * pb.M_vn * (size_t)S,
+                 nit = sizeof(int32_t) * B;
+    auto view = [&](const top_state *x, unsigned char *at) -> StateView {
+      StateView v{};
+      if (!host) {
+        v = StateView{x->p, x->m, x->ybox, x->qball, x->qvn, x->iters};
+      } else {
+        size_t o = 0;
+        auto take = [&](size_t n) { unsigned char *q = at + o; o = align_up(o + n, 256); return q; };
+        v.p = (double *)take(np);
+        v.m = (double *)take(np);
+        v.ybox = (double *)take(nyb);
+        v.qball = (double *)take(nqb);
+        v.qvn = (double *)take(nqv);
+        v.iters = (int32_t *)take(nit);
+      }
+      if (!pb.M_box) v.ybox = nullptr;
+      if (!pb.M_ball) v.qball = nullptr;
+      if (!pb.M_vn) v.qvn = nullptr;
+      return v;
+    };
+    const size_t one = 2 * align_up(np, 256) + align_up(nyb, 256) + align_up(nqb, 256) + align_up(nqv, 256) +
+                       align_up(nit, 256);
+    if (host) {
+      cudaError_t ge = grow((void **)&h->d_ws, &h->ws_bytes, 2 * one);
+      if (ge != cudaSuccess) {
+        if (d_hist) cudaFree(d_hist);
+        return ge == cudaErrorMemoryAllocation ? TOP_E_NOMEM : cuda_fail(h, ge);
+      }
+    }
+    if (from) {
+      fromv = view(from, h->d_ws);
+      if (host) {
+        TOP_CUDA(h, cudaMemcpyAsync(fromv.p, from->p, np, cudaMemcpyHostToDevice, st));
+        TOP_CUDA(h, cudaMemcpyAsync(fromv.m, from->m, np, cudaMemcpyHostToDevice, st));
+        if (fromv.ybox) TOP_CUDA(h, cudaMemcpyAsync(fromv.ybox, from->ybox, nyb, cudaMemcpyHostToDevice, st));
+        if (fromv.qball) TOP_CUDA(h, cudaMemcpyAsync(fromv.qball, from->qball, nqb, cudaMemcpyHostToDevice, st));
+        if (fromv.qvn) TOP_CUDA(h, cudaMemcpyAsync(fromv.qvn, from->qvn, nqv, cudaMemcpyHostToDevice, st));
+        TOP_CUDA(h, cudaMemcpyAsync(fromv.iters, from->iters, nit, cudaMemcpyHostToDevice, st));
+      }
+    }
+    if (to) {
+      tov = view(to, h->d_ws + (host ? one : 0));
+      // junctions of empty trajectories and the boundary rows no segment writes start at zero
+      TOP_CUDA(h, cudaMemsetAsync(tov.p, 0, np, st));
+      TOP_CUDA(h, cudaMemsetAsync(tov.m, 0, np, st));
+      TOP_CUDA(h, cudaMemsetAsync(tov.iters, 0, nit, st));
+    }
+  }
   if (h->plan_has_long && npack > 0) {  // fork point for the cluster launches (after the precompute)
     if (!h->side) {
       TOP_CUDA(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
@@ -656,6 +748,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     ResidentArgs ra{};
     ra.p = dp; ra.r = dr; ra.G = h->G; ra.packs = h->d_packs; ra.traj_list = h->d_tlist; ra.ntp = ntp;
     ra.E = adapt ? h->E : nullptr;
+    ra.from = fromv; ra.to = tov;
     Range r1("resident packs");
     if (h->profiling) cudaEventRecord(h->ev[2], st);
     int e = fp64 ? launch_resident_f64(ra, npack, C, L.total, fam, st)
@@ -702,6 +795,7 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     DevResult drc = dr;
     ClusterArgs ca{};
     ca.p = dp; ca.r = drc; ca.G = h->G; ca.E = adapt ? h->E : nullptr; ca.traj = h->d_ctraj;
+    ca.from = fromv; ca.to = tov;
     ca.poly = pdata;
     if (poly) {
       const size_t want = rbytes(h) * (size_t)dp.F_poly * dp.M_poly * (size_t)S + 256;
@@ -830,6 +924,15 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
     if (h->profiling) { cudaEventRecord(h->ev[5], st); h->ran[2] = true; }
   }
   // ---- outputs back to the host, error flags ----
+  if (host && to) {
+    const size_t np = sizeof(double) * 21 * (size_t)(S + B);
+    TOP_CUDA(h, cudaMemcpyAsync(to->p, tov.p, np, cudaMemcpyDeviceToHost, st));
+    TOP_CUDA(h, cudaMemcpyAsync(to->m, tov.m, np, cudaMemcpyDeviceToHost, st));
+    if (tov.ybox) TOP_CUDA(h, cudaMemcpyAsync(to->ybox, tov.ybox, sizeof(double) * 6 * pb.M_box * (size_t)S, cudaMemcpyDeviceToHost, st));
+    if (tov.qball) TOP_CUDA(h, cudaMemcpyAsync(to->qball, tov.qball, sizeof(double) * 3 * pb.M_ball * (size_t)S, cudaMemcpyDeviceToHost, st));
+    if (tov.qvn) TOP_CUDA(h, cudaMemcpyAsync(to->qvn, tov.qvn, sizeof(double) * 3 * pb.M_vn * (size_t)S, cudaMemcpyDeviceToHost, st));
+    TOP_CUDA(h, cudaMemcpyAsync(to->iters, tov.iters, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
+  }
   if (host) {
     TOP_CUDA(h, cudaMemcpyAsync(res_in->coeffs, res.coeffs, sizeof(double) * 24 * S, cudaMemcpyDeviceToHost, st));
     TOP_CUDA(h, cudaMemcpyAsync(res_in->cost, res.cost, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
@@ -850,6 +953,19 @@ int top_solve(top_handle *h, const top_problem *pb_in, top_result *res_in, void 
   if (*h->h_err & 1) return TOP_E_INVAL;
   if (*h->h_err & 2) return TOP_E_NUMERIC;
   return TOP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int top_solve(top_handle *h, const top_problem *pb, top_result *res, void *stream) {
+  return solve_impl(h, pb, res, nullptr, nullptr, stream);
+}
+
+int top_resume(top_handle *h, const top_problem *pb, const top_state *from, top_result *res, top_state *to,
+               void *stream) {
+  return solve_impl(h, pb, res, from, to, stream);
 }
 
 int top_set_layout(top_handle *h, int32_t B, const int32_t *host_seg_offset) {

@@ -157,6 +157,20 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
           mS[row] = z0;
         }
       }
+    if (A.from.p) {  // resume (top_resume): the exported targets and row states replace Init
+      const size_t oE = (size_t)(g + b + 1) * NJ, oS = (size_t)(g + b) * NJ;
+      for (int q = 0; q < NJ; ++q) {
+        pE[q] = R(A.from.p[oE + q]);
+        mE[q] = R(A.from.m[oE + q]);
+        if (first) {
+          pS[q] = R(A.from.p[oS + q]);
+          mS[q] = R(A.from.m[oS + q]);
+        }
+      }
+      if (BOX) for (int q = 0; q < 6 * Mb; ++q) sybox[q * C + l] = R(A.from.ybox[(size_t)g * 6 * Mb + q]);
+      if (BALL) for (int q = 0; q < 3 * Mq; ++q) sqball[q * C + l] = R(A.from.qball[(size_t)g * 3 * Mq + q]);
+      if (VN) for (int q = 0; q < 3 * Mv; ++q) sqvn[q * C + l] = R(A.from.qvn[(size_t)g * 3 * Mv + q]);
+    }
   } else {
 #pragma unroll
     for (int q = 0; q < NG; ++q) sc.G[q] = R(0);
@@ -164,6 +178,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
     for (int r = 0; r < NC; ++r) sc.s[r] = R(0);
   }
   cl.sync();
+  const int k0 = A.from.p ? A.from.iters[b] : 0;  // iterations run before a resume
   R fs[ND];  // r! T^-r
 #pragma unroll
   for (int r = 0; r < ND; ++r) fs[r] = R(fact(r)) * sc.s[r];
@@ -197,14 +212,14 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
       if (POLY) {
         const R *PN = (const R *)A.poly.N, *PH = (const R *)A.poly.H;
         R rhs[AX][NC];
-        family_rhs<R, F & 7, true>(sc, wS, wE, rho, k == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV,
+        family_rhs<R, F & 7, true>(sc, wS, wE, rho, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV,
                                    Mb, Mq, Mv, rhs);
         poly_rhs(PN, PH, (size_t)p.S, (size_t)g, Fp, Mp, rho, ypoly, p.S, tabP, rhs);
         poly_solve((const R *)A.poly.G, (const R *)A.poly.U, (size_t)p.S, (size_t)g, rhs, ch);
-        family_update<R, F & 7>(sc, k == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq, Mv, ch);
+        family_update<R, F & 7>(sc, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq, Mv, ch);
         poly_update(PN, PH, (size_t)p.S, (size_t)g, Fp, Mp, ypoly, p.S, tabP, ch);
       } else {
-        local_step<R, F, true>(sc, wS, wE, rho, k == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb,
+        local_step<R, F, true>(sc, wS, wE, rho, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb,
                                Mq, Mv, ch);
       }
       // ---- 2. publish start derivatives ----
@@ -378,6 +393,22 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
     }
   }
 
+  // ---- export of the state (top_resume) ----
+  if (A.to.p && valid) {
+    const size_t oE = (size_t)(g + b + 1) * NJ, oS = (size_t)(g + b) * NJ;
+    for (int q = 0; q < NJ; ++q) {
+      A.to.p[oE + q] = double(pE[q]);
+      A.to.m[oE + q] = double(mE[q]);
+      if (first) {
+        A.to.p[oS + q] = double(pS[q]);
+        A.to.m[oS + q] = double(mS[q]);
+      }
+    }
+    if (BOX) for (int q = 0; q < 6 * Mb; ++q) A.to.ybox[(size_t)g * 6 * Mb + q] = double(sybox[q * C + l]);
+    if (BALL) for (int q = 0; q < 3 * Mq; ++q) A.to.qball[(size_t)g * 3 * Mq + q] = double(sqball[q * C + l]);
+    if (VN) for (int q = 0; q < 3 * Mv; ++q) A.to.qvn[(size_t)g * 3 * Mv + q] = double(sqvn[q * C + l]);
+  }
+
   // ---- outputs: coefficients in the paper's basis, FP64 cost (cluster sum in rank order) ----
   double Ji = 0.0;
   if (valid) {
@@ -412,6 +443,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
       res.iters[b] = K;
       res.status[b] = 1;
     }
+    if (A.to.p) A.to.iters[b] = k0 + res.iters[b];
   }
   cl.sync();  // no CTA leaves while rank 0 reads its shared memory
 }

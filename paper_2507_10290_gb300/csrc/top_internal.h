@@ -64,9 +64,19 @@ struct PolyData {
   void *G, *U, *N, *H;
 };
 
+// Iteration state in the ABI's layout (top_state of top.h), device pointers:
+// p, m [S+B][3][7] consensus targets at every junction (start side, end side),
+// ybox [S][6 M_box], qball [S][M_ball][3], qvn [S][M_vn][3], iters [B].
+// p == nullptr: no state (Init of Algorithm 1 / no export).
+struct StateView {
+  double *p, *m, *ybox, *qball, *qvn;
+  int32_t *iters;
+};
+
 struct ResidentArgs {
   DevProblem p;
   DevResult r;
+  StateView from, to;   // resume from / export to (top_resume), or null views
   const void *G;        // [36][S] packed (D K D)^{-1}, element type = iteration type
   const void *E;        // [NE][S] adaptive-rho data (same type), or null
   const Pack *packs;
@@ -79,6 +89,7 @@ struct ResidentArgs {
 struct ClusterArgs {
   DevProblem p;
   DevResult r;
+  StateView from, to;   // resume from / export to (top_resume), or null views
   const void *G;        // [36][S], element type = iteration type (rewritten on a change of rho)
   const void *E;        // [NE][S] adaptive-rho data, or null
   const int *traj;      // [nclusters] trajectory ids

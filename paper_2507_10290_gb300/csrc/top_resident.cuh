@@ -179,6 +179,21 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
           mS[row] = z0;
         }
       }
+    if (A.from.p) {  // resume (top_resume): the exported targets and row states replace Init
+      const size_t oE = (size_t)(g + b + 1) * NJ, oS = (size_t)(g + b) * NJ;
+#pragma unroll
+      for (int q = 0; q < NJ; ++q) {
+        pE[q] = R(A.from.p[oE + q]);
+        mE[q] = R(A.from.m[oE + q]);
+        if (first) {
+          pS[q] = R(A.from.p[oS + q]);
+          mS[q] = R(A.from.m[oS + q]);
+        }
+      }
+      if (BOX) for (int q = 0; q < 6 * Mb; ++q) sybox[q * C + l] = R(A.from.ybox[(size_t)g * 6 * Mb + q]);
+      if (BALL) for (int q = 0; q < 3 * Mq; ++q) sqball[q * C + l] = R(A.from.qball[(size_t)g * 3 * Mq + q]);
+      if (VN) for (int q = 0; q < 3 * Mv; ++q) sqvn[q * C + l] = R(A.from.qvn[(size_t)g * 3 * Mv + q]);
+    }
   } else {
 #pragma unroll
     for (int q = 0; q < NG; ++q) sc.G[q] = R(0);
@@ -194,6 +209,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   const int cev = p.check_every > 0 ? p.check_every : 1;
   const bool periodic = p.eps > 0.0 || res.history != nullptr;
   R rho = rho0;  // this trajectory's rho (changes only with adaptive rho, step 5)
+  const int k0 = (A.from.p && valid) ? A.from.iters[b] : 0;  // iterations run before a resume
   for (int k = 0; k < K; ++k) {
     const bool check = adapt || (k == K - 1) || (periodic && ((k + 1) % cev == 0));
     const bool act = valid && !sdone[tb];
@@ -210,7 +226,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
           wS[a][r] = fs[r] * pS[a * ND + r];
           wE[a][r] = sc.s[r] * mE[a * ND + r];
         }
-      local_step<R, F, true>(sc, wS, wE, rho, k == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq,
+      local_step<R, F, true>(sc, wS, wE, rho, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq,
                        Mv, ch);
       // ---- 2. publish start derivatives ----
 #pragma unroll
@@ -378,6 +394,23 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
     }
   }
 
+  // ---- export of the state (top_resume) ----
+  if (A.to.p && valid) {
+    const size_t oE = (size_t)(g + b + 1) * NJ, oS = (size_t)(g + b) * NJ;
+#pragma unroll
+    for (int q = 0; q < NJ; ++q) {
+      A.to.p[oE + q] = double(pE[q]);
+      A.to.m[oE + q] = double(mE[q]);
+      if (first) {
+        A.to.p[oS + q] = double(pS[q]);
+        A.to.m[oS + q] = double(mS[q]);
+      }
+    }
+    if (BOX) for (int q = 0; q < 6 * Mb; ++q) A.to.ybox[(size_t)g * 6 * Mb + q] = double(sybox[q * C + l]);
+    if (BALL) for (int q = 0; q < 3 * Mq; ++q) A.to.qball[(size_t)g * 3 * Mq + q] = double(sqball[q * C + l]);
+    if (VN) for (int q = 0; q < 3 * Mv; ++q) A.to.qvn[(size_t)g * 3 * Mv + q] = double(sqvn[q * C + l]);
+  }
+
   // ---- outputs: coefficients in the paper's basis, FP64 cost per trajectory ----
   double Ji = 0.0;
   if (valid) {
@@ -419,6 +452,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
           res.iters[bb] = K;
           res.status[bb] = 1;
         }
+        if (A.to.p) A.to.iters[bb] = (A.from.p ? A.from.iters[bb] : 0) + res.iters[bb];
       }
     }
   }

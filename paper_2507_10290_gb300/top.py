@@ -83,10 +83,18 @@ class top_result(C.Structure):
                 ("history", C.c_void_p), ("rho", C.c_void_p)]
 
 
+class top_state(C.Structure):
+    _fields_ = [("p", C.c_void_p), ("m", C.c_void_p), ("ybox", C.c_void_p), ("qball", C.c_void_p),
+                ("qvn", C.c_void_p), ("iters", C.c_void_p)]
+
+
 _lib.top_create.argtypes = [C.POINTER(top_config), C.POINTER(C.c_void_p)]
 _lib.top_create.restype = C.c_int
 _lib.top_solve.argtypes = [C.c_void_p, C.POINTER(top_problem), C.POINTER(top_result), C.c_void_p]
 _lib.top_solve.restype = C.c_int
+_lib.top_resume.argtypes = [C.c_void_p, C.POINTER(top_problem), C.POINTER(top_state), C.POINTER(top_result),
+                            C.POINTER(top_state), C.c_void_p]
+_lib.top_resume.restype = C.c_int
 _lib.top_grad.argtypes = [C.c_void_p, C.POINTER(top_problem), C.c_void_p, C.c_void_p, C.c_void_p,
                           C.c_void_p]
 _lib.top_grad.restype = C.c_int
@@ -128,6 +136,12 @@ def top_create(cfg: top_config):
 
 def top_solve(handle, problem: top_problem, result: top_result, stream: int = 0) -> int:
     return _lib.top_solve(handle, C.byref(problem), C.byref(result), C.c_void_p(stream))
+
+
+def top_resume(handle, problem: top_problem, start, result: top_result, save, stream: int = 0) -> int:
+    """int top_resume(h, pb, from, res, to, stream); start / save: top_state or None"""
+    return _lib.top_resume(handle, C.byref(problem), None if start is None else C.byref(start), C.byref(result),
+                           None if save is None else C.byref(save), C.c_void_p(stream))
 
 
 def top_grad(handle, problem: top_problem, dJ: int, dwaypoints: int, ddurations: int, stream: int = 0) -> int:
@@ -330,6 +344,48 @@ class Solver:
             x = out.get(k)
             setattr(r, k, None if x is None else (x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()))
         return r
+
+    def alloc_state(self, w, device="cuda"):
+        """Buffers for an iteration state (top_state) of this workload's layout."""
+        torch = self.torch
+        B = int(np.asarray(w.seg_offset).shape[0] - 1)
+        S = int(np.asarray(w.seg_offset)[-1])
+        z = lambda *shape: torch.zeros(shape, dtype=torch.float64, device=device)  # noqa: E731
+        st = {"p": z(S + B, 3, 7), "m": z(S + B, 3, 7), "iters": torch.zeros(B, dtype=torch.int32, device=device)}
+        if getattr(w, "M_box", 0):
+            st["ybox"] = z(S, 6 * w.M_box)
+        if getattr(w, "M_ball", 0):
+            st["qball"] = z(S, w.M_ball, 3)
+        if getattr(w, "M_vn", 0):
+            st["qvn"] = z(S, w.M_vn, 3)
+        return st
+
+    @staticmethod
+    def state_struct(st):
+        if st is None:
+            return None
+        x = top_state()
+        for k in ("p", "m", "ybox", "qball", "qvn", "iters"):
+            v = st.get(k)
+            setattr(x, k, None if v is None else (v.ctypes.data if isinstance(v, np.ndarray) else v.data_ptr()))
+        return x
+
+    def resume(self, w, start=None, save=True, max_iters=None, eps=None, check_every: int = 1, stream=None,
+               tensors=None, out=None):
+        """top_resume: solve from the state `start` (None: Init) and return (outputs, saved state or None)."""
+        torch = self.torch
+        tensors = tensors if tensors is not None else self.device_inputs(w)
+        K = int(w.max_iters if max_iters is None else max_iters)
+        B = int(np.asarray(w.seg_offset).shape[0] - 1)
+        S = int(np.asarray(w.seg_offset)[-1])
+        out = out if out is not None else self.alloc_result(B, S, K)
+        saved = self.alloc_state(w) if save else None
+        pb = self.make_problem(w, tensors, TOP_MEM_DEVICE, max_iters=K, eps=eps, check_every=check_every)
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        rc = top_resume(self.handle, pb, self.state_struct(start), self.result_struct(out), self.state_struct(saved), s)
+        if rc != TOP_OK:
+            raise TopError(rc, "top_resume", top_last_cuda_error(self.handle))
+        return out, saved
 
     def solve(self, w, history: bool = False, max_iters=None, eps=None, check_every: int = 1, stream=None,
               tensors=None, out=None):

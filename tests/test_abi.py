@@ -47,6 +47,7 @@ def test_struct_layouts_match_the_header(top, tmp_path):
         "top_config": [f for f, _ in top.top_config._fields_],
         "top_problem": [f for f, _ in top.top_problem._fields_],
         "top_result": [f for f, _ in top.top_result._fields_],
+        "top_state": [f for f, _ in top.top_state._fields_],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for s, fs in fields.items():
@@ -60,7 +61,7 @@ def test_struct_layouts_match_the_header(top, tmp_path):
     got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
                                                          check=True).stdout.splitlines())
     for s, cls in (("top_config", top.top_config), ("top_problem", top.top_problem),
-                   ("top_result", top.top_result)):
+                   ("top_result", top.top_result), ("top_state", top.top_state)):
         assert int(got[f"{s} size"]) == C.sizeof(cls), s
         for f, _ in cls._fields_:
             assert int(got[f"{s}.{f}"]) == getattr(cls, f).offset, f"{s}.{f}"
