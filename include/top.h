@@ -57,6 +57,8 @@ extern "C" {
 #define TOP_E_LIMIT    -8  /* the problem exceeds the fixed scratch of top_solve_noalloc, or 32-bit
                                indexing of per-segment state (S x rows per segment >= 2^31, rows =
                                max(108, 6 M_box, 3 M_ball, 3 M_vn, 2 M_gen, F_poly M_poly)) */
+#define TOP_E_BOUNDS   -9  /* the bounds-checked build (libtop_checked.so, compiled with TOP_CHECKED)
+                               found an index outside its array; the access was skipped */
 
 /* fixed limits of top_solve_noalloc */
 #define TOP_NOALLOC_MAX_SEGMENTS 16384

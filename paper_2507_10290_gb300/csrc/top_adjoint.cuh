@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) adj_junction(const AdjArgs A) {
   R *eSb = (R *)A.eSb, *eEb = (R *)A.eEb;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < F.total; x += gridDim.x * blockDim.x) {
     int t, b, i, N, g;
-    stream_locate(F, x, t, b, i, N, g);
+    if (!stream_locate(F, x, t, b, i, N, g)) continue;
     const bool first = i == 0, last = i == N - 1;
     const int jE = g + b + 1;
     adj_fold<R>(A, b, g, first, last);
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(256) adj_segment(const AdjArgs A, int seed) {
   R *wbS = (R *)A.wbS, *wbE = (R *)A.wbE;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < F.total; x += gridDim.x * blockDim.x) {
     int t, b, i, N, g;
-    stream_locate(F, x, t, b, i, N, g);
+    if (!stream_locate(F, x, t, b, i, N, g)) continue;
     const bool first = i == 0, last = i == N - 1;
     const int jS = g + b, jE = g + b + 1;
     R G[NG], s[NC];
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) adj_segment_rows(const AdjArgs A, int see
   R *wbS = (R *)A.wbS, *wbE = (R *)A.wbE;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < Fw.total; x += gridDim.x * blockDim.x) {
     int t, b, i, N, g;
-    stream_locate(Fw, x, t, b, i, N, g);
+    if (!stream_locate(Fw, x, t, b, i, N, g)) continue;
     const bool first = i == 0, last = i == N - 1;
     const int jS = g + b, jE = g + b + 1;
     SegConst<R> sc;
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(256) adj_finish(const AdjArgs A, double *dwayp
   R *zb = (R *)A.zb;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < F.total; x += gridDim.x * blockDim.x) {
     int t, b, i, N, g;
-    stream_locate(F, x, t, b, i, N, g);
+    if (!stream_locate(F, x, t, b, i, N, g)) continue;
     const bool first = i == 0, last = i == N - 1;
     const int jS = g + b, jE = g + b + 1;
     adj_fold<R>(A, b, g, first, last);

@@ -83,12 +83,17 @@ __global__ void __launch_bounds__(256, 1) adjoint_resident_kernel(const AdjResAr
   R *tape = (R *)A.tape;
   const size_t state = (size_t)2 * NJ * Jn;  // one saved state: p and m of every slot
 
+  // (the pack descriptor is block-uniform: a bad one ends the whole block)
+  if (!TOP_IN_BOUNDS(p.err, pk.ntraj >= 1 && pk.ntraj <= ntp && pk.nseg >= 0 && pk.nseg <= C &&
+                                pk.tlist >= 0 && pk.tlist + pk.ntraj <= p.B))
+    return;
   for (int t = l; t < pk.ntraj; t += C) stid[t] = A.traj_list[pk.tlist + t];
   __syncthreads();
   if (l == 0) {
     int acc = 0;
     for (int t = 0; t < pk.ntraj; ++t) {
       soff[t] = acc;
+      if (!TOP_IN_BOUNDS(p.err, stid[t] >= 0 && stid[t] < p.B)) { acc = -1; break; }
       acc += p.seg_offset[stid[t] + 1] - p.seg_offset[stid[t]];
     }
     soff[pk.ntraj] = acc;
@@ -96,10 +101,11 @@ __global__ void __launch_bounds__(256, 1) adjoint_resident_kernel(const AdjResAr
   for (int q = l; q < NJ * J; q += C) { sp[q] = R(0); sm[q] = R(0); spb[q] = R(0); smb[q] = R(0); }
   for (int q = l; q < 3 * J; q += C) szP[q] = R(0);
   __syncthreads();
+  if (!TOP_IN_BOUNDS(p.err, soff[pk.ntraj] == pk.nseg)) return;
 
-  const bool valid = l < pk.nseg;
+  const bool inside = l < pk.nseg;
   int tb = 0;
-  if (valid) {
+  if (inside) {
     int lo = 0, hi = pk.ntraj - 1;
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
@@ -109,10 +115,11 @@ __global__ void __launch_bounds__(256, 1) adjoint_resident_kernel(const AdjResAr
   }
   const int i = l - soff[tb];
   const int Nb = soff[tb + 1] - soff[tb];
-  const bool first = valid && i == 0;
-  const bool last = valid && i == Nb - 1;
   const int b = stid[tb];
   const int g = p.seg_offset[b] + i;
+  const bool valid = inside && TOP_IN_BOUNDS(p.err, i >= 0 && i < Nb && g >= 0 && g < p.S);
+  const bool first = valid && i == 0;
+  const bool last = valid && i == Nb - 1;
   const int jS = l + tb, jE = l + tb + 1;
   const size_t gS = (size_t)g + b, gE = (size_t)g + b + 1;  // global slot indices (the waypoint rows)
   R *pS = sp + jS * NJ, *mS = sm + jS * NJ, *pE = sp + jE * NJ, *mE = sm + jE * NJ;

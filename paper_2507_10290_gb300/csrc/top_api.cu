@@ -326,6 +326,7 @@ const char *top_strerror(int code) {
     case TOP_E_STATE: return "call out of order";
     case TOP_E_NUMERIC: return "local KKT matrix not positive definite";
     case TOP_E_LIMIT: return "problem larger than the fixed scratch of top_solve_noalloc";
+    case TOP_E_BOUNDS: return "an index outside its array (bounds-checked build)";
     default: return "unknown error code";
   }
 }
@@ -551,7 +552,7 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
     }
   }
   DevProblem dp{};
-  dp.B = B; dp.S = S;
+  dp.B = B; dp.S = S; dp.err = h->d_err;
   dp.seg_offset = pb.seg_offset; dp.waypoints = pb.waypoints; dp.durations = pb.durations;
   dp.start_state = pb.start_state; dp.end_state = pb.end_state;
   dp.mode = pb.mode; dp.inner = pb.inner; dp.rho = pb.rho; dp.eps = pb.eps;
@@ -952,6 +953,7 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
   if (d_hist) cudaFree(d_hist);
   if (*h->h_err & 1) return TOP_E_INVAL;
   if (*h->h_err & 2) return TOP_E_NUMERIC;
+  if (*h->h_err & 4) return TOP_E_BOUNDS;
   return TOP_OK;
 }
 
@@ -997,6 +999,7 @@ int top_sync(top_handle *h, void *stream) {
   TOP_CUDA(h, cudaStreamSynchronize(st));
   if (*h->h_err & 1) return TOP_E_INVAL;
   if (*h->h_err & 2) return TOP_E_NUMERIC;
+  if (*h->h_err & 4) return TOP_E_BOUNDS;
   return TOP_OK;
 }
 
@@ -1113,7 +1116,7 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
     d_dT = (double *)(base + o_dT);
   }
   DevProblem dp{};
-  dp.B = B; dp.S = S;
+  dp.B = B; dp.S = S; dp.err = h->d_err;
   dp.seg_offset = pb.seg_offset; dp.waypoints = pb.waypoints; dp.durations = pb.durations;
   dp.start_state = pb.start_state; dp.end_state = pb.end_state;
   dp.mode = pb.mode; dp.inner = TOP_CLOSED_FORM; dp.rho = pb.rho; dp.eps = 0.0;
@@ -1238,6 +1241,7 @@ int top_grad(top_handle *h, const top_problem *pb_in, const double *dJ, double *
   TOP_CUDA(h, cudaStreamSynchronize(st));
   if (*h->h_err & 1) return TOP_E_INVAL;
   if (*h->h_err & 2) return TOP_E_NUMERIC;
+  if (*h->h_err & 4) return TOP_E_BOUNDS;
   return TOP_OK;
 }
 

@@ -50,8 +50,12 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
   const DevProblem &p = A.p;
   const DevResult &res = A.r;
   const int b = A.traj[blockIdx.x / csz];
+  // (cluster-uniform checks: a bad trajectory ends every CTA of the cluster
+  // before any of them touches another's shared memory)
+  if (!TOP_IN_BOUNDS(p.err, b >= 0 && b < p.B)) return;
   const int g0 = p.seg_offset[b];
   const int Nb = p.seg_offset[b + 1] - g0;
+  if (!TOP_IN_BOUNDS(p.err, Nb >= 0 && Nb <= csz * (int)blockDim.x && g0 >= 0 && g0 + Nb <= p.S)) return;
   const int C = blockDim.x;
   const int l = threadIdx.x;
   const int Mb = BOX ? p.M_box : 0, Mq = BALL ? p.M_ball : 0, Mv = VN ? p.M_vn : 0;

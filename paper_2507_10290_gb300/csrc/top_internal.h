@@ -39,7 +39,24 @@ struct DevProblem {
   int adaptive;   // residual balancing of rho (Eq. 22)
   double rho_mu, rho_incr, rho_decr;
   int M_poly, F_poly; const double *poly_n, *poly_h;  // polytope corridors
+  int *err;       // error word: 1 invalid input, 2 not positive definite, 4 bounds (checked build)
 };
+
+// Bounds checks of the checked build (TOP_CHECKED, libtop_checked.so): every
+// kernel checks the index bases it derives (pack, trajectory, segment, slot)
+// against the sizes of the arrays they address; every other access is a
+// compile-time-bounded offset from one of them.  A failed check sets bit 4 of
+// the error word and the thread skips its accesses (the host then returns
+// TOP_E_BOUNDS).  In the regular build the checks compile to nothing.
+#ifdef TOP_CHECKED
+__device__ __forceinline__ bool top_in_bounds(int *err, bool ok) {
+  if (!ok && err) atomicOr(err, 4);
+  return ok;
+}
+#define TOP_IN_BOUNDS(err, cond) top_in_bounds((err), (cond))
+#else
+#define TOP_IN_BOUNDS(err, cond) true
+#endif
 
 struct DevResult {
   double *coeffs, *cost, *r_primal, *r_dual, *history;

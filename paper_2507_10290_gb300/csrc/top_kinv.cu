@@ -215,8 +215,10 @@ __global__ void __launch_bounds__(128) kinv_kernel(const DevProblem p, double rh
                                                    const int *__restrict__ list) {
   const int S = p.S;
   const int n = list ? list[0] : S;
+  if (!TOP_IN_BOUNDS(p.err, n >= 0 && n <= S)) return;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
     const int g = list ? list[1 + x] : x;
+    if (!TOP_IN_BOUNDS(p.err, g >= 0 && g < S)) continue;
     bool first, last;
     double s[NC];
     if (!segment_setup(p, g, first, last, s)) {

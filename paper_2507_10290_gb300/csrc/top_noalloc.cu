@@ -160,7 +160,7 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
   int *d_list = (int *)(base + kListOff);
   int *d_err = (int *)(base + kErrOff);
   DevProblem dp{};
-  dp.B = B; dp.S = S;
+  dp.B = B; dp.S = S; dp.err = d_err;
   dp.seg_offset = pb->seg_offset; dp.waypoints = pb->waypoints; dp.durations = pb->durations;
   dp.start_state = pb->start_state; dp.end_state = pb->end_state;
   dp.mode = pb->mode; dp.inner = pb->inner; dp.rho = pb->rho; dp.eps = pb->eps;
@@ -202,5 +202,6 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
     return TOP_E_CUDA;
   if (herr & 1) return TOP_E_INVAL;
   if (herr & 2) return TOP_E_NUMERIC;
+  if (herr & 4) return TOP_E_BOUNDS;
   return TOP_OK;
 }

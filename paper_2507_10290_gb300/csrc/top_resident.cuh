@@ -89,12 +89,17 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   const bool pin = (p.mode == 0);
 
   // ---- set-up: the pack's trajectories, local offsets, tables, zeroed state ----
+  // (the pack descriptor is block-uniform: a bad one ends the whole block)
+  if (!TOP_IN_BOUNDS(p.err, pk.ntraj >= 1 && pk.ntraj <= ntp && pk.nseg >= 0 && pk.nseg <= C &&
+                                pk.tlist >= 0 && pk.tlist + pk.ntraj <= p.B))
+    return;
   for (int t = l; t < pk.ntraj; t += C) stid[t] = A.traj_list[pk.tlist + t];
   __syncthreads();
   if (l == 0) {
     int acc = 0;
     for (int t = 0; t < pk.ntraj; ++t) {
       soff[t] = acc;
+      if (!TOP_IN_BOUNDS(p.err, stid[t] >= 0 && stid[t] < p.B)) { acc = -1; break; }
       acc += p.seg_offset[stid[t] + 1] - p.seg_offset[stid[t]];
     }
     soff[pk.ntraj] = acc;
@@ -112,11 +117,13 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   if (BALL) fill_sample_table(tabQ, Mq, 0, l, C);
   if (VN) fill_sample_table(tabV, Mv, 1, l, C);
   __syncthreads();
+  // the trajectories' segments fill the pack exactly (else the whole block ends)
+  if (!TOP_IN_BOUNDS(p.err, soff[pk.ntraj] == pk.nseg)) return;
   for (int t = l; t < pk.ntraj; t += C) sdone[t] = (soff[t + 1] == soff[t]) ? 1 : 0;
 
-  const bool valid = l < pk.nseg;
+  const bool inside = l < pk.nseg;
   int tb = 0;
-  if (valid) {
+  if (inside) {
     int lo = 0, hi = pk.ntraj - 1;
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
@@ -126,10 +133,11 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   }
   const int i = l - soff[tb];
   const int Nb = soff[tb + 1] - soff[tb];
-  const bool first = valid && i == 0;
-  const bool last = valid && i == Nb - 1;
   const int b = stid[tb];
   const int g = p.seg_offset[b] + i;        // global segment
+  const bool valid = inside && TOP_IN_BOUNDS(p.err, i >= 0 && i < Nb && g >= 0 && g < p.S);
+  const bool first = valid && i == 0;
+  const bool last = valid && i == Nb - 1;
   const int jS = l + tb, jE = l + tb + 1;   // junction slots in shared memory
   R *pS = sp + jS * NJ, *mS = sm + tb * NJ;  // start slot (m only at a trajectory's start: [trajectory][21])
   R *pE = sp + jE * NJ;                      // end slot (owned by this thread)

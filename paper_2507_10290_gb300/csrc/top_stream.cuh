@@ -24,7 +24,9 @@
 
 namespace top {
 
-__device__ __forceinline__ void stream_locate(const StreamArgs &A, int x, int &t, int &b, int &i, int &N, int &g) {
+// false (checked build only) when the derived indices leave their arrays: the
+// caller then skips the segment
+__device__ __forceinline__ bool stream_locate(const StreamArgs &A, int x, int &t, int &b, int &i, int &N, int &g) {
   int lo = 0, hi = A.nl - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
@@ -32,9 +34,11 @@ __device__ __forceinline__ void stream_locate(const StreamArgs &A, int x, int &t
   }
   t = lo;
   b = A.lt_b[t];
+  if (!TOP_IN_BOUNDS(A.p.err, b >= 0 && b < A.p.B)) return false;
   i = x - A.lt_prefix[t];
   N = A.lt_prefix[t + 1] - A.lt_prefix[t];
   g = A.p.seg_offset[b] + i;
+  return TOP_IN_BOUNDS(A.p.err, i >= 0 && i < N && g >= 0 && g < A.S && g + b + 1 < A.Jn);
 }
 
 template <class R, int F>
@@ -45,7 +49,7 @@ __global__ void stream_init(const StreamArgs A) {
   R *ch = (R *)A.ch, *ybox = (R *)A.ybox, *qball = (R *)A.qball, *qvn = (R *)A.qvn;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
     int t, b, i, N, g;
-    stream_locate(A, x, t, b, i, N, g);
+    if (!stream_locate(A, x, t, b, i, N, g)) continue;
     const bool first = i == 0, last = i == N - 1;
     const int jS = g + b, jE = g + b + 1;
     for (int a = 0; a < AX; ++a)
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
   const bool pin = p.mode == 0;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
     int t, b, i, N, g;
-    stream_locate(A, x, t, b, i, N, g);
+    if (!stream_locate(A, x, t, b, i, N, g)) continue;
     if (A.done[t]) continue;
     const R rho = R(A.rho_t[t]);
     const bool first = i == 0, last = i == N - 1;
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(256) stream_numeric_warp(const StreamArgs A) {
   for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < n; item += nwarps) {
     const int x = A.work[item];
     int t, b, i, N, g;
-    stream_locate(A, x, t, b, i, N, g);
+    if (!stream_locate(A, x, t, b, i, N, g)) continue;
     const R rho = R(A.rho_t[t]);
     const bool first = i == 0, last = i == N - 1;
     const int jS = g + b, jE = g + b + 1;
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(256) stream_junction(const StreamArgs A, int c
   const bool pin = p.mode == 0;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
     int t, b, i, N, g;
-    stream_locate(A, x, t, b, i, N, g);
+    if (!stream_locate(A, x, t, b, i, N, g)) continue;
     if (A.done[t]) continue;
     const bool first = i == 0, last = i == N - 1;
     const int jS = g + b, jE = g + b + 1;
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(256) stream_dual(const StreamArgs A) {
   const R *dz = (const R *)A.dz;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
     int t, b, i, N, g;
-    stream_locate(A, x, t, b, i, N, g);
+    if (!stream_locate(A, x, t, b, i, N, g)) continue;
     if (A.done[t]) continue;
     const R rho = R(A.rho_t[t]);
     const bool first = i == 0, last = i == N - 1;
@@ -365,6 +369,7 @@ __global__ void __launch_bounds__(256) stream_reduce(const StreamArgs A, int k) 
   }
   const int b = A.lt_b[t];
   const int x0 = A.lt_prefix[t], x1 = A.lt_prefix[t + 1];
+  if (!TOP_IN_BOUNDS(A.p.err, b >= 0 && b < A.p.B && x0 >= 0 && x0 <= x1 && x1 <= A.total)) return;
   double a1 = 0.0, a2 = 0.0;
   for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) { a1 += A.rp2[x]; a2 += A.rd2[x]; }
   s1[threadIdx.x] = a1;
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(256) stream_rescale(const StreamArgs A) {
   const bool pin = p.mode == 0;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
     int t, b, i, N, g;
-    stream_locate(A, x, t, b, i, N, g);
+    if (!stream_locate(A, x, t, b, i, N, g)) continue;
     if (A.done[t] || A.fac_t[t] == 1.0) continue;
     const R f = R(A.fac_t[t]);
     const bool first = i == 0, last = i == N - 1;
@@ -450,7 +455,7 @@ __global__ void __launch_bounds__(256) stream_output(const StreamArgs A) {
   const R *chg = (const R *)A.ch;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
     int t, b, i, N, g;
-    stream_locate(A, x, t, b, i, N, g);
+    if (!stream_locate(A, x, t, b, i, N, g)) continue;
     const double T = p.durations[g];
     double sd[NC];
     sd[0] = 1.0;
@@ -474,6 +479,7 @@ __global__ void __launch_bounds__(256) stream_finish(const StreamArgs A, int K) 
   if (t >= A.nl) return;
   const int b = A.lt_b[t];
   const int x0 = A.lt_prefix[t], x1 = A.lt_prefix[t + 1];
+  if (!TOP_IN_BOUNDS(A.p.err, b >= 0 && b < A.p.B && x0 >= 0 && x0 <= x1 && x1 <= A.total)) return;
   double a1 = 0.0;
   for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) a1 += A.rp2[x];
   s1[threadIdx.x] = a1;

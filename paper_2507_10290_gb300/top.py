@@ -16,7 +16,10 @@ import re
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtop.so")
+# TOP_CHECKED=1 in the environment selects the bounds-checked build
+# (libtop_checked.so: index checks in every kernel, failures as TOP_E_BOUNDS)
+CHECKED = os.environ.get("TOP_CHECKED", "0") not in ("", "0")
+LIB_PATH = os.path.join(_HERE, "libtop_checked.so" if CHECKED else "libtop.so")
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "top.h")
 
 if not os.path.exists(LIB_PATH):
@@ -44,6 +47,7 @@ TOP_E_NOTSUP = _K["TOP_E_NOTSUP"]
 TOP_E_STATE = _K["TOP_E_STATE"]
 TOP_E_NUMERIC = _K["TOP_E_NUMERIC"]
 TOP_E_LIMIT = _K["TOP_E_LIMIT"]
+TOP_E_BOUNDS = _K["TOP_E_BOUNDS"]
 TOP_NOALLOC_MAX_SEGMENTS = _K["TOP_NOALLOC_MAX_SEGMENTS"]
 TOP_NOALLOC_MAX_BATCH = _K["TOP_NOALLOC_MAX_BATCH"]
 TOP_CONVERGED, TOP_NOT_CONVERGED, TOP_NONFINITE = 0, 1, 2

@@ -69,7 +69,7 @@ def test_struct_layouts_match_the_header(top, tmp_path):
 
 def test_error_strings_and_constants(top):
     for code in (top.TOP_OK, top.TOP_E_INVAL, top.TOP_E_NOMEM, top.TOP_E_CUDA, top.TOP_E_TIMEOUT,
-                 top.TOP_E_NOTSUP, top.TOP_E_STATE, top.TOP_E_NUMERIC):
+                 top.TOP_E_NOTSUP, top.TOP_E_STATE, top.TOP_E_NUMERIC, top.TOP_E_LIMIT, top.TOP_E_BOUNDS):
         s = top.top_strerror(code)
         assert s and s != "unknown error code"
     assert top.top_strerror(12345) == "unknown error code"
