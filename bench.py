@@ -622,6 +622,8 @@ def run_suite(args):
         return res
 
     def gpu_case(name, w, precs=("fp32", "fp64"), extra=None, tol_eps=None, tol_cap=20000, fp32_then_fp64=False):
+        if args.no_tolerance:  # fixed iteration counts only (e.g. for a profiler capture)
+            tol_eps = None
         line = {"suite": name, "workload": w.name, "segments": int(w.S), "trajectories": int(w.B),
                 "iterations": int(w.max_iters)}
         o, odt = oracle_rate(w)

@@ -105,6 +105,155 @@ __device__ __forceinline__ void end_derivs_f(const R (&ch)[NC], const R (&s)[NC]
   }
 }
 
+// ---- the same two maps through a Taylor shift (resident and cluster kernels) ----
+// With F(k,r) = r! C(k,r) the end derivatives are eE_r = r! s_r b_r, where
+// b_r = sum_{k>=r} C(k,r) ch_k are the coefficients of the same polynomial in
+// powers of (t/T - 1); synthetic division (a Taylor shift by one) forms b_0..b_7
+// with 28 additions.  The end-side part of the consensus right-hand side,
+// sum_{r<=min(k,6)} F(k,r) s_r w_r, is the transposed shift applied to
+// v_r = r! s_r w_r: the same 28 additions in reverse order.  Axes 0 and 1 run
+// as one packed pair (two FP32 lanes per instruction), axis 2 alone.
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 mk2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ double2 mk2(double x, double y) { return make_double2(x, y); }
+template <class R> struct Vec2;
+template <> struct Vec2<float> { using T = float2; };
+template <> struct Vec2<double> { using T = double2; };
+
+// a_r <- sum_{k>=r} C(k,r) a_k
+template <class V>
+__device__ __forceinline__ void taylor_shift(V (&a)[NC]) {
+#pragma unroll
+  for (int i = 0; i < NC - 1; ++i)
+#pragma unroll
+    for (int j = NC - 2; j >= i; --j) a[j] = vadd(a[j], a[j + 1]);
+}
+
+// v_k <- sum_{r<=k} C(k,r) v_r  (the transpose of taylor_shift)
+template <class V>
+__device__ __forceinline__ void taylor_shift_t(V (&v)[NC]) {
+#pragma unroll
+  for (int i = NC - 2; i >= 0; --i)
+#pragma unroll
+    for (int j = i; j <= NC - 2; ++j) v[j + 1] = vadd(v[j + 1], v[j]);
+}
+
+// eS_r = fs_r ch_r and eE_r = fs_r b_r for the three axes (fs_r = r! s_r)
+template <class R>
+__device__ __forceinline__ void end_derivs_shift(const R (&ch)[AX][NC], const R (&fs)[ND], R (&eS)[AX][ND],
+                                                 R (&eE)[AX][ND]) {
+  using V = typename Vec2<R>::T;
+  V p[NC];
+  R q[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    p[k] = mk2(ch[0][k], ch[1][k]);
+    q[k] = ch[2][k];
+  }
+  taylor_shift(p);
+  taylor_shift(q);
+#pragma unroll
+  for (int r = 0; r < ND; ++r) {
+    if (r == 0) {  // fs_0 = 1
+#pragma unroll
+      for (int a = 0; a < AX; ++a) eS[a][0] = ch[a][0];
+      eE[0][0] = p[0].x;
+      eE[1][0] = p[0].y;
+      eE[2][0] = q[0];
+      continue;
+    }
+    const V f2 = mk2(fs[r], fs[r]);
+    const V s01 = vmul(f2, mk2(ch[0][r], ch[1][r]));
+    const V e01 = vmul(f2, p[r]);
+    eS[0][r] = s01.x;
+    eS[1][r] = s01.y;
+    eS[2][r] = fs[r] * ch[2][r];
+    eE[0][r] = e01.x;
+    eE[1][r] = e01.y;
+    eE[2][r] = fs[r] * q[r];
+  }
+}
+
+// ch = G rhs for the three axes; axes 0 and 1 as one packed pair, each entry of G
+// applied to both lanes (the same sums in the same order as apply_g)
+template <class R>
+__device__ __forceinline__ void apply_g3(const R (&G)[NG], const R (&rhs)[AX][NC], R (&ch)[AX][NC]) {
+  using V = typename Vec2<R>::T;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const R g0 = G[gidx(k, 0)];
+    V acc = vmul(mk2(g0, g0), mk2(rhs[0][0], rhs[1][0]));
+    R a2 = g0 * rhs[2][0];
+#pragma unroll
+    for (int l = 1; l < NC; ++l) {
+      const R g = G[gidx(k, l)];
+      acc = vfma(mk2(g, g), mk2(rhs[0][l], rhs[1][l]), acc);
+      a2 += g * rhs[2][l];
+    }
+    ch[0][k] = acc.x;
+    ch[1][k] = acc.y;
+    ch[2][k] = a2;
+  }
+}
+
+// rhs_k = rho (wSf_k + sum_{r<=min(k,6)} C(k,r) vE_r) for the three axes, with
+// wSf_r = r! s_r (start-side target) and vE_r = r! s_r (end-side target)
+template <class R>
+__device__ __forceinline__ void consensus_rhs_shift(const R (&wSf)[AX][ND], const R (&vE)[AX][ND], R rho,
+                                                    R (&rhs)[AX][NC]) {
+  using V = typename Vec2<R>::T;
+  V t[NC];
+  R u[NC];
+#pragma unroll
+  for (int r = 0; r < ND; ++r) {
+    t[r] = mk2(vE[0][r], vE[1][r]);
+    u[r] = vE[2][r];
+  }
+  t[NC - 1] = mk2(R(0), R(0));
+  u[NC - 1] = R(0);
+  taylor_shift_t(t);
+  taylor_shift_t(u);
+  const V rr = mk2(rho, rho);
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    if (k < ND) {
+      t[k] = vadd(t[k], mk2(wSf[0][k], wSf[1][k]));
+      u[k] += wSf[2][k];
+    }
+    t[k] = vmul(rr, t[k]);
+    rhs[0][k] = t[k].x;
+    rhs[1][k] = t[k].y;
+    rhs[2][k] = rho * u[k];
+  }
+}
+
+// The junction update of a free row (Eq. 18b-c in the targets p = z + u_R,
+// m = z - u_L): u = (p - m)/2, p' = eE + u, m' = eS_next - u; two rows at once
+// (axes 0 and 1), each result rounded exactly as the scalar form rounds it.
+__device__ __forceinline__ void junction_pair(float ee0, float ee1, float en0, float en1, float &p0, float &p1,
+                                              float &m0, float &m1) {
+  const float2 u = __ffma2_rn(make_float2(-0.5f, -0.5f), make_float2(m0, m1),
+                              __fmul2_rn(make_float2(0.5f, 0.5f), make_float2(p0, p1)));
+  const float2 pn = __fadd2_rn(make_float2(ee0, ee1), u);
+  const float2 mn = __ffma2_rn(make_float2(-1.0f, -1.0f), u, make_float2(en0, en1));
+  p0 = pn.x; p1 = pn.y; m0 = mn.x; m1 = mn.y;
+}
+__device__ __forceinline__ void junction_pair(double ee0, double ee1, double en0, double en1, double &p0, double &p1,
+                                              double &m0, double &m1) {
+  const double u0 = 0.5 * (p0 - m0), u1 = 0.5 * (p1 - m1);
+  p0 = ee0 + u0; p1 = ee1 + u1;
+  m0 = en0 - u0; m1 = en1 - u1;
+}
+
 // ch = G rhs, G packed symmetric 8x8
 template <class R>
 __device__ __forceinline__ void apply_g(const R (&G)[NG], const R (&rhs)[NC], R (&ch)[NC]) {

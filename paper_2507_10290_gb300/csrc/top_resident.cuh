@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
 #pragma unroll
     for (int q = 0; q < NG; ++q) sc.G[q] = R(0);
 #pragma unroll
-    for (int r = 0; r < NC; ++r) sc.s[r] = R(0);
+    for (int r = 0; r < NC; ++r) sc.s[r] = R(r == 0);  // s_0 = 1 in every thread
   }
   __syncthreads();
   R fs[ND];  // r! T^-r
@@ -228,20 +228,44 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
       // ---- 1. local step (Eq. 18a, 18d-g) ----
       R wS[AX][ND], wE[AX][ND];
 #pragma unroll
-      for (int a = 0; a < AX; ++a)
+      for (int r = 0; r < ND; ++r) {
+        if (r == 0) {  // fs_0 = 1
 #pragma unroll
-        for (int r = 0; r < ND; ++r) {
-          wS[a][r] = fs[r] * pS[a * ND + r];
-          wE[a][r] = sc.s[r] * mE[a * ND + r];
+          for (int a = 0; a < AX; ++a) {
+            wS[a][0] = pS[a * ND];
+            wE[a][0] = mE[a * ND];
+          }
+          continue;
         }
+        using V = typename Vec2<R>::T;
+        const V f2 = mk2(fs[r], fs[r]);
+        const V s01 = vmul(f2, mk2(pS[r], pS[ND + r]));
+        const V e01 = vmul(f2, mk2(mE[r], mE[ND + r]));
+        wS[0][r] = s01.x;
+        wS[1][r] = s01.y;
+        wS[2][r] = fs[r] * pS[2 * ND + r];
+        wE[0][r] = e01.x;
+        wE[1][r] = e01.y;
+        wE[2][r] = fs[r] * mE[2 * ND + r];
+      }
       local_step<R, F, true>(sc, wS, wE, rho, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq,
                        Mv, ch);
       // ---- 2. publish start derivatives ----
+      end_derivs_shift(ch, fs, eSv, eE);
 #pragma unroll
-      for (int a = 0; a < AX; ++a) {
-        end_derivs_f(ch[a], sc.s, fs, eSv[a], eE[a]);
+      for (int a = 0; a < AX; ++a)
 #pragma unroll
         for (int r = 0; r < ND; ++r) seS[l * NJ + a * ND + r] = eSv[a][r];
+      // the start slot of a trajectory's first segment has no other reader: its
+      // dual update (Eq. 18c against the fixed start state) needs no barrier
+      if (first) {
+#pragma unroll
+        for (int a = 0; a < AX; ++a)
+#pragma unroll
+          for (int r = 0; r < PO; ++r) {
+            const int row = a * ND + r;
+            pS[row] += mS[row] - eSv[a][r];
+          }
       }
       // a check iteration may be a trajectory's last: keep its coefficients
       if (check) {
@@ -256,28 +280,38 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
     R rp2 = R(0);  // this segment's share of ||r_p||^2, formed on check iterations only
     if (act) {
       if (!last) {
+        if (check) {  // residual share and consensus change, from the values before the update
 #pragma unroll
-        for (int a = 0; a < AX; ++a) {
+          for (int a = 0; a < AX; ++a) {
 #pragma unroll
-          for (int r = 0; r < ND; ++r) {
-            const int row = a * ND + r;
-            const R ee = eE[a][r], en = eSnext[row];
-            const R pv = pE[row], mv = mE[row];
-            if (check) {
+            for (int r = 0; r < ND; ++r) {
+              const int row = a * ND + r;
+              const R ee = eE[a][r], en = eSnext[row];
               const R gap = ee - en;
               rp2 += gap * gap;
+              sdz[jE * NJ + row] = (pin && r == 0) ? R(0) : R(0.5) * ((ee + en) - (pE[row] + mE[row]));
             }
-            if (pin && r == 0) {
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < ND; ++r) {
+          if (pin && r == 0) {  // pinned position: z stays the waypoint
+#pragma unroll
+            for (int a = 0; a < AX; ++a) {
+              const int row = a * ND;
               const R P = szP[jE * 3 + a];
-              mE[row] = mv + (P - ee);
-              pE[row] = pv + (P - en);
-              if (check) sdz[jE * NJ + row] = R(0);
-            } else {
-              const R uL = R(0.5) * (pv - mv);
-              pE[row] = ee + uL;
-              mE[row] = en - uL;
-              if (check) sdz[jE * NJ + row] = R(0.5) * ((ee + en) - (pv + mv));
+              mE[row] = mE[row] + (P - eE[a][0]);
+              pE[row] = pE[row] + (P - eSnext[row]);
             }
+          } else {
+            R p0 = pE[r], p1 = pE[ND + r];
+            junction_pair(eE[0][r], eE[1][r], eSnext[r], eSnext[ND + r], p0, p1, mE[r], mE[ND + r]);
+            pE[r] = p0;
+            pE[ND + r] = p1;
+            const int row = 2 * ND + r;
+            const R u2 = R(0.5) * (pE[row] - mE[row]);
+            pE[row] = eE[2][r] + u2;
+            mE[row] = eSnext[row] - u2;
           }
         }
       } else {
@@ -287,15 +321,6 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
           for (int r = 0; r < PO; ++r) {
             const int row = a * ND + r;
             mE[row] += pE[row] - eE[a][r];
-          }
-      }
-      if (first) {
-#pragma unroll
-        for (int a = 0; a < AX; ++a)
-#pragma unroll
-          for (int r = 0; r < PO; ++r) {
-            const int row = a * ND + r;
-            pS[row] += mS[row] - eSv[a][r];
           }
       }
     }
@@ -427,15 +452,13 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
     for (int a = 0; a < AX; ++a)
 #pragma unroll
       for (int q = 0; q < NC; ++q) ch[a][q] = sch[(a * NC + q) * C + l];
-    const double T = p.durations[g];
-    double sd[NC];
-    sd[0] = 1.0;
-    for (int q = 1; q < NC; ++q) sd[q] = sd[q - 1] / T;
+    // c_k = ch_k T^-k with the iteration's own powers s_k (one rounding in the
+    // iteration precision; the FP64 pipe runs at 1/64 of the FP32 rate)
 #pragma unroll
     for (int a = 0; a < AX; ++a)
 #pragma unroll
-      for (int q = 0; q < NC; ++q) res.coeffs[((size_t)g * AX + a) * NC + q] = double(ch[a][q]) * sd[q];
-    Ji = segment_cost(ch, sd[7]);
+      for (int q = 0; q < NC; ++q) res.coeffs[((size_t)g * AX + a) * NC + q] = double(ch[a][q] * sc.s[q]);
+    Ji = segment_cost(ch, double(sc.s[7]));
   }
   red_rp[l] = Ji;
   __syncthreads();

@@ -45,7 +45,8 @@ __device__ __forceinline__ void fill_sample_table(R *tab, int M, int order, int 
 
 // The right-hand side of Eq. 18a for the consensus rows and the box / ball /
 // velocity-norm families (the first half of the local step).
-// FS: the start-side targets wS already carry the factor k! (see consensus_rhs_f)
+// FS: the targets wS and wE both carry the factor r! (wS = r! s_r p, wE = r! s_r m)
+// and the consensus rows go through the Taylor shift (consensus_rhs_shift)
 template <class R, int F, bool FS = false>
 __device__ __forceinline__ void family_rhs(const SegConst<R> &sc, const R (&wS)[AX][ND], const R (&wE)[AX][ND],
                                            R rho, bool first_iter, const R *ybox, const R *qball, const R *qvn,
@@ -54,12 +55,15 @@ __device__ __forceinline__ void family_rhs(const SegConst<R> &sc, const R (&wS)[
   constexpr bool BOX = (F & FAM_BOX) != 0;
   constexpr bool BALL = (F & FAM_BALL) != 0;
   constexpr bool VN = (F & FAM_VN) != 0;
+  if (FS) {
+    consensus_rhs_shift(wS, wE, rho, rhs);
+  } else {
 #pragma unroll
-  for (int a = 0; a < AX; ++a) {
+    for (int a = 0; a < AX; ++a) {
 #pragma unroll
-    for (int q = 0; q < NC; ++q) rhs[a][q] = R(0);
-    if (FS) consensus_rhs_f(wS[a], wE[a], rho, rhs[a]);
-    else consensus_rhs(wS[a], wE[a], rho, rhs[a]);
+      for (int q = 0; q < NC; ++q) rhs[a][q] = R(0);
+      consensus_rhs(wS[a], wE[a], rho, rhs[a]);
+    }
   }
   if (BOX) {
     for (int j = 0; j < Mb; ++j) {
@@ -180,8 +184,12 @@ __device__ __forceinline__ void local_step(const SegConst<R> &sc, const R (&wS)[
                                            R (&ch)[AX][NC]) {
   R rhs[AX][NC];
   family_rhs<R, F, FS>(sc, wS, wE, rho, first_iter, ybox, qball, qvn, stride, tabB, tabQ, tabV, Mb, Mq, Mv, rhs);
+  if (FS) {
+    apply_g3(sc.G, rhs, ch);
+  } else {
 #pragma unroll
-  for (int a = 0; a < AX; ++a) apply_g(sc.G, rhs[a], ch[a]);
+    for (int a = 0; a < AX; ++a) apply_g(sc.G, rhs[a], ch[a]);
+  }
   family_update<R, F>(sc, first_iter, ybox, qball, qvn, stride, tabB, tabQ, tabV, Mb, Mq, Mv, ch);
 }
 
