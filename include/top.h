@@ -75,6 +75,7 @@ enum top_inner     { TOP_CLOSED_FORM = 0, TOP_NUMERIC = 1 };
 enum top_memory    { TOP_MEM_DEVICE = 0, TOP_MEM_HOST = 1 };
 enum top_schedule  { TOP_SCHED_AUTO = 0, TOP_SCHED_RESIDENT = 1, TOP_SCHED_STREAM = 2 };
 enum top_numeric_form { TOP_NUMERIC_AUTO = 0, TOP_NUMERIC_WARP = 1, TOP_NUMERIC_THREAD = 2 };
+enum top_gemm_form { TOP_GEMM_CUDA_CORES = 0, TOP_GEMM_TENSOR = 1 };
 
 typedef struct top_handle top_handle;
 
@@ -99,7 +100,14 @@ typedef struct top_config {
                              TOP_NUMERIC_THREAD: one thread per segment, no extra launch;
                              TOP_NUMERIC_AUTO: WARP in FP64, THREAD in FP32.  Results agree within the
                              L-BFGS tolerance, not bit for bit. */
-  int32_t reserved[8];    /* must be zero */
+  int32_t gemm_form;      /* enum top_gemm_form, for the product (D K D)^-1 rhs of the closed-form local
+                             step (Eq. 18a) in the resident form: where all 32 segments of a warp share one
+                             inverse (interior segments of one trajectory with one duration, Sec. III-D.1)
+                             TOP_GEMM_TENSOR runs the warp's 96 products as mma.sync m16n8k8 TF32 tiles
+                             with the operands split into high and low TF32 parts (FP32 accuracy);
+                             TOP_FP32, no inequality rows and fixed rho only, elsewhere ignored.
+                             TOP_GEMM_CUDA_CORES (the default) keeps every product on the FP32 pipe. */
+  int32_t reserved[7];    /* must be zero */
 } top_config;
 
 /* One batch.  Pointers are device pointers for TOP_MEM_DEVICE and host
@@ -247,10 +255,14 @@ int top_sync(top_handle *h, void *stream);
  * batch at every capacity from 512 down to 128 in steps of 64 that fits the
  * shared memory (trajectories longer than the capacity run in clusters or
  * streaming), after one untimed solve each, and keeps the fastest in the
- * handle in place of top_config.segs_per_cta.  out_segs_per_cta (may be NULL)
- * gets the choice; ms (may be NULL) gets up to n_ms timings, in the order
- * 512, 448, ... (negative for a capacity that does not fit).  Results of the
- * trial solves are discarded.  Errors: as top_solve. */
+ * handle in place of top_config.segs_per_cta.  Where top_config.gemm_form
+ * applies (FP32, closed form, no inequality rows, fixed rho) it then times
+ * both gemm forms at the chosen capacity and keeps the faster in the handle.
+ * out_segs_per_cta (may be NULL) gets the capacity; ms (may be NULL) gets up
+ * to n_ms timings: entries 0..6 the capacities 512, 448, ..., 128 (negative
+ * for one that does not fit), entries 7 and 8 the CUDA-core and tensor-core
+ * forms at the chosen capacity (negative where the choice does not apply).
+ * Results of the trial solves are discarded.  Errors: as top_solve. */
 int top_autotune(top_handle *h, const top_problem *pb, int32_t iters, int32_t *out_segs_per_cta, float *ms,
                  int32_t n_ms, void *stream);
 

@@ -401,7 +401,8 @@ int top_create(const top_config *cfg, top_handle **out) {
   if (cfg->precision != TOP_FP32 && cfg->precision != TOP_FP64) return TOP_E_INVAL;
   if (cfg->schedule < TOP_SCHED_AUTO || cfg->schedule > TOP_SCHED_STREAM) return TOP_E_INVAL;
   if (cfg->numeric_form < TOP_NUMERIC_AUTO || cfg->numeric_form > TOP_NUMERIC_THREAD) return TOP_E_INVAL;
-  for (int q = 0; q < 8; ++q)
+  if (cfg->gemm_form != TOP_GEMM_CUDA_CORES && cfg->gemm_form != TOP_GEMM_TENSOR) return TOP_E_INVAL;
+  for (int q = 0; q < 7; ++q)
     if (cfg->reserved[q] != 0) return TOP_E_INVAL;
   top_handle *h = new (std::nothrow) top_handle;
   if (!h) return TOP_E_NOMEM;

@@ -57,12 +57,14 @@ TOP_CLOSED_FORM, TOP_NUMERIC = 0, 1
 TOP_MEM_DEVICE, TOP_MEM_HOST = 0, 1
 TOP_SCHED_AUTO, TOP_SCHED_RESIDENT, TOP_SCHED_STREAM = 0, 1, 2
 TOP_NUMERIC_AUTO, TOP_NUMERIC_WARP, TOP_NUMERIC_THREAD = 0, 1, 2
+TOP_GEMM_CUDA_CORES, TOP_GEMM_TENSOR = 0, 1
 
 
 class top_config(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_batch", C.c_int32), ("max_segments", C.c_int32),
                 ("max_samples", C.c_int32), ("schedule", C.c_int32), ("segs_per_cta", C.c_int32),
-                ("ckpt_interval", C.c_int32), ("numeric_form", C.c_int32), ("reserved", C.c_int32 * 8)]
+                ("ckpt_interval", C.c_int32), ("numeric_form", C.c_int32), ("gemm_form", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
 
 
 class top_problem(C.Structure):
@@ -245,7 +247,7 @@ class Solver:
 
     def __init__(self, max_batch: int, max_segments: int, precision: str = "fp32", max_samples: int = 16,
                  schedule: str = "auto", segs_per_cta: int = 0, ckpt_interval: int = 10,
-                 numeric_form: str = "auto"):
+                 numeric_form: str = "auto", gemm_form: str = "cuda_cores"):
         import torch  # device memory and streams only
         self.torch = torch
         cfg = top_config()
@@ -258,6 +260,7 @@ class Solver:
         cfg.ckpt_interval = int(ckpt_interval)
         cfg.numeric_form = {"auto": TOP_NUMERIC_AUTO, "warp": TOP_NUMERIC_WARP,
                             "thread": TOP_NUMERIC_THREAD}[numeric_form]
+        cfg.gemm_form = {"cuda_cores": TOP_GEMM_CUDA_CORES, "tensor": TOP_GEMM_TENSOR}[gemm_form]
         self.precision = precision
         rc, h = top_create(cfg)
         if rc != TOP_OK:
@@ -427,16 +430,21 @@ class Solver:
             raise TopError(rc, "top_grad", top_last_cuda_error(self.handle))
         return dw, dT
 
-    def autotune(self, w, iters: int = 20, tensors=None, stream=None):
-        """top_autotune on this batch: returns (segments per CTA chosen, {capacity: ms})."""
+    def autotune(self, w, iters: int = 20, tensors=None, stream=None, gemm=False):
+        """top_autotune on this batch: returns (segments per CTA chosen, {capacity: ms}); with
+        gemm=True also {"cuda_cores": ms, "tensor": ms} of the two gemm forms at that capacity
+        (negative where the choice does not apply)."""
         torch = self.torch
         tensors = tensors if tensors is not None else self.device_inputs(w)
         pb = self.make_problem(w, tensors, TOP_MEM_DEVICE)
         s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
-        rc, best, ms = top_autotune(self.handle, pb, iters, 7, s)
+        rc, best, ms = top_autotune(self.handle, pb, iters, 9, s)
         if rc != TOP_OK:
             raise TopError(rc, "top_autotune", top_last_cuda_error(self.handle))
-        return best, {512 - 64 * q: t for q, t in enumerate(ms)}
+        caps = {512 - 64 * q: t for q, t in enumerate(ms[:7])}
+        if gemm:
+            return best, caps, {"cuda_cores": ms[7], "tensor": ms[8]}
+        return best, caps
 
     def sample(self, w, coeffs, M: int, order: int = 0, tensors=None, stream=None):
         """Every trajectory of w with coefficients `coeffs` ([S,3,8] device tensor)
