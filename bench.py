@@ -707,9 +707,13 @@ def shared_duration_line(top):
     """The full 4096-trajectory batch with durations shared per trajectory
     against per-segment durations: the precompute reuses the first interior
     segment's inverse for every interior segment of the same duration."""
-    line = {"suite": "batch 4096, shared vs per-segment durations (FP32, 300 iterations)"}
-    for kind, w in (("per_segment_T", W.batch()), ("shared_T", W.batch(shared_T=True))):
-        s = top.Solver(max_batch=w.B, max_segments=w.S, precision="fp32")
+    line = {"suite": "batch 4096, shared vs per-segment durations (FP32, 300 iterations); shared_T_tensor: "
+                     "the G product of warps whose 32 segments share one inverse on the tensor cores "
+                     "(mma.sync m16n8k8, 3xTF32)"}
+    coeffs = {}
+    for kind, w, form in (("per_segment_T", W.batch(), "cuda_cores"), ("shared_T", W.batch(shared_T=True), "cuda_cores"),
+                          ("shared_T_tensor", W.batch(shared_T=True), "tensor")):
+        s = top.Solver(max_batch=w.B, max_segments=w.S, precision="fp32", gemm_form=form)
         tensors = s.device_inputs(w)
         out = s.alloc_result(w.B, w.S, w.max_iters)
         s.solve(w, tensors=tensors, out=out)
@@ -723,7 +727,15 @@ def shared_duration_line(top):
         line[kind] = {"segments": w.S, "ms": float(np.median(ms)), "precompute_ms": float(kt[0]),
                       "resident_ms": float(kt[1]), "cluster_ms": float(kt[3]),
                       "segment_iterations_per_s": w.S * w.max_iters / (float(np.median(ms)) / 1000)}
+        if kind.startswith("shared_T"):
+            coeffs[kind] = out["coeffs"].cpu().numpy()
+            if kind == "shared_T":
+                best, _, forms = s.autotune(w, iters=30, tensors=tensors, gemm=True)
+                line["autotune_30_iterations_ms"] = {"segs_per_cta": best, **forms}
         s.close()
+    sc = np.asarray(W.batch(shared_T=True).durations)[:, None, None] ** np.arange(8)[None, None, :]
+    a, b = coeffs["shared_T"] * sc, coeffs["shared_T_tensor"] * sc  # time-normalised coefficients
+    line["tensor_vs_cuda_cores_coeff_rel_diff"] = float(np.linalg.norm(b - a) / np.linalg.norm(a))
     print(json.dumps(line), flush=True)
 
 

@@ -746,9 +746,13 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
     const int ntp = std::max(1, max_ntraj);
     const int Mb = (fam & FAM_BOX) ? pb.M_box : 0, Mq = (fam & FAM_BALL) ? pb.M_ball : 0,
               Mv = (fam & FAM_VN) ? pb.M_vn : 0;
-    const ResLayout L = res_layout_resident(C, ntp, Mb, Mq, Mv, (int)rbytes(h));
+    // the tensor-core form of the G product (top_config.gemm_form) where it applies and fits
+    int tc = (h->cfg.gemm_form == TOP_GEMM_TENSOR && !fp64 && fam == 0 && !adapt) ? 1 : 0;
+    if (tc && res_layout_resident(C, ntp, Mb, Mq, Mv, (int)rbytes(h), true).total > (size_t)h->smem_optin) tc = 0;
+    const ResLayout L = res_layout_resident(C, ntp, Mb, Mq, Mv, (int)rbytes(h), tc != 0);
     ResidentArgs ra{};
     ra.p = dp; ra.r = dr; ra.G = h->G; ra.packs = h->d_packs; ra.traj_list = h->d_tlist; ra.ntp = ntp;
+    ra.tc = tc;
     ra.E = adapt ? h->E : nullptr;
     ra.from = fromv; ra.to = tov;
     Range r1("resident packs");
@@ -1306,6 +1310,28 @@ int top_autotune(top_handle *h, const top_problem *pb_in, int32_t iters, int32_t
   for (; ms && q < n_ms; ++q) ms[q] = -1.0f;
   h->cfg.segs_per_cta = (rc == TOP_OK && best_ms > 0.0f) ? best : saved;
   h->plan_valid = false;
+  // the two forms of the G product at the chosen capacity, where the choice applies
+  const bool gemm_applies = h->cfg.precision == TOP_FP32 && pb.inner == TOP_CLOSED_FORM && pb.M_box == 0 &&
+                            pb.M_ball == 0 && pb.M_vn == 0 && pb.M_gen == 0 && pb.M_poly == 0 && !pb.adaptive_rho;
+  float tg[2] = {-1.0f, -1.0f};
+  if (rc == TOP_OK && best_ms > 0.0f && gemm_applies) {
+    const int saved_form = h->cfg.gemm_form;
+    for (int f = 0; f < 2 && rc == TOP_OK; ++f) {
+      h->cfg.gemm_form = f == 0 ? TOP_GEMM_CUDA_CORES : TOP_GEMM_TENSOR;
+      rc = top_solve(h, &pb, &r, stream);  // untimed
+      if (rc == TOP_OK) {
+        cudaEventRecord(e0, st);
+        rc = top_solve(h, &pb, &r, stream);
+        cudaEventRecord(e1, st);
+        if (rc == TOP_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&tg[f], e0, e1);
+      }
+    }
+    h->cfg.gemm_form = (rc == TOP_OK && tg[0] > 0.0f && tg[1] > 0.0f)
+                           ? (tg[1] < tg[0] ? TOP_GEMM_TENSOR : TOP_GEMM_CUDA_CORES)
+                           : saved_form;
+  }
+  if (ms && n_ms > 7) ms[7] = tg[0];
+  if (ms && n_ms > 8) ms[8] = tg[1];
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (host) std::free(buf); else cudaFree(buf);

@@ -99,6 +99,7 @@ struct ResidentArgs {
   const Pack *packs;
   const int *traj_list; // trajectory ids, grouped by pack
   int ntp;              // trajectory slots per pack (shared-memory sizing)
+  int tc;               // 1: the G product of warps that share one inverse on the tensor cores
 };
 
 // Cluster-resident form (top_cluster.cuh): one trajectory per thread-block
@@ -130,9 +131,11 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 // mreg (the resident kernel): the end-side targets of a segment's end slot
 // live in its thread's registers, so m holds only the start slots of the
 // pack's trajectories ([trajectory][21]); the coefficients of check
-// iterations are kept in ch ([24][C]) for the output.
+// iterations are kept in ch ([24][C]) for the output; with tc (the tensor-core
+// form of the G product) ch is [C][28], one row per segment, and doubles as
+// the warps' operand scratch.
 __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, int Mv, int rb, int Mp = 0,
-                                                bool mreg = false) {
+                                                bool mreg = false, bool tc = false) {
   ResLayout L{};
   const size_t J = size_t(C) + size_t(ntp);
   size_t o = 0;
@@ -153,7 +156,7 @@ __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, 
   L.tabQ = o;   o += size_t(rb) * 8 * Mq;
   L.tabV = o;   o += size_t(rb) * 8 * Mv;
   L.tabP = o;   o += size_t(rb) * 8 * Mp;  // polytope sample rows (cluster form)
-  L.ch = o;     o += mreg ? size_t(rb) * 24 * C : 0;
+  L.ch = o;     o += mreg ? size_t(rb) * (tc ? 28 : 24) * C : 0;
   o = align_up(o, 16);
   L.off = o;    o += sizeof(int) * (ntp + 1);
   L.done = o;   o += sizeof(int) * ntp;
@@ -167,8 +170,9 @@ __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, 
 }
 
 // the layout of the resident kernel (top_resident.cuh)
-__host__ __device__ inline ResLayout res_layout_resident(int C, int ntp, int Mb, int Mq, int Mv, int rb) {
-  return res_layout(C, ntp, Mb, Mq, Mv, rb, 0, true);
+__host__ __device__ inline ResLayout res_layout_resident(int C, int ntp, int Mb, int Mq, int Mv, int rb,
+                                                         bool tc = false) {
+  return res_layout(C, ntp, Mb, Mq, Mv, rb, 0, true, tc);
 }
 
 // Streaming form (trajectories longer than a resident CTA): state in global

@@ -40,11 +40,14 @@
 #include "top_internal.h"
 #include "top_math.cuh"
 #include "top_step.cuh"
+#include "top_tc.cuh"
 
 namespace top {
 
 // FP64 state needs twice the registers: 256 threads per CTA (255 registers each) in FP64
-template <class R, int F, bool ADAPT>
+// TC: the G product of a warp whose 32 segments share one inverse runs on the
+// tensor cores (top_tc.cuh); FP32, no inequality rows, fixed rho only.
+template <class R, int F, bool ADAPT, bool TC = false>
 __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel(const ResidentArgs A) {
   constexpr bool BOX = (F & FAM_BOX) != 0;
   constexpr bool BALL = (F & FAM_BALL) != 0;
@@ -58,7 +61,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   const int ntp = A.ntp;
   const int J = C + ntp;
   const int Mb = BOX ? p.M_box : 0, Mq = BALL ? p.M_ball : 0, Mv = VN ? p.M_vn : 0;
-  const ResLayout L = res_layout_resident(C, ntp, Mb, Mq, Mv, (int)sizeof(R));
+  const ResLayout L = res_layout_resident(C, ntp, Mb, Mq, Mv, (int)sizeof(R), TC);
   double *red_rp = (double *)(smem + L.red_rp);  // FP64 cost shares (epilogue)
   R *sh_rp = (R *)(smem + L.red_rp);              // residual shares (check iterations)
   R *sh_rd = (R *)(smem + L.red_rd);
@@ -75,7 +78,9 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   R *tabB = (R *)(smem + L.tabB);
   R *tabQ = (R *)(smem + L.tabQ);
   R *tabV = (R *)(smem + L.tabV);
-  R *sch = (R *)(smem + L.ch);  // [24][C] coefficients of the last check iteration (the output)
+  R *sch = (R *)(smem + L.ch);  // coefficients of the last check iteration (the output)
+  // element q of segment l's coefficients in ch: [24][C], or [C][28] with TC
+  auto chx = [C](int q, int seg) { return TC ? seg * kTcRow + q : q * C + seg; };
   int *soff = (int *)(smem + L.off);
   int *sdone = (int *)(smem + L.done);
   int *stid = (int *)(smem + L.tid);
@@ -209,6 +214,19 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
     for (int r = 0; r < NC; ++r) sc.s[r] = R(r == 0);  // s_0 = 1 in every thread
   }
   __syncthreads();
+  // tensor-core form: does this warp's every segment hold the same inverse?
+  bool wtc = false;
+  TcA tca{};
+  if constexpr (TC) {
+    bool same = valid;
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+      const R g0 = __shfl_sync(0xffffffffu, sc.G[q], 0);
+      same = same && (sc.G[q] == g0);
+    }
+    wtc = __all_sync(0xffffffffu, same);
+    if (wtc) tca = tc_a_fragments((const float *)A.G + g, (size_t)p.S, l & 31);
+  }
   R fs[ND];  // r! T^-r
 #pragma unroll
   for (int r = 0; r < ND; ++r) fs[r] = R(fact(r)) * sc.s[r];
@@ -221,6 +239,8 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   for (int k = 0; k < K; ++k) {
     const bool check = adapt || (k == K - 1) || (periodic && ((k + 1) % cev == 0));
     const bool act = valid && !sdone[tb];
+    bool tcw = false;  // the whole warp takes the tensor-core product this iteration
+    if constexpr (TC) tcw = wtc && __all_sync(0xffffffffu, act);
     R eE[AX][ND];
     R eSv[AX][ND];
     if (act) {
@@ -248,8 +268,16 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
         wE[1][r] = e01.y;
         wE[2][r] = fs[r] * mE[2 * ND + r];
       }
-      local_step<R, F, true>(sc, wS, wE, rho, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq,
-                       Mv, ch);
+      if constexpr (TC) {
+        R rhs[AX][NC];
+        family_rhs<R, F, true>(sc, wS, wE, rho, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV,
+                               Mb, Mq, Mv, rhs);
+        if (tcw) apply_g_mma(tca, rhs, ch, sch + (l & ~31) * kTcRow, l & 31);
+        else apply_g3(sc.G, rhs, ch);
+      } else {
+        local_step<R, F, true>(sc, wS, wE, rho, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb,
+                               Mq, Mv, ch);
+      }
       // ---- 2. publish start derivatives ----
       end_derivs_shift(ch, fs, eSv, eE);
 #pragma unroll
@@ -272,7 +300,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
 #pragma unroll
         for (int a = 0; a < AX; ++a)
 #pragma unroll
-          for (int q = 0; q < NC; ++q) sch[(a * NC + q) * C + l] = ch[a][q];
+          for (int q = 0; q < NC; ++q) sch[chx(a * NC + q, l)] = ch[a][q];
       }
     }
     __syncthreads();
@@ -451,7 +479,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
 #pragma unroll
     for (int a = 0; a < AX; ++a)
 #pragma unroll
-      for (int q = 0; q < NC; ++q) ch[a][q] = sch[(a * NC + q) * C + l];
+      for (int q = 0; q < NC; ++q) ch[a][q] = sch[chx(a * NC + q, l)];
     // c_k = ch_k T^-k with the iteration's own powers s_k (one rounding in the
     // iteration precision; the FP64 pipe runs at 1/64 of the FP32 rate)
 #pragma unroll
@@ -493,6 +521,15 @@ template <class R>
 int launch_resident_t(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const bool adapt = a.p.adaptive != 0 && a.E != nullptr;
+  if constexpr (sizeof(R) == 4) {
+    if (a.tc && fam == 0 && !adapt) {
+      auto kern = resident_kernel<R, 0, false, true>;
+      cudaError_t e = func_attr_once((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return (int)e;
+      kern<<<nblocks, C, smem, st>>>(a);
+      return (int)cudaGetLastError();
+    }
+  }
 #define TOP_RES_CASE(FV)                                                                               \
   case FV: {                                                                                           \
     auto kern = adapt ? resident_kernel<R, FV, true> : resident_kernel<R, FV, false>;                  \
