@@ -77,8 +77,8 @@ struct top_handle {
   // cluster-resident form: trajectory lists (pinned host, device) and the cached
   // largest co-schedulable cluster size for (C, family, precision)
   int *h_ctraj = nullptr, *d_ctraj = nullptr;  // [max_batch]
-  int csz_key_C = -1, csz_key_fam = -1, csz_val = 0;
-  size_t csz_key_smem = 0;
+  int csz_key_C[3] = {-1, -1, -1}, csz_key_fam[3] = {-1, -1, -1}, csz_val[3] = {0, 0, 0};  // per lanes group
+  size_t csz_key_smem[3] = {0, 0, 0};
   // top_resume with host memory: device copies of the states (grow-only)
   unsigned char *d_ws = nullptr;
   size_t ws_bytes = 0;
@@ -659,8 +659,8 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
               Mv = (fam & FAM_VN) ? pb.M_vn : 0;
     const bool ok = h->cfg.schedule == TOP_SCHED_AUTO && cap > 0 && (fam & ~(FAM_BOX | FAM_BALL | FAM_VN)) == 0;
     const int cc = ok ? cluster_capacity(h, &pb) : 0;
-    const int cm = cc > 0 ? cluster_max_size(cc, res_layout(cc, kClusterNtp, Mb, Mq, Mv, (int)rbytes(h)).total, fam, fp64)
-                          : 0;
+    const int cm =
+        cc > 0 ? cluster_max_size(cc, 1, res_layout(cc, kClusterNtp, Mb, Mq, Mv, (int)rbytes(h)).total, fam, fp64) : 0;
     for (int b = 0; b < B; ++b) {
       const int nb = off[b + 1] - off[b];
       if (nb > cap && !(cm >= 2 && (long long)nb <= (long long)cm * cc)) {
@@ -768,36 +768,49 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
   // adaptive rho)
   // polytope trajectories of any length use the cluster form (a cluster of one CTA
   // for short ones): the resident packs have no room for their per-axis inverses
-  int ccap = 0, cmax = 0;
-  size_t csmem = 0;
+  // cluster groups: lanes per segment, segments per CTA, shared memory, largest cluster.  With
+  // sample rows (FP32, fixed rho) a segment's rows are split over 4 or 2 lanes where the
+  // trajectory fits a cluster of such CTAs; the rest run one lane per segment.
+  struct CGroup { int ln, C, cmax; size_t smem; };
+  CGroup grp[3];
+  int ngrp = 0;
   const bool poly = (fam & FAM_POLY) != 0;
   const bool cluster_ok = has_long && (cap > 0 || poly) && h->cfg.schedule == TOP_SCHED_AUTO &&
                           (fam & ~(FAM_BOX | FAM_BALL | FAM_VN | FAM_POLY)) == 0;
   const int cmin = poly ? 1 : 2;
   if (cluster_ok) {
-    ccap = cluster_capacity(h, &pb);
+    const int ccap = cluster_capacity(h, &pb);
     if (ccap > 0) {
       const int Mb = (fam & FAM_BOX) ? pb.M_box : 0, Mq = (fam & FAM_BALL) ? pb.M_ball : 0,
                 Mv = (fam & FAM_VN) ? pb.M_vn : 0;
       const int Mp = poly ? pb.M_poly : 0;
-      csmem = res_layout(ccap, kClusterNtp, Mb, Mq, Mv, (int)rbytes(h), Mp).total;
-      if (h->csz_key_C != ccap || h->csz_key_fam != fam || h->csz_key_smem != csmem) {
-        h->csz_val = cluster_max_size(ccap, csmem, fam, fp64);
-        h->csz_key_C = ccap;
-        h->csz_key_fam = fam;
-        h->csz_key_smem = csmem;
+      const bool lanes = !fp64 && !adapt && !poly && Mb + Mq + Mv >= 8;
+      const int lns[3] = {4, 2, 1};
+      for (int q = lanes ? 0 : 2; q < 3; ++q) {
+        const int ln = lns[q];
+        const int C = ln == 1 ? ccap : std::min(ccap, max_cta_threads(h) / ln / 32 * 32);
+        if (C < 32) continue;
+        const size_t sm = res_layout(C, kClusterNtp, Mb, Mq, Mv, (int)rbytes(h), Mp).total;
+        if (h->csz_key_C[q] != C || h->csz_key_fam[q] != fam || h->csz_key_smem[q] != sm) {
+          h->csz_val[q] = cluster_max_size(C, ln, sm, fam, fp64);
+          h->csz_key_C[q] = C;
+          h->csz_key_fam[q] = fam;
+          h->csz_key_smem[q] = sm;
+        }
+        if (h->csz_val[q] >= cmin) grp[ngrp++] = CGroup{ln, C, h->csz_val[q], sm};
       }
-      cmax = h->csz_val;
     }
   }
-  auto cluster_size_for = [&](int nb) -> int {  // smallest power of two of CTAs that holds nb segments
-    if (cmax < cmin || ccap <= 0) return 0;
-    for (int c = cmin; c <= cmax; c <<= 1)
-      if ((long long)c * ccap >= nb) return c;
+  // a long trajectory's cluster: the first group (most lanes) and the smallest power of two
+  // of its CTAs that hold it, as group * 32 + CTAs; 0 = none
+  auto placement = [&](int nb) -> int {
+    for (int q = 0; q < ngrp; ++q)
+      for (int c = cmin; c <= grp[q].cmax; c <<= 1)
+        if ((long long)c * grp[q].C >= nb) return q * 32 + c;
     return 0;
   };
   bool any_cluster = false;
-  if (cluster_ok && cmax >= cmin) {
+  if (ngrp > 0) {
     DevResult drc = dr;
     ClusterArgs ca{};
     ca.p = dp; ca.r = drc; ca.G = h->G; ca.E = adapt ? h->E : nullptr; ca.traj = h->d_ctraj;
@@ -812,13 +825,14 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
       }
       ca.ypoly = h->d_ypoly;
     }
-    // one launch per cluster size, trajectories listed back to back in d_ctraj
+    // one launch per (group, cluster size), trajectories listed back to back in d_ctraj
     int nlist = 0;
-    for (int c = cmin; c <= cmax; c <<= 1)
-      for (int b = 0; b < B; ++b) {
-        const int nb = off[b + 1] - off[b];
-        if (nb > 0 && (cap == 0 || nb > cap) && cluster_size_for(nb) == c) h->h_ctraj[nlist++] = b;
-      }
+    for (int q = 0; q < ngrp; ++q)
+      for (int c = cmin; c <= grp[q].cmax; c <<= 1)
+        for (int b = 0; b < B; ++b) {
+          const int nb = off[b + 1] - off[b];
+          if (nb > 0 && (cap == 0 || nb > cap) && placement(nb) == q * 32 + c) h->h_ctraj[nlist++] = b;
+        }
     if (nlist > 0) {
       any_cluster = true;
       cudaStream_t cs = (npack > 0 && h->side) ? h->side : st;  // beside the resident packs when there are any
@@ -827,17 +841,18 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
       Range r3("cluster-resident trajectories");
       if (h->profiling) cudaEventRecord(h->ev[6], cs);
       int at = 0;
-      for (int c = cmin; c <= cmax; c <<= 1) {
-        int n = 0;
-        while (at + n < nlist && cluster_size_for(off[h->h_ctraj[at + n] + 1] - off[h->h_ctraj[at + n]]) == c) ++n;
-        if (n == 0) continue;
-        ca.traj = h->d_ctraj + at;
-        int e = fp64 ? launch_cluster_f64(ca, n, c, ccap, csmem, fam, cs)
-                     : launch_cluster_f32(ca, n, c, ccap, csmem, fam, cs);
-        h->launches += 1;
-        if (e) return cuda_fail(h, (cudaError_t)e);
-        at += n;
-      }
+      for (int q = 0; q < ngrp; ++q)
+        for (int c = cmin; c <= grp[q].cmax; c <<= 1) {
+          int n = 0;
+          while (at + n < nlist && placement(off[h->h_ctraj[at + n] + 1] - off[h->h_ctraj[at + n]]) == q * 32 + c) ++n;
+          if (n == 0) continue;
+          ca.traj = h->d_ctraj + at;
+          int e = fp64 ? launch_cluster_f64(ca, n, c, grp[q].C, grp[q].ln, grp[q].smem, fam, cs)
+                       : launch_cluster_f32(ca, n, c, grp[q].C, grp[q].ln, grp[q].smem, fam, cs);
+          h->launches += 1;
+          if (e) return cuda_fail(h, (cudaError_t)e);
+          at += n;
+        }
       if (h->profiling) { cudaEventRecord(h->ev[7], cs); h->ran[3] = true; }
       if (cs != st) {
         TOP_CUDA(h, cudaEventRecord(h->join_ev, cs));
@@ -850,7 +865,7 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
   if (has_long)
     for (int b = 0; b < B; ++b) {
       const int nb = off[b + 1] - off[b];
-      if (nb > 0 && (cap == 0 || nb > cap) && !(any_cluster && cluster_size_for(nb) > 0)) ++n_stream_traj;
+      if (nb > 0 && (cap == 0 || nb > cap) && !(any_cluster && placement(nb) > 0)) ++n_stream_traj;
     }
   if (n_stream_traj > 0) {
     int nl = 0, total = 0;
@@ -859,7 +874,7 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
     lt_pre[0] = 0;
     for (int b = 0; b < B; ++b) {
       const int nb = off[b + 1] - off[b];
-      if (nb > 0 && (cap == 0 || nb > cap) && !(any_cluster && cluster_size_for(nb) > 0)) {
+      if (nb > 0 && (cap == 0 || nb > cap) && !(any_cluster && placement(nb) > 0)) {
         lt_b[nl] = b;
         total += nb;
         lt_pre[++nl] = total;

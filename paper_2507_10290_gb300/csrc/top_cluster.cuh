@@ -37,8 +37,16 @@ namespace top {
 
 namespace cg = cooperative_groups;
 
-template <class R, int F, bool ADAPT>
+// LN lanes per segment (1, 2 or 4; LN > 1 for FP32 with box / ball / velocity-norm
+// rows and fixed rho): the sample rows of a segment's local step are split over
+// its LN consecutive lanes and their shares of the right-hand side summed across
+// them (xor butterfly: every lane gets the same sum, so every lane forms the same
+// coefficients and updates the states of its own samples); lane 0 of the segment
+// (`own`) does everything else.
+template <class R, int F, bool ADAPT, int LN = 1>
 __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(const ClusterArgs A) {
+  static_assert(LN == 1 || (LN == 2 || LN == 4) && !ADAPT && (F & FAM_POLY) == 0 && sizeof(R) == 4,
+                "lanes per segment: FP32, fixed rho, closed-form families only");
   constexpr bool BOX = (F & FAM_BOX) != 0;
   constexpr bool BALL = (F & FAM_BALL) != 0;
   constexpr bool VN = (F & FAM_VN) != 0;
@@ -56,8 +64,11 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
   const int g0 = p.seg_offset[b];
   const int Nb = p.seg_offset[b + 1] - g0;
   if (!TOP_IN_BOUNDS(p.err, Nb >= 0 && Nb <= csz * (int)blockDim.x && g0 >= 0 && g0 + Nb <= p.S)) return;
-  const int C = blockDim.x;
-  const int l = threadIdx.x;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int C = nthr / LN;      // segments per CTA
+  const int l = tid / LN;       // this thread's segment in the CTA
+  const int sub = tid % LN;     // its lane within the segment
+  const bool own = sub == 0;
   const int Mb = BOX ? p.M_box : 0, Mq = BALL ? p.M_ball : 0, Mv = VN ? p.M_vn : 0;
   const int Mp = POLY ? p.M_poly : 0, Fp = POLY ? p.F_poly : 0;
   const ResLayout L = res_layout(C, kClusterNtp, Mb, Mq, Mv, (int)sizeof(R), Mp);
@@ -92,16 +103,16 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
   const int jS = l, jE = l + 1;
 
   // ---- set-up: zeroed state, tables ----
-  for (int q = l; q < NJ * J; q += C) { sdz[q] = R(0); sp[q] = R(0); sm[q] = R(0); }
-  for (int q = l; q < 3 * J; q += C) szP[q] = R(0);
-  if (BOX) for (int q = l; q < 6 * Mb * C; q += C) sybox[q] = R(0);
-  if (BALL) for (int q = l; q < 3 * Mq * C; q += C) sqball[q] = R(0);
-  if (VN) for (int q = l; q < 3 * Mv * C; q += C) sqvn[q] = R(0);
-  if (BOX) fill_sample_table(tabB, Mb, 1, l, C);
-  if (BALL) fill_sample_table(tabQ, Mq, 0, l, C);
-  if (VN) fill_sample_table(tabV, Mv, 1, l, C);
-  if (POLY) fill_sample_table(tabP, Mp, 0, l, C);
-  if (l == 0) {
+  for (int q = tid; q < NJ * J; q += nthr) { sdz[q] = R(0); sp[q] = R(0); sm[q] = R(0); }
+  for (int q = tid; q < 3 * J; q += nthr) szP[q] = R(0);
+  if (BOX) for (int q = tid; q < 6 * Mb * C; q += nthr) sybox[q] = R(0);
+  if (BALL) for (int q = tid; q < 3 * Mq * C; q += nthr) sqball[q] = R(0);
+  if (VN) for (int q = tid; q < 3 * Mv * C; q += nthr) sqvn[q] = R(0);
+  if (BOX) fill_sample_table(tabB, Mb, 1, tid, nthr);
+  if (BALL) fill_sample_table(tabQ, Mq, 0, tid, nthr);
+  if (VN) fill_sample_table(tabV, Mv, 1, tid, nthr);
+  if (POLY) fill_sample_table(tabP, Mp, 0, tid, nthr);
+  if (tid == 0) {
     sdone[0] = 0;
     part[5] = p.rho;
     part[6] = 1.0;
@@ -142,7 +153,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
     }
     // Init of Algorithm 1 (the owner writes its end junction; the first
     // segment also its start junction)
-    for (int a = 0; a < AX; ++a)
+    for (int a = 0; a < (own ? AX : 0); ++a)
       for (int r = 0; r < ND; ++r) {
         const int row = a * ND + r;
         if (!last) {
@@ -161,7 +172,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
           mS[row] = z0;
         }
       }
-    if (A.from.p) {  // resume (top_resume): the exported targets and row states replace Init
+    if (A.from.p && own) {  // resume (top_resume): the exported targets and row states replace Init
       const size_t oE = (size_t)(g + b + 1) * NJ, oS = (size_t)(g + b) * NJ;
       for (int q = 0; q < NJ; ++q) {
         pE[q] = R(A.from.p[oE + q]);
@@ -197,7 +208,9 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
   const bool periodic = p.eps > 0.0 || res.history != nullptr;
   int done = 0;     // the stop decision, identical in every CTA of the cluster
   double rp_last = 0.0, rd_last = 0.0;
-  const int warp = l >> 5, lane = l & 31;
+  const int warp = tid >> 5, lane = tid & 31;
+  const unsigned vmask = __ballot_sync(0xffffffffu, valid);  // lanes of valid segments (a prefix of the warp)
+  (void)vmask;
   for (int k = 0; k < K; ++k) {
     const bool check = ADAPT || (k == K - 1) || (periodic && ((k + 1) % cev == 0));
     const bool act = valid && !done;
@@ -236,32 +249,47 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
         poly_solve((const R *)A.poly.G, (const R *)A.poly.U, (size_t)p.S, (size_t)g, rhs, ch);
         family_update<R, F & 7>(sc, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq, Mv, ch);
         poly_update(PN, PH, (size_t)p.S, (size_t)g, Fp, Mp, ypoly, p.S, tabP, ch);
+      } else if constexpr (LN > 1) {
+        R rhs[AX][NC];
+        family_rhs<R, F & 7, true>(sc, wS, wE, rho, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV,
+                                   Mb, Mq, Mv, rhs, sub, LN, own);
+#pragma unroll
+        for (int a = 0; a < AX; ++a)
+#pragma unroll
+          for (int q = 0; q < NC; ++q)
+#pragma unroll
+            for (int o = 1; o < LN; o <<= 1) rhs[a][q] += __shfl_xor_sync(vmask, rhs[a][q], o);
+        apply_g3(sc.G, rhs, ch);
+        family_update<R, F & 7>(sc, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq, Mv, ch,
+                                sub, LN);
       } else {
         local_step<R, F, true>(sc, wS, wE, rho, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb,
                                Mq, Mv, ch);
       }
       // ---- 2. publish start derivatives ----
-      end_derivs_shift(ch, fs, eSv, eE);
-#pragma unroll
-      for (int a = 0; a < AX; ++a)
-#pragma unroll
-        for (int r = 0; r < ND; ++r) seS[l * NJ + a * ND + r] = eSv[a][r];
-      // the trajectory's start slot has no other reader: its dual update (Eq. 18c
-      // against the fixed start state) needs no barrier
-      if (first) {
+      if (own) {
+        end_derivs_shift(ch, fs, eSv, eE);
 #pragma unroll
         for (int a = 0; a < AX; ++a)
 #pragma unroll
-          for (int r = 0; r < PO; ++r) {
-            const int row = a * ND + r;
-            pS[row] += mS[row] - eSv[a][r];
-          }
+          for (int r = 0; r < ND; ++r) seS[l * NJ + a * ND + r] = eSv[a][r];
+        // the trajectory's start slot has no other reader: its dual update (Eq. 18c
+        // against the fixed start state) needs no barrier
+        if (first) {
+#pragma unroll
+          for (int a = 0; a < AX; ++a)
+#pragma unroll
+            for (int r = 0; r < PO; ++r) {
+              const int row = a * ND + r;
+              pS[row] += mS[row] - eSv[a][r];
+            }
+        }
       }
     }
     cl.sync();
     // ---- 3. junction update (Eq. 18b, 18c) and primal residual (Eq. 19) ----
     R rp2 = R(0);
-    if (act) {
+    if (act && own) {
       if (!last) {
         if (check) {  // residual share and consensus change, from the values before the update
 #pragma unroll
@@ -313,7 +341,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
     if (check) {
       // ---- 4. dual residual (Eq. 20), cluster reduction, stopping rule (Eq. 21) ----
       R rd2 = R(0);
-      if (act) {
+      if (act && own) {
         R Tk[NC];
         Tk[0] = R(1);
 #pragma unroll
@@ -329,8 +357,10 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
           rd2 += dual_residual_sq(dS, dE, rho, Tk);
         }
       }
-      sh_rp[l] = rp2;
-      sh_rd[l] = rd2;
+      if (own) {
+        sh_rp[l] = rp2;
+        sh_rd[l] = rd2;
+      }
       __syncthreads();
       if (warp == 0) {  // this CTA's shares, accumulated in FP64 in a fixed order
         double a1 = 0.0, a2 = 0.0;
@@ -343,7 +373,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
         if (lane == 0) { part[0] = a1; part[1] = a2; }
       }
       cl.sync();
-      if (rank == 0 && l == 0 && !done) {  // shares in rank order, the stop decision
+      if (rank == 0 && tid == 0 && !done) {  // shares in rank order, the stop decision
         double s1 = 0.0, s2 = 0.0;
         for (int q = 0; q < csz; ++q) {
           const double *pq = cl.map_shared_rank(part, q);
@@ -425,7 +455,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
   }
 
   // ---- export of the state (top_resume) ----
-  if (A.to.p && valid) {
+  if (A.to.p && valid && own) {
     const size_t oE = (size_t)(g + b + 1) * NJ, oS = (size_t)(g + b) * NJ;
     for (int q = 0; q < NJ; ++q) {
       A.to.p[oE + q] = double(pE[q]);
@@ -442,7 +472,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
 
   // ---- outputs: coefficients in the paper's basis, FP64 cost (cluster sum in rank order) ----
   double Ji = 0.0;
-  if (valid) {
+  if (valid && own) {
     // c_k = ch_k T^-k with the iteration's own powers s_k
 #pragma unroll
     for (int a = 0; a < AX; ++a)
@@ -450,7 +480,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
       for (int q = 0; q < NC; ++q) res.coeffs[((size_t)g * AX + a) * NC + q] = double(ch[a][q] * sc.s[q]);
     Ji = segment_cost(ch, double(sc.s[7]));
   }
-  red[l] = Ji;
+  if (own) red[l] = Ji;
   __syncthreads();
   if (warp == 0) {
     double a1 = 0.0;
@@ -460,7 +490,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
     if (lane == 0) part[4] = a1;
   }
   cl.sync();
-  if (rank == 0 && l == 0) {
+  if (rank == 0 && tid == 0) {
     double J = 0.0;
     for (int q = 0; q < csz; ++q) J += cl.map_shared_rank(part, q)[4];
     res.cost[b] = J;
@@ -503,14 +533,16 @@ __host__ void *cluster_kernel_for_t(int fam) {
   }
 }
 
+// ln lanes per segment (ln > 1: FP32, fixed rho, families 1-7; top_cluster_lanes_f32.cu)
 template <class R>
-__host__ void *cluster_kernel_for(int fam, bool adapt) {
+__host__ void *cluster_kernel_for(int fam, bool adapt, int ln) {
+  if (ln > 1) return (sizeof(R) == 4 && !adapt) ? cluster_lanes_kernel_f32(fam, ln) : nullptr;
   return adapt ? cluster_kernel_for_t<R, true>(fam) : cluster_kernel_for_t<R, false>(fam);
 }
 
 template <class R>
-__host__ int cluster_max_size_t(int C, size_t smem, int fam) {
-  void *kern = cluster_kernel_for<R>(fam, false);
+__host__ int cluster_max_size_t(int C, int ln, size_t smem, int fam) {
+  void *kern = cluster_kernel_for<R>(fam, false, ln);
   if (!kern) return 0;
   if (func_attr_once(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       func_attr_once(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
@@ -520,7 +552,7 @@ __host__ int cluster_max_size_t(int C, size_t smem, int fam) {
   for (int csz = 16; csz >= 1; csz >>= 1) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(csz);
-    cfg.blockDim = dim3(C);
+    cfg.blockDim = dim3(C * ln);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -537,16 +569,16 @@ __host__ int cluster_max_size_t(int C, size_t smem, int fam) {
 }
 
 template <class R>
-__host__ int launch_cluster_t(const ClusterArgs &a, int nclusters, int csz, int C, size_t smem, int fam,
+__host__ int launch_cluster_t(const ClusterArgs &a, int nclusters, int csz, int C, int ln, size_t smem, int fam,
                               void *stream) {
-  void *kern = cluster_kernel_for<R>(fam, a.p.adaptive != 0 && a.E != nullptr);
+  void *kern = cluster_kernel_for<R>(fam, a.p.adaptive != 0 && a.E != nullptr, ln);
   if (!kern || nclusters <= 0) return kern ? 0 : (int)cudaErrorInvalidValue;
   cudaError_t e = func_attr_once(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = func_attr_once(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return (int)e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nclusters * csz);
-  cfg.blockDim = dim3(C);
+  cfg.blockDim = dim3(C * ln);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = (cudaStream_t)stream;
   cudaLaunchAttribute attr[1];

@@ -2,8 +2,9 @@
 #include "top_cluster.cuh"
 
 namespace top {
-int launch_cluster_f32(const ClusterArgs &a, int nclusters, int csz, int C, size_t smem, int fam, void *stream) {
-  return launch_cluster_t<float>(a, nclusters, csz, C, smem, fam, stream);
+int launch_cluster_f32(const ClusterArgs &a, int nclusters, int csz, int C, int ln, size_t smem, int fam,
+                       void *stream) {
+  return launch_cluster_t<float>(a, nclusters, csz, C, ln, smem, fam, stream);
 }
-int cluster_max_size_f32(int C, size_t smem, int fam) { return cluster_max_size_t<float>(C, smem, fam); }
+int cluster_max_size_f32(int C, int ln, size_t smem, int fam) { return cluster_max_size_t<float>(C, ln, smem, fam); }
 }  // namespace top

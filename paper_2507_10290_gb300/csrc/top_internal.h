@@ -259,13 +259,17 @@ int launch_sample(const int32_t *off, const double *T, int B, int M, int order, 
 int launch_time_step(double *T, const double *dT, int S, double kT, double lr, void *stream);
 int launch_resident_f32(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
 int launch_resident_f64(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
-int launch_cluster_f32(const ClusterArgs &a, int nclusters, int csz, int C, size_t smem, int fam, void *stream);
-int launch_cluster_f64(const ClusterArgs &a, int nclusters, int csz, int C, size_t smem, int fam, void *stream);
+// C segments per CTA, ln lanes per segment (blockDim = C * ln; ln > 1: FP32, fixed rho, families 1-7)
+int launch_cluster_f32(const ClusterArgs &a, int nclusters, int csz, int C, int ln, size_t smem, int fam,
+                       void *stream);
+int launch_cluster_f64(const ClusterArgs &a, int nclusters, int csz, int C, int ln, size_t smem, int fam,
+                       void *stream);
+void *cluster_lanes_kernel_f32(int fam, int ln);
 // largest cluster size (power of two <= 16) whose CTAs of C threads and `smem`
 // bytes can be co-scheduled, 0 if none
-int cluster_max_size(int C, size_t smem, int fam, bool fp64);
-int cluster_max_size_f32(int C, size_t smem, int fam);
-int cluster_max_size_f64(int C, size_t smem, int fam);
+int cluster_max_size(int C, int ln, size_t smem, int fam, bool fp64);
+int cluster_max_size_f32(int C, int ln, size_t smem, int fam);
+int cluster_max_size_f64(int C, int ln, size_t smem, int fam);
 int launch_stream_f32(const StreamArgs &a, int fam, void *stream);
 int launch_stream_f64(const StreamArgs &a, int fam, void *stream);
 // Adjoint of the unrolled iteration (top_grad)

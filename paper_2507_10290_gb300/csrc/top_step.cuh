@@ -47,15 +47,22 @@ __device__ __forceinline__ void fill_sample_table(R *tab, int M, int order, int 
 // velocity-norm families (the first half of the local step).
 // FS: the targets wS and wE both carry the factor r! (wS = r! s_r p, wE = r! s_r m)
 // and the consensus rows go through the Taylor shift (consensus_rhs_shift)
+// j0, js: the sample rows j = j0, j0 + js, ... (a segment's rows split over js
+// lanes); cons: include the consensus rows (one lane of the js)
 template <class R, int F, bool FS = false>
 __device__ __forceinline__ void family_rhs(const SegConst<R> &sc, const R (&wS)[AX][ND], const R (&wE)[AX][ND],
                                            R rho, bool first_iter, const R *ybox, const R *qball, const R *qvn,
                                            int stride, const R *tabB, const R *tabQ, const R *tabV, int Mb, int Mq,
-                                           int Mv, R (&rhs)[AX][NC]) {
+                                           int Mv, R (&rhs)[AX][NC], int j0 = 0, int js = 1, bool cons = true) {
   constexpr bool BOX = (F & FAM_BOX) != 0;
   constexpr bool BALL = (F & FAM_BALL) != 0;
   constexpr bool VN = (F & FAM_VN) != 0;
-  if (FS) {
+  if (!cons) {
+#pragma unroll
+    for (int a = 0; a < AX; ++a)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) rhs[a][q] = R(0);
+  } else if (FS) {
     consensus_rhs_shift(wS, wE, rho, rhs);
   } else {
 #pragma unroll
@@ -66,7 +73,7 @@ __device__ __forceinline__ void family_rhs(const SegConst<R> &sc, const R (&wS)[
     }
   }
   if (BOX) {
-    for (int j = 0; j < Mb; ++j) {
+    for (int j = j0; j < Mb; j += js) {
 #pragma unroll
       for (int a = 0; a < AX; ++a) {
         const R yp = ybox[((j * 3 + a) * 2 + 0) * stride];
@@ -78,7 +85,7 @@ __device__ __forceinline__ void family_rhs(const SegConst<R> &sc, const R (&wS)[
     }
   }
   if (BALL && !first_iter) {
-    for (int j = 0; j < Mq; ++j) {
+    for (int j = j0; j < Mq; j += js) {
       R qv[3], ph[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) qv[a] = qball[(j * 3 + a) * stride];
@@ -93,7 +100,7 @@ __device__ __forceinline__ void family_rhs(const SegConst<R> &sc, const R (&wS)[
   }
   if (VN && !first_iter) {
     const R zero3[3] = {R(0), R(0), R(0)};
-    for (int j = 0; j < Mv; ++j) {
+    for (int j = j0; j < Mv; j += js) {
       R qv[3], ph[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) qv[a] = qvn[(j * 3 + a) * stride];
@@ -110,15 +117,16 @@ __device__ __forceinline__ void family_rhs(const SegConst<R> &sc, const R (&wS)[
 
 // Projections and their duals with the new coefficients (Eq. 18d-g) for the
 // box / ball / velocity-norm families (the second half of the local step).
+// (j0, js as in family_rhs: each lane updates the rows of its own samples)
 template <class R, int F>
 __device__ __forceinline__ void family_update(const SegConst<R> &sc, bool first_iter, R *ybox, R *qball, R *qvn,
                                               int stride, const R *tabB, const R *tabQ, const R *tabV, int Mb,
-                                              int Mq, int Mv, const R (&ch)[AX][NC]) {
+                                              int Mq, int Mv, const R (&ch)[AX][NC], int j0 = 0, int js = 1) {
   constexpr bool BOX = (F & FAM_BOX) != 0;
   constexpr bool BALL = (F & FAM_BALL) != 0;
   constexpr bool VN = (F & FAM_VN) != 0;
   if (BOX) {
-    for (int j = 0; j < Mb; ++j) {
+    for (int j = j0; j < Mb; j += js) {
 #pragma unroll
       for (int a = 0; a < AX; ++a) {
         R v = R(0);
@@ -135,7 +143,7 @@ __device__ __forceinline__ void family_update(const SegConst<R> &sc, bool first_
     }
   }
   if (BALL) {
-    for (int j = 0; j < Mq; ++j) {
+    for (int j = j0; j < Mq; j += js) {
       R qv[3], ph[3], pos[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -155,7 +163,7 @@ __device__ __forceinline__ void family_update(const SegConst<R> &sc, bool first_
   }
   if (VN) {
     const R zero3[3] = {R(0), R(0), R(0)};
-    for (int j = 0; j < Mv; ++j) {
+    for (int j = j0; j < Mv; j += js) {
       R qv[3], ph[3], vel[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {

@@ -88,6 +88,20 @@ def test_default_capacity_corridor_runs_in_clusters(T):
     compare(g, o, w, TOL["fp32"])
 
 
+@pytest.mark.parametrize("N", [600, 2600])
+def test_lanes_per_segment_corridors_fp32(T, N):
+    """FP32 corridors with box and ball rows: the cluster kernel splits each
+    segment's sample rows over 4 lanes (N = 600: 128 segments per CTA) or over
+    2 (N = 2600, longer than 16 CTAs of 128 segments), and must still match
+    the oracle with no streaming."""
+    from test_parity_gpu import solver
+    w = W.corridor(N=N).with_(max_iters=150)
+    g, ms = solve_profiled(T, solver(T, "fp32"), w)
+    assert ms[3] > 0.0 and ms[2] == 0.0
+    o = oracle.solve(w)
+    compare(g, o, w, TOL["fp32"])
+
+
 @pytest.mark.parametrize("mode", ["pin", "free"])
 def test_cluster_form_with_adaptive_rho_fp64(T, mode):
     """Residual balancing (Eq. 22) inside clusters: rank 0 applies the rule,
