@@ -112,7 +112,9 @@ typedef struct top_config {
 
 /* One batch.  Pointers are device pointers for TOP_MEM_DEVICE and host
  * pointers for TOP_MEM_HOST (the library then stages them through its
- * workspace); optional families pass M_* = 0 and NULL pointers. */
+ * workspace; a page-locked, mapped top_result.coeffs buffer is written by the
+ * kernels directly instead, with no copy after the solve); optional families
+ * pass M_* = 0 and NULL pointers. */
 typedef struct top_problem {
   int32_t B;                  /* trajectories */
   int32_t memory;             /* enum top_memory */

@@ -77,8 +77,8 @@ struct top_handle {
   // cluster-resident form: trajectory lists (pinned host, device) and the cached
   // largest co-schedulable cluster size for (C, family, precision)
   int *h_ctraj = nullptr, *d_ctraj = nullptr;  // [max_batch]
-  int csz_key_C[3] = {-1, -1, -1}, csz_key_fam[3] = {-1, -1, -1}, csz_val[3] = {0, 0, 0};  // per lanes group
-  size_t csz_key_smem[3] = {0, 0, 0};
+  int csz_key_C[4] = {-1, -1, -1, -1}, csz_key_fam[4] = {-1, -1, -1, -1}, csz_val[4] = {0, 0, 0, 0};  // per lanes group
+  size_t csz_key_smem[4] = {0, 0, 0, 0};
   // top_resume with host memory: device copies of the states (grow-only)
   unsigned char *d_ws = nullptr;
   size_t ws_bytes = 0;
@@ -509,6 +509,7 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
   const bool host = pb_in->memory == TOP_MEM_HOST;
   const StagePlan SP = stage_plan(h->cfg.max_batch, h->cfg.max_segments);
   double *d_hist = nullptr;
+  double *coef_mapped = nullptr;  // device view of page-locked caller memory for the coefficients
   if (host) {
     unsigned char *base = h->d_stage;
     auto up = [&](const void *src, size_t off_, size_t bytes) -> const void * {
@@ -537,7 +538,18 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
       pb.poly_h = (const double *)(h->d_pstage + align_up(bn, 256));
     }
     TOP_CUDA(h, cudaGetLastError());
-    res.coeffs = (double *)(base + SP.off_coef);
+    // page-locked (mapped) caller memory takes the coefficients directly: the
+    // kernels write them over the chip-to-host link as their CTAs finish, and
+    // the copy back after the solve is skipped
+    coef_mapped = nullptr;
+    {
+      cudaPointerAttributes pa{};
+      if (res_in->coeffs && cudaPointerGetAttributes(&pa, res_in->coeffs) == cudaSuccess &&
+          pa.type == cudaMemoryTypeHost && pa.devicePointer)
+        coef_mapped = (double *)pa.devicePointer;
+      cudaGetLastError();
+    }
+    res.coeffs = coef_mapped ? coef_mapped : (double *)(base + SP.off_coef);
     res.cost = (double *)(base + SP.off_cost);
     res.r_primal = (double *)(base + SP.off_rp);
     res.r_dual = (double *)(base + SP.off_rd);
@@ -769,8 +781,9 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
   // polytope trajectories of any length use the cluster form (a cluster of one CTA
   // for short ones): the resident packs have no room for their per-axis inverses
   // cluster groups: lanes per segment, segments per CTA, shared memory, largest cluster.  With
-  // sample rows (FP32, fixed rho) a segment's rows are split over 4 or 2 lanes where the
-  // trajectory fits a cluster of such CTAs; the rest run one lane per segment.
+  // sample rows (FP32, fixed rho) a segment's rows are split over 4 or 2 lanes (at least two
+  // rows per lane) where the trajectory fits a cluster of such CTAs; the rest run one lane per
+  // segment.
   struct CGroup { int ln, C, cmax; size_t smem; };
   CGroup grp[3];
   int ngrp = 0;
@@ -784,10 +797,11 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
       const int Mb = (fam & FAM_BOX) ? pb.M_box : 0, Mq = (fam & FAM_BALL) ? pb.M_ball : 0,
                 Mv = (fam & FAM_VN) ? pb.M_vn : 0;
       const int Mp = poly ? pb.M_poly : 0;
-      const bool lanes = !fp64 && !adapt && !poly && Mb + Mq + Mv >= 8;
-      const int lns[3] = {4, 2, 1};
-      for (int q = lanes ? 0 : 2; q < 3; ++q) {
+      const int rows = Mb + Mq + Mv + Mp;  // sample rows per segment
+      const int lns[3] = {4, 2, 1};  // (8 lanes measured no faster: the rows a lane repeats dominate)
+      for (int q = 0; q < 3; ++q) {
         const int ln = lns[q];
+        if (ln > 1 && (fp64 || adapt || rows < 2 * ln)) continue;  // at least two rows per lane
         const int C = ln == 1 ? ccap : std::min(ccap, max_cta_threads(h) / ln / 32 * 32);
         if (C < 32) continue;
         const size_t sm = res_layout(C, kClusterNtp, Mb, Mq, Mv, (int)rbytes(h), Mp).total;
@@ -955,7 +969,8 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
     TOP_CUDA(h, cudaMemcpyAsync(to->iters, tov.iters, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
   }
   if (host) {
-    TOP_CUDA(h, cudaMemcpyAsync(res_in->coeffs, res.coeffs, sizeof(double) * 24 * S, cudaMemcpyDeviceToHost, st));
+    if (!coef_mapped)
+      TOP_CUDA(h, cudaMemcpyAsync(res_in->coeffs, res.coeffs, sizeof(double) * 24 * S, cudaMemcpyDeviceToHost, st));
     TOP_CUDA(h, cudaMemcpyAsync(res_in->cost, res.cost, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
     TOP_CUDA(h, cudaMemcpyAsync(res_in->r_primal, res.r_primal, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
     TOP_CUDA(h, cudaMemcpyAsync(res_in->r_dual, res.r_dual, sizeof(double) * B, cudaMemcpyDeviceToHost, st));

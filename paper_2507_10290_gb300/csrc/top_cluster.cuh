@@ -37,16 +37,28 @@ namespace top {
 
 namespace cg = cooperative_groups;
 
-// LN lanes per segment (1, 2 or 4; LN > 1 for FP32 with box / ball / velocity-norm
-// rows and fixed rho): the sample rows of a segment's local step are split over
-// its LN consecutive lanes and their shares of the right-hand side summed across
-// them (xor butterfly: every lane gets the same sum, so every lane forms the same
-// coefficients and updates the states of its own samples); lane 0 of the segment
-// (`own`) does everything else.
+// the sum of a right-hand side over the LN lanes of a segment (xor butterfly:
+// every lane gets the same sum, the additions being commutative)
+template <int LN, class R>
+__device__ __forceinline__ void lanes_allreduce(R (&rhs)[AX][NC], unsigned mask) {
+#pragma unroll
+  for (int a = 0; a < AX; ++a)
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+#pragma unroll
+      for (int o = 1; o < LN; o <<= 1) rhs[a][q] += __shfl_xor_sync(mask, rhs[a][q], o);
+}
+
+// LN lanes per segment (1, 2 or 4; LN > 1 for FP32 with sample rows and fixed
+// rho): the sample rows of a segment's local step (box, ball, velocity-norm,
+// polytope) are split over its LN consecutive lanes and their shares of the
+// right-hand side summed across them, so every lane forms the same
+// coefficients and updates the states of its own samples; lane 0 of the
+// segment (`own`) does everything else.
 template <class R, int F, bool ADAPT, int LN = 1>
 __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(const ClusterArgs A) {
-  static_assert(LN == 1 || (LN == 2 || LN == 4) && !ADAPT && (F & FAM_POLY) == 0 && sizeof(R) == 4,
-                "lanes per segment: FP32, fixed rho, closed-form families only");
+  static_assert(LN == 1 || ((LN == 2 || LN == 4) && !ADAPT && sizeof(R) == 4),
+                "lanes per segment: FP32 and fixed rho only");
   constexpr bool BOX = (F & FAM_BOX) != 0;
   constexpr bool BALL = (F & FAM_BALL) != 0;
   constexpr bool VN = (F & FAM_VN) != 0;
@@ -141,7 +153,8 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
     } else {
 #pragma unroll
       for (int q = 0; q < NG; ++q) sc.G[q] = R(0);
-      for (int q = 0; q < Fp * Mp; ++q) ypoly[(size_t)q * p.S] = R(0);
+      if (own)
+        for (int q = 0; q < Fp * Mp; ++q) ypoly[(size_t)q * p.S] = R(0);
     }
     Tq = R(p.durations[g]);
     inv_powers(Tq, sc.s);
@@ -244,21 +257,18 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
         const R *PN = (const R *)A.poly.N, *PH = (const R *)A.poly.H;
         R rhs[AX][NC];
         family_rhs<R, F & 7, true>(sc, wS, wE, rho, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV,
-                                   Mb, Mq, Mv, rhs);
-        poly_rhs(PN, PH, (size_t)p.S, (size_t)g, Fp, Mp, rho, ypoly, p.S, tabP, rhs);
+                                   Mb, Mq, Mv, rhs, sub, LN, own);
+        poly_rhs(PN, PH, (size_t)p.S, (size_t)g, Fp, Mp, rho, ypoly, p.S, tabP, rhs, sub, LN);
+        if constexpr (LN > 1) lanes_allreduce<LN>(rhs, vmask);
         poly_solve((const R *)A.poly.G, (const R *)A.poly.U, (size_t)p.S, (size_t)g, rhs, ch);
-        family_update<R, F & 7>(sc, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq, Mv, ch);
-        poly_update(PN, PH, (size_t)p.S, (size_t)g, Fp, Mp, ypoly, p.S, tabP, ch);
+        family_update<R, F & 7>(sc, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq, Mv, ch,
+                                sub, LN);
+        poly_update(PN, PH, (size_t)p.S, (size_t)g, Fp, Mp, ypoly, p.S, tabP, ch, sub, LN);
       } else if constexpr (LN > 1) {
         R rhs[AX][NC];
         family_rhs<R, F & 7, true>(sc, wS, wE, rho, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV,
                                    Mb, Mq, Mv, rhs, sub, LN, own);
-#pragma unroll
-        for (int a = 0; a < AX; ++a)
-#pragma unroll
-          for (int q = 0; q < NC; ++q)
-#pragma unroll
-            for (int o = 1; o < LN; o <<= 1) rhs[a][q] += __shfl_xor_sync(vmask, rhs[a][q], o);
+        lanes_allreduce<LN>(rhs, vmask);
         apply_g3(sc.G, rhs, ch);
         family_update<R, F & 7>(sc, k + k0 == 0, sybox + l, sqball + l, sqvn + l, C, tabB, tabQ, tabV, Mb, Mq, Mv, ch,
                                 sub, LN);
@@ -533,7 +543,7 @@ __host__ void *cluster_kernel_for_t(int fam) {
   }
 }
 
-// ln lanes per segment (ln > 1: FP32, fixed rho, families 1-7; top_cluster_lanes_f32.cu)
+// ln lanes per segment (ln > 1: FP32, fixed rho, families with sample rows; top_cluster_l*_f32.cu)
 template <class R>
 __host__ void *cluster_kernel_for(int fam, bool adapt, int ln) {
   if (ln > 1) return (sizeof(R) == 4 && !adapt) ? cluster_lanes_kernel_f32(fam, ln) : nullptr;

@@ -152,6 +152,7 @@ __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, 
   L.ybox = o;   o += size_t(rb) * 6 * Mb * C;
   L.qball = o;  o += size_t(rb) * 3 * Mq * C;
   L.qvn = o;    o += size_t(rb) * 3 * Mv * C;
+  o = align_up(o, 16);  // table rows are read as 16-byte vectors
   L.tabB = o;   o += size_t(rb) * 8 * Mb;
   L.tabQ = o;   o += size_t(rb) * 8 * Mq;
   L.tabV = o;   o += size_t(rb) * 8 * Mv;
@@ -265,6 +266,8 @@ int launch_cluster_f32(const ClusterArgs &a, int nclusters, int csz, int C, int 
 int launch_cluster_f64(const ClusterArgs &a, int nclusters, int csz, int C, int ln, size_t smem, int fam,
                        void *stream);
 void *cluster_lanes_kernel_f32(int fam, int ln);
+void *cluster_lanes2_kernel_f32(int fam);
+void *cluster_lanes4_kernel_f32(int fam);
 // largest cluster size (power of two <= 16) whose CTAs of C threads and `smem`
 // bytes can be co-scheduled, 0 if none
 int cluster_max_size(int C, int ln, size_t smem, int fam, bool fp64);

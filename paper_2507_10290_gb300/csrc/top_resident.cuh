@@ -473,6 +473,8 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   }
 
   // ---- outputs: coefficients in the paper's basis, FP64 cost per trajectory ----
+  __syncthreads();  // the junction state is dead: its memory holds the warps' output tiles
+  double *tile = (double *)(smem + L.p) + (size_t)(l >> 5) * 32 * kOutRow;
   double Ji = 0.0;
   if (valid) {
     R ch[AX][NC];
@@ -485,9 +487,10 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
 #pragma unroll
     for (int a = 0; a < AX; ++a)
 #pragma unroll
-      for (int q = 0; q < NC; ++q) res.coeffs[((size_t)g * AX + a) * NC + q] = double(ch[a][q] * sc.s[q]);
+      for (int q = 0; q < NC; ++q) tile[(l & 31) * kOutRow + a * NC + q] = double(ch[a][q] * sc.s[q]);
     Ji = segment_cost(ch, double(sc.s[7]));
   }
+  store_rows_warp(res.coeffs, tile, g, valid);
   red_rp[l] = Ji;
   __syncthreads();
   {

@@ -43,6 +43,44 @@ __device__ __forceinline__ void fill_sample_table(R *tab, int M, int order, int 
   }
 }
 
+// Coefficient output of a warp's 32 segments (one per lane) through a
+// shared-memory tile: each lane has written its 24 values to row `lane` of
+// `tile` (stride kOutRow doubles); the warp then stores them with consecutive
+// lanes on consecutive words, so the segments of one trajectory (consecutive
+// in g) go out as contiguous runs instead of 24 stores strided by a segment's
+// 192 bytes.  That matters most when `out` is page-locked host memory written
+// over the chip-to-host link.  Every lane of the warp calls it.
+constexpr int kOutRow = 25;
+__device__ __forceinline__ void store_rows_warp(double *out, const double *tile, int g, bool valid) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+#pragma unroll 4
+  for (int t = 0; t < 24; ++t) {
+    const int e = t * 32 + lane, s = e / 24, w = e - s * 24;
+    const int gs = __shfl_sync(0xffffffffu, g, s);
+    const int vs = __shfl_sync(0xffffffffu, valid ? 1 : 0, s);
+    if (vs) out[(size_t)gs * 24 + w] = tile[s * kOutRow + w];
+  }
+  __syncwarp();
+}
+
+// One row of a sample table (8 values; rows start on 16-byte boundaries).
+template <class R>
+__device__ __forceinline__ void tab_row(const R *t, R (&v)[NC]) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 a = reinterpret_cast<const float4 *>(t)[0], b = reinterpret_cast<const float4 *>(t)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < NC / 2; ++q) {
+      const double2 x = reinterpret_cast<const double2 *>(t)[q];
+      v[2 * q] = x.x;
+      v[2 * q + 1] = x.y;
+    }
+  }
+}
+
 // The right-hand side of Eq. 18a for the consensus rows and the box / ball /
 // velocity-norm families (the first half of the local step).
 // FS: the targets wS and wE both carry the factor r! (wS = r! s_r p, wE = r! s_r m)
@@ -74,19 +112,22 @@ __device__ __forceinline__ void family_rhs(const SegConst<R> &sc, const R (&wS)[
   }
   if (BOX) {
     for (int j = j0; j < Mb; j += js) {
+      R tb[NC];
+      tab_row(tabB + j * 8, tb);
 #pragma unroll
       for (int a = 0; a < AX; ++a) {
         const R yp = ybox[((j * 3 + a) * 2 + 0) * stride];
         const R ym = ybox[((j * 3 + a) * 2 + 1) * stride];
         const R coef = rho * sc.s[1] * (rabs(ym) - rabs(yp));
 #pragma unroll
-        for (int q = 0; q < NC; ++q) rhs[a][q] += coef * tabB[j * 8 + q];
+        for (int q = 0; q < NC; ++q) rhs[a][q] += coef * tb[q];
       }
     }
   }
   if (BALL && !first_iter) {
     for (int j = j0; j < Mq; j += js) {
-      R qv[3], ph[3];
+      R qv[3], ph[3], tq[NC];
+      tab_row(tabQ + j * 8, tq);
 #pragma unroll
       for (int a = 0; a < 3; ++a) qv[a] = qball[(j * 3 + a) * stride];
       project_ball(qv, sc.bo, sc.brad, ph);
@@ -94,14 +135,15 @@ __device__ __forceinline__ void family_rhs(const SegConst<R> &sc, const R (&wS)[
       for (int a = 0; a < AX; ++a) {
         const R coef = rho * (R(2) * ph[a] - qv[a]);
 #pragma unroll
-        for (int q = 0; q < NC; ++q) rhs[a][q] += coef * tabQ[j * 8 + q];
+        for (int q = 0; q < NC; ++q) rhs[a][q] += coef * tq[q];
       }
     }
   }
   if (VN && !first_iter) {
     const R zero3[3] = {R(0), R(0), R(0)};
     for (int j = j0; j < Mv; j += js) {
-      R qv[3], ph[3];
+      R qv[3], ph[3], tv[NC];
+      tab_row(tabV + j * 8, tv);
 #pragma unroll
       for (int a = 0; a < 3; ++a) qv[a] = qvn[(j * 3 + a) * stride];
       project_ball(qv, zero3, sc.vnorm, ph);
@@ -109,7 +151,7 @@ __device__ __forceinline__ void family_rhs(const SegConst<R> &sc, const R (&wS)[
       for (int a = 0; a < AX; ++a) {
         const R coef = rho * sc.s[1] * (R(2) * ph[a] - qv[a]);
 #pragma unroll
-        for (int q = 0; q < NC; ++q) rhs[a][q] += coef * tabV[j * 8 + q];
+        for (int q = 0; q < NC; ++q) rhs[a][q] += coef * tv[q];
       }
     }
   }
@@ -127,11 +169,13 @@ __device__ __forceinline__ void family_update(const SegConst<R> &sc, bool first_
   constexpr bool VN = (F & FAM_VN) != 0;
   if (BOX) {
     for (int j = j0; j < Mb; j += js) {
+      R tb[NC];
+      tab_row(tabB + j * 8, tb);
 #pragma unroll
       for (int a = 0; a < AX; ++a) {
         R v = R(0);
 #pragma unroll
-        for (int q = 0; q < NC; ++q) v += tabB[j * 8 + q] * ch[a][q];
+        for (int q = 0; q < NC; ++q) v += tb[q] * ch[a][q];
         v *= sc.s[1];
         R *yp = &ybox[((j * 3 + a) * 2 + 0) * stride];
         R *ym = &ybox[((j * 3 + a) * 2 + 1) * stride];
@@ -144,13 +188,14 @@ __device__ __forceinline__ void family_update(const SegConst<R> &sc, bool first_
   }
   if (BALL) {
     for (int j = j0; j < Mq; j += js) {
-      R qv[3], ph[3], pos[3];
+      R qv[3], ph[3], pos[3], tq[NC];
+      tab_row(tabQ + j * 8, tq);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         qv[a] = qball[(j * 3 + a) * stride];
         R acc = R(0);
 #pragma unroll
-        for (int q = 0; q < NC; ++q) acc += tabQ[j * 8 + q] * ch[a][q];
+        for (int q = 0; q < NC; ++q) acc += tq[q] * ch[a][q];
         pos[a] = acc;
       }
       project_ball(qv, sc.bo, sc.brad, ph);
@@ -164,13 +209,14 @@ __device__ __forceinline__ void family_update(const SegConst<R> &sc, bool first_
   if (VN) {
     const R zero3[3] = {R(0), R(0), R(0)};
     for (int j = j0; j < Mv; j += js) {
-      R qv[3], ph[3], vel[3];
+      R qv[3], ph[3], vel[3], tv[NC];
+      tab_row(tabV + j * 8, tv);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         qv[a] = qvn[(j * 3 + a) * stride];
         R acc = R(0);
 #pragma unroll
-        for (int q = 0; q < NC; ++q) acc += tabV[j * 8 + q] * ch[a][q];
+        for (int q = 0; q < NC; ++q) acc += tv[q] * ch[a][q];
         vel[a] = acc * sc.s[1];
       }
       project_ball(qv, zero3, sc.vnorm, ph);
@@ -209,19 +255,22 @@ __device__ __forceinline__ void local_step(const SegConst<R> &sc, const R (&wS)[
 // rhs_a += rho sum_j tau_j^k sum_f n_f[a] (h_f - |y_jf|)   (A°^T (b - s - v), Eq. 18a)
 template <class R>
 __device__ __forceinline__ void poly_rhs(const R *PN, const R *PH, size_t S, size_t g, int F, int M, R rho,
-                                         const R *ypoly, int stride, const R *tabP, R (&rhs)[AX][NC]) {
-  for (int j = 0; j < M; ++j) {
+                                         const R *ypoly, int stride, const R *tabP, R (&rhs)[AX][NC], int j0 = 0,
+                                         int js = 1) {
+  for (int j = j0; j < M; j += js) {
     R w[3] = {R(0), R(0), R(0)};
     for (int f = 0; f < F; ++f) {
       const R c = PH[(size_t)f * S + g] - rabs(ypoly[(j * F + f) * stride]);
 #pragma unroll
       for (int a = 0; a < 3; ++a) w[a] += PN[(size_t)(f * 3 + a) * S + g] * c;
     }
+    R tp[NC];
+    tab_row(tabP + j * 8, tp);
 #pragma unroll
     for (int a = 0; a < AX; ++a) {
       const R coef = rho * w[a];
 #pragma unroll
-      for (int q = 0; q < NC; ++q) rhs[a][q] += coef * tabP[j * 8 + q];
+      for (int q = 0; q < NC; ++q) rhs[a][q] += coef * tp[q];
     }
   }
 }
@@ -259,14 +308,16 @@ __device__ __forceinline__ void poly_solve(const R *PG, const R *PU, size_t S, s
 // update of Eq. 18d-e in the compressed form (s = max(0, -y), v = max(0, y))
 template <class R>
 __device__ __forceinline__ void poly_update(const R *PN, const R *PH, size_t S, size_t g, int F, int M, R *ypoly,
-                                            int stride, const R *tabP, const R (&ch)[AX][NC]) {
-  for (int j = 0; j < M; ++j) {
-    R pos[3];
+                                            int stride, const R *tabP, const R (&ch)[AX][NC], int j0 = 0,
+                                            int js = 1) {
+  for (int j = j0; j < M; j += js) {
+    R pos[3], tp[NC];
+    tab_row(tabP + j * 8, tp);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       R acc = R(0);
 #pragma unroll
-      for (int q = 0; q < NC; ++q) acc += tabP[j * 8 + q] * ch[a][q];
+      for (int q = 0; q < NC; ++q) acc += tp[q] * ch[a][q];
       pos[a] = acc;
     }
     for (int f = 0; f < F; ++f) {

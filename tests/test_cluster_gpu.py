@@ -90,10 +90,10 @@ def test_default_capacity_corridor_runs_in_clusters(T):
 
 @pytest.mark.parametrize("N", [600, 2600])
 def test_lanes_per_segment_corridors_fp32(T, N):
-    """FP32 corridors with box and ball rows: the cluster kernel splits each
-    segment's sample rows over 4 lanes (N = 600: 128 segments per CTA) or over
-    2 (N = 2600, longer than 16 CTAs of 128 segments), and must still match
-    the oracle with no streaming."""
+    """FP32 corridors with box and ball rows (32 sample rows per segment): the
+    cluster kernel splits each segment's rows over 4 lanes (N = 600: 128
+    segments per CTA) or 2 (N = 2600: longer than 16 CTAs of 128), and must
+    still match the oracle with no streaming."""
     from test_parity_gpu import solver
     w = W.corridor(N=N).with_(max_iters=150)
     g, ms = solve_profiled(T, solver(T, "fp32"), w)
