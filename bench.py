@@ -696,7 +696,7 @@ def run_suite(args):
     if want("grad"):
         grad_line(top, oracle)
     if want("general_full"):
-        general_full_line(top)
+        general_full_line(top, args)
     if want("shared"):
         gpu_case("batch with one duration per trajectory (64-trajectory subset for the oracle)",
                  W.batch(shared_T=True).subset(list(range(64))), precs=("fp32", "fp64"))
@@ -882,26 +882,47 @@ def grad_line(top, oracle):
                       "oracle_one_directional_fd_seconds_per_trajectory": fd_s}), flush=True)
 
 
-def general_full_line(top):
+# streaming form, one segment-iteration in FP32 with no general bound active: the state it
+# reads (z, u of both junctions 45, y 32, T 1 floats) and writes (45 + 32 floats)
+STREAM_BYTES_PER_SEG_IT = 4 * (45 + 32 + 1 + 45 + 32)
+
+
+def general_full_line(top, args):
     """The full 1e5-segment general-bounds trajectory on the GPU only (the
-    oracle's comparison is the N=1000 line)."""
+    oracle's comparison is the N=1000 line), with the streaming kernels'
+    time per iteration against the HBM and FP32 rooflines."""
     w = W.general()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
     for prec in ("fp32",):
         s = top.Solver(max_batch=1, max_segments=w.S, precision=prec, max_samples=16)
         tensors = s.device_inputs(w)
         out = s.alloc_result(1, w.S, w.max_iters)
         s.solve(w, tensors=tensors, out=out, max_iters=5)
         ms = _timed_solve(s, w, tensors, out)
-        wt = w.with_(eps=1e-4, max_iters=20000)
-        out2 = s.alloc_result(1, w.S, 20000)
-        mt = _timed_solve(s, wt, tensors, out2)
-        print(json.dumps({"suite": "general (N=100000, numerical step)", "segments": int(w.S),
-                          prec: {"ms_200_iterations": ms, "us_per_iteration": 1000 * ms / 200,
-                                 "to_tolerance": {"eps": 1e-4, "cap": 20000, "ms": mt,
-                                                  "iterations": int(out2["iters"][0]),
-                                                  "status": int(out2["status"][0]),
-                                                  "r_primal": float(out2["r_primal"][0]),
-                                                  "r_dual": float(out2["r_dual"][0])}}}), flush=True)
+        top.top_set_profiling(s.handle, True)
+        _timed_solve(s, w, tensors, out)
+        kt = top.top_kernel_times(s.handle, 4)[1]
+        top.top_set_profiling(s.handle, False)
+        it_s = kt[2] / 1000 / w.max_iters  # streaming kernels per iteration
+        hbm = STREAM_BYTES_PER_SEG_IT * w.S / it_s / 1e9
+        alu = FLOP_PER_SEG_IT * w.S / it_s / 1e12
+        import torch
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        line = {"ms_200_iterations": ms, "us_per_iteration": 1000 * ms / 200,
+                "streaming_kernels_us_per_iteration": it_s * 1e6,
+                "roofline": {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": hbm / peaks["hbm_gbs"], "bytes_per_segment_iteration": STREAM_BYTES_PER_SEG_IT,
+                             "alu_tflops": alu, "alu_frac": alu / (nsm * 128 * 2 * 2.07e9 / 1e12)}}
+        if not args.no_tolerance:
+            wt = w.with_(eps=1e-4, max_iters=20000)
+            out2 = s.alloc_result(1, w.S, 20000)
+            mt = _timed_solve(s, wt, tensors, out2)
+            line["to_tolerance"] = {"eps": 1e-4, "cap": 20000, "ms": mt, "iterations": int(out2["iters"][0]),
+                                    "status": int(out2["status"][0]), "r_primal": float(out2["r_primal"][0]),
+                                    "r_dual": float(out2["r_dual"][0])}
+        print(json.dumps({"suite": "general (N=100000, numerical step)", "segments": int(w.S), prec: line}),
+              flush=True)
         s.close()
 
 

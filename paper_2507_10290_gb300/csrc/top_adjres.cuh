@@ -138,10 +138,24 @@ __global__ void __launch_bounds__(256, 1) adjoint_resident_kernel(const AdjResAr
 #pragma unroll
     for (int q = 0; q < NG; ++q) G[q] = R(0);
 #pragma unroll
-    for (int r = 0; r < NC; ++r) s[r] = R(0);
+    for (int r = 0; r < NC; ++r) s[r] = R(r == 0);  // s_0 = 1 in every thread
   }
 #pragma unroll
   for (int r = 0; r < ND; ++r) fs[r] = R(fact(r)) * s[r];
+  // the local step's coefficients (Eq. 18a) from the start- and end-side targets of
+  // the three axes (the resident kernel's maps: Taylor shift, packed pairs)
+  auto local_coeffs = [&](const R *tS, size_t strS, const R *tE, size_t strE, R (&ch)[AX][NC]) {
+    R wS[AX][ND], wE[AX][ND], rhs[AX][NC];
+#pragma unroll
+    for (int a = 0; a < AX; ++a)
+#pragma unroll
+      for (int r = 0; r < ND; ++r) {
+        wS[a][r] = fs[r] * tS[(size_t)(a * ND + r) * strS];
+        wE[a][r] = fs[r] * tE[(size_t)(a * ND + r) * strE];
+      }
+    consensus_rhs_shift(wS, wE, rho, rhs);
+    apply_g3(G, rhs, ch);
+  };
 
   // the initial state x^0 (Init of Algorithm 1), into the slots this thread owns
   auto init_state = [&]() {
@@ -173,22 +187,13 @@ __global__ void __launch_bounds__(256, 1) adjoint_resident_kernel(const AdjResAr
   auto forward = [&]() {
     R eE[AX][ND], eSv[AX][ND];
     if (valid) {
+      R ch[AX][NC];
+      local_coeffs(pS, 1, mE, 1, ch);
+      end_derivs_shift(ch, fs, eSv, eE);
 #pragma unroll
-      for (int a = 0; a < AX; ++a) {
-        R wS[ND], wE[ND], rhs[NC], ch[NC];
-#pragma unroll
-        for (int r = 0; r < ND; ++r) {
-          wS[r] = fs[r] * pS[a * ND + r];
-          wE[r] = s[r] * mE[a * ND + r];
-        }
-#pragma unroll
-        for (int q = 0; q < NC; ++q) rhs[q] = R(0);
-        consensus_rhs_f(wS, wE, rho, rhs);
-        apply_g(G, rhs, ch);
-        end_derivs_f(ch, s, fs, eSv[a], eE[a]);
+      for (int a = 0; a < AX; ++a)
 #pragma unroll
         for (int r = 0; r < ND; ++r) seS[l * NJ + a * ND + r] = eSv[a][r];
-      }
     }
     __syncthreads();
     if (valid) {
@@ -290,93 +295,82 @@ __global__ void __launch_bounds__(256, 1) adjoint_resident_kernel(const AdjResAr
         const R *eSb = seS + l * NJ;
         R tb_k = R(0);  // this iteration's dJ/dT terms, in the iteration precision
         const R iT = s[1];
+        // the iteration's coefficients, re-formed from the taped targets
+        R ch[AX][NC];
+        local_coeffs(tk + gS, Jn, tk + (size_t)NJ * Jn + gE, Jn, ch);
+        // the adjoint of the end derivatives e = s .* (M ch) with respect to ch (the
+        // transposed map takes r! s_r times the adjoints)
+        R xS[AX][ND], xE[AX][ND];
 #pragma unroll
-        for (int a = 0; a < AX; ++a) {
-          R w0[ND], w1[ND], wS[ND], wE[ND], rhs[NC], ch[NC];
-#pragma unroll
-          for (int r = 0; r < ND; ++r) {
-            w0[r] = tk[(size_t)(a * ND + r) * Jn + gS];              // p at the start slot
-            w1[r] = tk[(size_t)(NJ + a * ND + r) * Jn + gE];         // m at the end slot
-            wS[r] = fs[r] * w0[r];
-            wE[r] = s[r] * w1[r];
-          }
-#pragma unroll
-          for (int q = 0; q < NC; ++q) rhs[q] = R(0);
-          consensus_rhs_f(wS, wE, rho, rhs);
-          apply_g(G, rhs, ch);
-          // M ch rows without the s_r factors
-          R mcS[ND], mcE[ND];
+        for (int a = 0; a < AX; ++a)
 #pragma unroll
           for (int r = 0; r < ND; ++r) {
-            mcS[r] = R(fact(r)) * ch[r];
-            R acc = R(0);
-#pragma unroll
-            for (int q = r; q < NC; ++q) acc += R(falling(q, r)) * ch[q];
-            mcE[r] = acc;
+            xS[a][r] = fs[r] * eSb[a * ND + r];
+            xE[a][r] = fs[r] * eEb[a][r];
           }
-          // e = s .* (M ch): the s_r(T) factors
-          R sbS[ND], sbE[ND];
+        R chb[AX][NC];
+        consensus_rhs_shift(xS, xE, R(1), chb);
+        if (k == K - 1) {  // the cost seed: J = T^-7 ch^T Qh ch
+          const double dj = A.dJ[b];
+          const double t7 = double(s[7]);
 #pragma unroll
-          for (int r = 0; r < ND; ++r) {
-            tb_k += (eSb[a * ND + r] * mcS[r] + eEb[a][r] * mcE[r]) * (-R(r) * s[r] * iT);
-            sbS[r] = s[r] * eSb[a * ND + r];
-            sbE[r] = s[r] * eEb[a][r];
-          }
-          R chb[NC];
-#pragma unroll
-          for (int q = 0; q < NC; ++q) chb[q] = R(0);
-          consensus_rhs(sbS, sbE, R(1), chb);
-          if (k == K - 1) {  // the cost seed: J = T^-7 ch^T Qh ch
-            const double dj = A.dJ[b];
-            const double t7 = double(s[7]);
+          for (int a = 0; a < AX; ++a) {
             double cqc = 0.0;
 #pragma unroll
             for (int k1q = PO; k1q < NC; ++k1q) {
               double acc = 0.0;
 #pragma unroll
-              for (int k2 = PO; k2 < NC; ++k2) acc += qhat(k1q, k2) * double(ch[k2]);
-              chb[k1q] += R(dj * 2.0 * t7 * acc);
-              cqc += double(ch[k1q]) * acc;
+              for (int k2 = PO; k2 < NC; ++k2) acc += qhat(k1q, k2) * double(ch[a][k2]);
+              chb[a][k1q] += R(dj * 2.0 * t7 * acc);
+              cqc += double(ch[a][k1q]) * acc;
             }
             tbar += dj * (-7.0) * t7 / double(Tq) * cqc;
           }
-          R rb[NC];
-          apply_g(G, chb, rb);
+        }
+        R rb[AX][NC];
+        apply_g3(G, chb, rb);
+#pragma unroll
+        for (int a = 0; a < AX; ++a) {
+          // M ch and M rb without the s_r factors: start rows r! x_r, end rows r! (x shifted by one)_r
+          R mcE[NC], mrb[NC];
+#pragma unroll
+          for (int q = 0; q < NC; ++q) { mcE[q] = ch[a][q]; mrb[q] = rb[a][q]; }
+          taylor_shift(mcE);
+          taylor_shift(mrb);
+          // e = s .* (M ch): the s_r(T) factors
+#pragma unroll
+          for (int r = 0; r < ND; ++r)
+            tb_k += (eSb[a * ND + r] * (R(fact(r)) * ch[a][r]) + eEb[a][r] * (R(fact(r)) * mcE[r])) *
+                    (-R(r) * s[r] * iT);
           // G(T) = K(T)^-1:  -rb^T K'(T) ch,  K' = -14 T^-8 Qh + rho sum_r (-2 r s_r^2 / T) (rows of M)
-          {
-            R rqc = R(0);
+          R rqc = R(0);
 #pragma unroll
-            for (int k1q = PO; k1q < NC; ++k1q) {
-              R acc = R(0);
+          for (int k1q = PO; k1q < NC; ++k1q) {
+            R acc = R(0);
 #pragma unroll
-              for (int k2 = PO; k2 < NC; ++k2) acc += R(qhat(k1q, k2)) * ch[k2];
-              rqc += rb[k1q] * acc;
-            }
-            R kp = R(-14) * s[7] * iT * rqc;
-#pragma unroll
-            for (int r = 1; r < ND; ++r) {
-              const R c2 = R(-2 * r) * s[r] * s[r] * iT;
-              if (!(first && r >= PO)) kp += rho * c2 * (R(fact(r)) * rb[r]) * mcS[r];
-              if (!(last && r >= PO)) {
-                R mr = R(0);
-#pragma unroll
-                for (int q = r; q < NC; ++q) mr += R(falling(q, r)) * rb[q];
-                kp += rho * c2 * mr * mcE[r];
-              }
-            }
-            tb_k -= kp;
+            for (int k2 = PO; k2 < NC; ++k2) acc += R(qhat(k1q, k2)) * ch[a][k2];
+            rqc += rb[a][k1q] * acc;
           }
+          R kp = R(-14) * s[7] * iT * rqc;
+#pragma unroll
+          for (int r = 1; r < ND; ++r) {
+            const R c2 = R(-2 * r) * s[r] * s[r] * iT;
+            const R fr = R(fact(r));
+            if (!(first && r >= PO)) kp += rho * c2 * (fr * rb[a][r]) * (fr * ch[a][r]);
+            if (!(last && r >= PO)) kp += rho * c2 * (fr * mrb[r]) * (fr * mcE[r]);
+          }
+          tb_k -= kp;
           // the targets: w = s .* (rho M rb) (masked rows are constants)
 #pragma unroll
           for (int r = 0; r < ND; ++r) {
-            R obS = rho * R(fact(r)) * rb[r];
-            R acc = R(0);
-#pragma unroll
-            for (int q = r; q < NC; ++q) acc += R(falling(q, r)) * rb[q];
-            R obE = rho * acc;
+            const R fr = R(fact(r));
+            R obS = rho * fr * rb[a][r];
+            R obE = rho * fr * mrb[r];
             if (first && r >= PO) obS = R(0);
             if (last && r >= PO) obE = R(0);
-            tb_k += (obS * w0[r] + obE * w1[r]) * (-R(r) * s[r] * iT);
+            const R w0 = tk[(size_t)(a * ND + r) * Jn + gS];       // p at the start slot
+            const R w1 = tk[(size_t)(NJ + a * ND + r) * Jn + gE];  // m at the end slot
+            tb_k += (obS * w0 + obE * w1) * (-R(r) * s[r] * iT);
             pbS[a * ND + r] += s[r] * obS;
             mbE[a * ND + r] += s[r] * obE;
           }
