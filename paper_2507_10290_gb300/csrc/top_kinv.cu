@@ -93,10 +93,11 @@ __device__ __forceinline__ void add_rho_terms(const DevProblem &p, const double 
     }
     if (!(last && q >= PO)) {
       const double w = rho * s[q] * s[q];
+      // F(r,q) F(c,q) is an integer below 2^25, formed at compile time: one FMA per entry
 #pragma unroll
       for (int r = q; r < NC; ++r)
 #pragma unroll
-        for (int c = q; c <= r; ++c) A[lidx(r, c)] += w * double(falling(r, q)) * double(falling(c, q));
+        for (int c = q; c <= r; ++c) A[lidx(r, c)] += w * double(falling(r, q) * falling(c, q));
     }
   }
   if (SAMPLES && p.inner == 0) {
@@ -165,14 +166,18 @@ __device__ __forceinline__ bool equil_chol_inv(double (&A)[NG], double (&d)[NC])
 // written to rows base + gidx(k, l) of the [rows][S] output
 __device__ __forceinline__ void store_inverse(const double (&A)[NG], const double (&d)[NC], int S, int g, int base,
                                               float *G32, double *G64) {
+  double X[NG];  // L^-1 D: column k of L^-1 times d_k, so K^-1 = X^T X
+#pragma unroll
+  for (int q = 0; q < NC; ++q)
+#pragma unroll
+    for (int k = 0; k <= q; ++k) X[lidx(q, k)] = A[lidx(q, k)] * d[k];
 #pragma unroll
   for (int k = 0; k < NC; ++k)
 #pragma unroll
     for (int l = k; l < NC; ++l) {
-      double a = 0.0;
+      double v = 0.0;
 #pragma unroll
-      for (int q = l; q < NC; ++q) a += A[lidx(q, k)] * A[lidx(q, l)];
-      const double v = d[k] * a * d[l];
+      for (int q = l; q < NC; ++q) v += X[lidx(q, k)] * X[lidx(q, l)];
       const size_t idx = size_t(base + gidx(k, l)) * S + g;
       if (G64) G64[idx] = v;
       if (G32) G32[idx] = float(v);
@@ -226,10 +231,11 @@ __global__ void __launch_bounds__(128) kinv_kernel(const DevProblem p, double rh
       continue;
     }
     double A[NG];
+    const double t7x2 = 2.0 * s[7];  // the cost block 2 T^-7 Qh lives on coefficients 4..7
 #pragma unroll
     for (int r = 0; r < NC; ++r)
 #pragma unroll
-      for (int c = 0; c <= r; ++c) A[lidx(r, c)] = 2.0 * s[7] * qhat(r, c);
+      for (int c = 0; c <= r; ++c) A[lidx(r, c)] = (r >= PO && c >= PO) ? t7x2 * qhat(r, c) : 0.0;
     add_rho_terms<SAMPLES>(p, s, first, last, rho, A);
     double d[NC];
     if (!equil_chol_inv(A, d)) {
@@ -426,10 +432,11 @@ __global__ void __launch_bounds__(128) kinv_poly_kernel(const DevProblem p, doub
     for (int b = 0; b < 3; ++b) {
       const double nu = C3[b][b] > 0.0 ? C3[b][b] : 0.0;
       double A[NG];
+      const double t7x2 = 2.0 * s[7];
 #pragma unroll
       for (int r = 0; r < NC; ++r)
 #pragma unroll
-        for (int c = 0; c <= r; ++c) A[lidx(r, c)] = 2.0 * s[7] * qhat(r, c);
+        for (int c = 0; c <= r; ++c) A[lidx(r, c)] = (r >= PO && c >= PO) ? t7x2 * qhat(r, c) : 0.0;
       add_rho_terms<SAMPLES>(p, s, first, last, rho, A);
       if (nu > 0.0) add_sample_rows(A, p.M_poly, 0, rho * nu);
       double d[NC];
