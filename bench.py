@@ -570,21 +570,15 @@ def run_suite(args):
                                           w.start_state[b], w.end_state[b])
         return out
 
-    def handoff(w, o_solve, eps, cap, cev=10):
-        """Time to eps: FP32 until its residuals stop falling, then FP64 from the
-        FP32 state (top_resume), against FP64 alone; residuals every `cev`
-        iterations in both.  The switch point K1 is the iteration of the FP32
-        run's smallest residual (max of ||r_p||, ||r_d|| over N eps), read from
-        an untimed FP32 run with history."""
+    def handoff(w, o_solve, eps, cap, cev=10, stall=50):
+        """Time to eps: FP32 until the stall rule stops it (top_problem.stall_checks:
+        no 1 % better residual ratio in `stall` checks, decided inside the
+        kernel), then FP64 from the FP32 state (top_resume), against FP64 alone;
+        residuals every `cev` iterations in both."""
         wt = w.with_(eps=eps, max_iters=cap)
         s32 = top.Solver(max_batch=w.B, max_segments=w.S, precision="fp32", max_samples=16)
         s64 = top.Solver(max_batch=w.B, max_segments=w.S, precision="fp64", max_samples=16)
         t32, t64 = s32.device_inputs(w), s64.device_inputs(w)
-        h = s32.solve(wt, tensors=t32, history=True, check_every=cev)["history"].cpu().numpy()[:, 0, :]
-        tol = np.diff(w.seg_offset)[0] * eps
-        ratio = np.max(h, axis=1) / tol
-        ok = np.isfinite(ratio)
-        K1 = int(cev * (np.argmin(np.where(ok, ratio, np.inf)) // cev + 1)) if ok.any() else cap
         st = torch.cuda.current_stream()
 
         def timed(fn):
@@ -598,16 +592,18 @@ def run_suite(args):
 
         s32.resume(wt, tensors=t32, max_iters=5)  # warm-up of both handles
         s64.resume(wt, tensors=t64, max_iters=5, save=False)
-        (a, state), ms32 = timed(lambda: s32.resume(wt, tensors=t32, eps=eps, max_iters=K1, check_every=cev))
+        (a, state), ms32 = timed(lambda: s32.resume(wt, tensors=t32, eps=eps, max_iters=cap, check_every=cev,
+                                                     stall_checks=stall))
         it32 = int(a["iters"][0])
-        done32 = int(a["status"][0]) == 0
-        ms64, it64, status = 0.0, 0, int(a["status"][0])
-        if not done32:
+        status32 = int(a["status"][0])
+        ms64, it64, status = 0.0, 0, status32
+        if status32 != 0 and it32 < cap:
             (b, _), ms64 = timed(lambda: s64.resume(wt, start=state, tensors=t64, eps=eps, max_iters=cap - it32,
                                                     check_every=cev, save=False))
             it64, status = int(b["iters"][0]), int(b["status"][0])
         c, ms_alone = timed(lambda: s64.solve(wt, tensors=t64, eps=eps, max_iters=cap, check_every=cev))
-        res = {"eps": eps, "cap": cap, "check_every": cev, "switch_iteration": K1,
+        res = {"eps": eps, "cap": cap, "check_every": cev, "stall_checks": stall,
+               "fp32_status": status32, "switch_iteration": it32,
                "fp32_ms": ms32, "fp32_iterations": it32, "fp64_ms": ms64, "fp64_iterations": it64,
                "total_ms": ms32 + ms64, "status": status,
                "fp64_alone_ms": ms_alone, "fp64_alone_iterations": int(c["iters"][0]),

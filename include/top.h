@@ -68,6 +68,9 @@ extern "C" {
 #define TOP_CONVERGED      0  /* ||r_p|| < N eps and ||r_d|| < N eps (Eq. 21) */
 #define TOP_NOT_CONVERGED  1  /* max_iters reached first (always the case for eps = 0) */
 #define TOP_NONFINITE      2  /* a residual became NaN or Inf; results are those of that iteration */
+#define TOP_STALLED        3  /* the stall rule stopped it (top_problem.stall_checks): the iteration
+                                 precision's residual floor is above N eps; results and the saved
+                                 state (top_resume) are those of that iteration */
 
 enum top_precision { TOP_FP32 = 0, TOP_FP64 = 1 };     /* arithmetic of the iteration */
 enum top_mode      { TOP_PIN = 0, TOP_FREE = 1 };      /* interior waypoints pinned or free */
@@ -168,6 +171,12 @@ typedef struct top_problem {
   int32_t F_poly;             /* faces per segment (>= 1 when M_poly > 0) */
   const double *poly_n;       /* [S][F_poly][3] face normals (any length; rows scale with it) */
   const double *poly_h;       /* [S][F_poly] offsets */
+  /* Stall rule (an extension for precision hand-off; the paper has none): with
+   * eps > 0, a trajectory whose residual ratio max(||r_p||, ||r_d||) / (N eps)
+   * has not fallen below 0.99 of its best value for stall_checks consecutive
+   * residual checks stops with status TOP_STALLED (0 = off).  Resident and
+   * cluster-resident forms; the streaming form ignores it. */
+  int32_t stall_checks;
 } top_problem;
 
 /* Outputs (same memory kind as the problem).  history may be NULL. */
@@ -177,7 +186,7 @@ typedef struct top_result {
   double *r_primal;  /* [B] ||r_p|| (Eq. 19) at the last evaluated iteration */
   double *r_dual;    /* [B] ||r_d|| (Eq. 20) at the last evaluated iteration */
   int32_t *iters;    /* [B] iterations run */
-  int32_t *status;   /* [B] TOP_CONVERGED | TOP_NOT_CONVERGED | TOP_NONFINITE */
+  int32_t *status;   /* [B] TOP_CONVERGED | TOP_NOT_CONVERGED | TOP_NONFINITE | TOP_STALLED */
   double *history;   /* optional [max_iters][B][2]: (||r_p||, ||r_d||) at every evaluated iteration
                         (entries of iterations that were not evaluated are left untouched) */
   double *rho;       /* optional [B]: rho after the last update (adaptive_rho), else the fixed rho */
@@ -300,9 +309,8 @@ int64_t top_launch_count(const top_handle *h);
  * Limits: S <= TOP_NOALLOC_MAX_SEGMENTS, B <= TOP_NOALLOC_MAX_BATCH and every
  * trajectory short enough for one CTA of the resident kernel; otherwise
  * TOP_E_LIMIT.  The first call on a device looks up the array's device
- * address (once, with that device current): make it before any stream
- * capture.  The address is kept for the life of the device's primary
- * context: do not call it on a device after cudaDeviceReset.  All calls share
+ * address (once, with that device current) and keeps it for the life of the
+ * device's primary context: do not call it on a device after cudaDeviceReset.  All calls share
  * the array; calls whose GPU work overlaps race on it and must be serialised
  * by the caller.  Synchronises `stream` like
  * top_solve.  Errors: TOP_E_INVAL, TOP_E_NOTSUP, TOP_E_LIMIT, TOP_E_NUMERIC,

@@ -286,7 +286,7 @@ int validate(const top_handle *h, const top_problem *pb, const top_result *res) 
   if (pb->inner != TOP_CLOSED_FORM && pb->inner != TOP_NUMERIC) return TOP_E_INVAL;
   if (!(pb->rho > 0.0) || !(pb->rho < 1e300)) return TOP_E_INVAL;
   if (!(pb->eps >= 0.0)) return TOP_E_INVAL;
-  if (pb->max_iters < 0 || pb->check_every < 0) return TOP_E_INVAL;
+  if (pb->max_iters < 0 || pb->check_every < 0 || pb->stall_checks < 0) return TOP_E_INVAL;
   if (pb->M_box < 0 || pb->M_ball < 0 || pb->M_vn < 0 || pb->M_gen < 0) return TOP_E_INVAL;
   const int mmax = std::max(std::max(pb->M_box, pb->M_ball), std::max(pb->M_vn, pb->M_gen));
   if (mmax > h->cfg.max_samples) return TOP_E_NOMEM;
@@ -565,7 +565,7 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
     }
   }
   DevProblem dp{};
-  dp.B = B; dp.S = S; dp.err = h->d_err;
+  dp.B = B; dp.S = S; dp.err = h->d_err; dp.stall = pb.stall_checks;
   dp.seg_offset = pb.seg_offset; dp.waypoints = pb.waypoints; dp.durations = pb.durations;
   dp.start_state = pb.start_state; dp.end_state = pb.end_state;
   dp.mode = pb.mode; dp.inner = pb.inner; dp.rho = pb.rho; dp.eps = pb.eps;

@@ -22,12 +22,12 @@
 //
 // Host code never uses the array's name as a device address (in host code it
 // is only a stand-in symbol): the first call on each device, with that device
-// current, looks the address up once with cudaGetSymbolAddress and keeps it;
-// make that first call before any stream capture.  The kept address belongs
-// to the device's primary context: it stays valid while that context lives,
-// which is the whole process unless the caller resets the device
-// (cudaDeviceReset), after which no call may be made on that device.  No
-// cudaMalloc, cudaFree or allocating library routine is called here.
+// current, looks the address up once with cudaGetSymbolAddress and keeps it.
+// The kept address belongs to the device's primary context: it stays valid
+// while that context lives, which is the whole process unless the caller
+// resets the device (cudaDeviceReset), after which no call may be made on
+// that device.  No cudaMalloc, cudaFree or allocating library routine is
+// called here.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -92,7 +92,7 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
   if (!pb || !res) return TOP_E_INVAL;
   if (precision != TOP_FP32 && precision != TOP_FP64) return TOP_E_INVAL;
   if (pb->memory != TOP_MEM_DEVICE) return TOP_E_NOTSUP;
-  if (pb->B < 0 || pb->max_iters < 0 || pb->check_every < 0 || !(pb->rho > 0.0) || !(pb->rho < 1e300) ||
+  if (pb->B < 0 || pb->max_iters < 0 || pb->check_every < 0 || pb->stall_checks < 0 || !(pb->rho > 0.0) || !(pb->rho < 1e300) ||
       !(pb->eps >= 0.0))
     return TOP_E_INVAL;
   if (pb->mode != TOP_PIN && pb->mode != TOP_FREE) return TOP_E_INVAL;
@@ -160,7 +160,7 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
   int *d_list = (int *)(base + kListOff);
   int *d_err = (int *)(base + kErrOff);
   DevProblem dp{};
-  dp.B = B; dp.S = S; dp.err = d_err;
+  dp.B = B; dp.S = S; dp.err = d_err; dp.stall = pb->stall_checks;
   dp.seg_offset = pb->seg_offset; dp.waypoints = pb->waypoints; dp.durations = pb->durations;
   dp.start_state = pb->start_state; dp.end_state = pb->end_state;
   dp.mode = pb->mode; dp.inner = pb->inner; dp.rho = pb->rho; dp.eps = pb->eps;

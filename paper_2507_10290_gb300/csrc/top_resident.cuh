@@ -87,6 +87,8 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   int *sflag = (int *)(smem + L.flag);
   double *srho = (double *)(smem + L.rho);  // per-trajectory rho (Eq. 22)
   double *sfac = (double *)(smem + L.fac);  // rho_old / rho_new of the last update
+  double *sbest = (double *)(smem + L.best);  // stall rule: best residual ratio so far
+  int *sstc = (int *)(smem + L.stc);           // stall rule: checks since it
 
   const R rho0 = R(p.rho);
   constexpr bool adapt = ADAPT;  // residual balancing of rho (Eq. 22); A.E is non-null
@@ -109,7 +111,10 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
     }
     soff[pk.ntraj] = acc;
   }
-  for (int t = l; t < ntp; t += C) { tr_rp[t] = 0.0; tr_rd[t] = 0.0; srho[t] = p.rho; sfac[t] = 1.0; }
+  for (int t = l; t < ntp; t += C) {
+    tr_rp[t] = 0.0; tr_rd[t] = 0.0; srho[t] = p.rho; sfac[t] = 1.0;
+    sbest[t] = 1e300; sstc[t] = 0;
+  }
   if (l == 0) *sflag = 0;
   for (int q = l; q < NJ * J; q += C) { sdz[q] = R(0); sp[q] = R(0); }
   for (int q = l; q < NJ * ntp; q += C) sm[q] = R(0);
@@ -400,6 +405,11 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
           int st = -1;
           if (!finite_d(rp) || !finite_d(rd)) st = 2;
           else if (p.eps > 0.0 && rp < tol && rd < tol) st = 0;
+          if (st < 0 && p.stall > 0 && p.eps > 0.0) {  // the stall rule (top_problem.stall_checks)
+            const double ratio = fmax(rp, rd) / tol;
+            if (ratio < 0.99 * sbest[t]) { sbest[t] = ratio; sstc[t] = 0; }
+            else if (++sstc[t] >= p.stall) st = 3;
+          }
           if (st >= 0) {
             sdone[t] = 1;
             res.iters[bb] = k + 1;

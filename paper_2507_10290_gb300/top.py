@@ -50,7 +50,7 @@ TOP_E_LIMIT = _K["TOP_E_LIMIT"]
 TOP_E_BOUNDS = _K["TOP_E_BOUNDS"]
 TOP_NOALLOC_MAX_SEGMENTS = _K["TOP_NOALLOC_MAX_SEGMENTS"]
 TOP_NOALLOC_MAX_BATCH = _K["TOP_NOALLOC_MAX_BATCH"]
-TOP_CONVERGED, TOP_NOT_CONVERGED, TOP_NONFINITE = 0, 1, 2
+TOP_CONVERGED, TOP_NOT_CONVERGED, TOP_NONFINITE, TOP_STALLED = 0, 1, 2, 3
 TOP_FP32, TOP_FP64 = 0, 1
 TOP_PIN, TOP_FREE = 0, 1
 TOP_CLOSED_FORM, TOP_NUMERIC = 0, 1
@@ -80,7 +80,8 @@ class top_problem(C.Structure):
                 ("lbfgs_mem", C.c_int32), ("lbfgs_max_iters", C.c_int32), ("lbfgs_tol", C.c_double),
                 ("adaptive_rho", C.c_int32), ("rho_mu", C.c_double), ("rho_tau_incr", C.c_double),
                 ("rho_tau_decr", C.c_double),
-                ("M_poly", C.c_int32), ("F_poly", C.c_int32), ("poly_n", C.c_void_p), ("poly_h", C.c_void_p)]
+                ("M_poly", C.c_int32), ("F_poly", C.c_int32), ("poly_n", C.c_void_p), ("poly_h", C.c_void_p),
+                ("stall_checks", C.c_int32)]
 
 
 class top_result(C.Structure):
@@ -295,7 +296,8 @@ class Solver:
             "poly_n": t(getattr(w, "poly_n", None)), "poly_h": t(getattr(w, "poly_h", None)),
         }
 
-    def make_problem(self, w, tensors, memory=TOP_MEM_DEVICE, max_iters=None, eps=None, check_every=1):
+    def make_problem(self, w, tensors, memory=TOP_MEM_DEVICE, max_iters=None, eps=None, check_every=1,
+                     stall_checks=0):
         pb = top_problem()
         pb.B = int(np.asarray(w.seg_offset).shape[0] - 1)
         pb.memory = memory
@@ -327,6 +329,7 @@ class Solver:
         pb.rho_tau_decr = float(getattr(w, "rho_tau_decr", 0.0) or 0.0)
         pb.M_poly = int(getattr(w, "M_poly", 0) or 0)
         pb.F_poly = int(getattr(w, "F_poly", 0) or 0)
+        pb.stall_checks = int(stall_checks)
         return pb
 
     def alloc_result(self, B: int, S: int, max_iters: int = 0, history: bool = False, device="cuda"):
@@ -378,16 +381,17 @@ class Solver:
         return x
 
     def resume(self, w, start=None, save=True, max_iters=None, eps=None, check_every: int = 1, stream=None,
-               tensors=None, out=None):
+               tensors=None, out=None, stall_checks: int = 0, history: bool = False):
         """top_resume: solve from the state `start` (None: Init) and return (outputs, saved state or None)."""
         torch = self.torch
         tensors = tensors if tensors is not None else self.device_inputs(w)
         K = int(w.max_iters if max_iters is None else max_iters)
         B = int(np.asarray(w.seg_offset).shape[0] - 1)
         S = int(np.asarray(w.seg_offset)[-1])
-        out = out if out is not None else self.alloc_result(B, S, K)
+        out = out if out is not None else self.alloc_result(B, S, K, history)
         saved = self.alloc_state(w) if save else None
-        pb = self.make_problem(w, tensors, TOP_MEM_DEVICE, max_iters=K, eps=eps, check_every=check_every)
+        pb = self.make_problem(w, tensors, TOP_MEM_DEVICE, max_iters=K, eps=eps, check_every=check_every,
+                               stall_checks=stall_checks)
         s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
         rc = top_resume(self.handle, pb, self.state_struct(start), self.result_struct(out), self.state_struct(saved), s)
         if rc != TOP_OK:
@@ -395,7 +399,7 @@ class Solver:
         return out, saved
 
     def solve(self, w, history: bool = False, max_iters=None, eps=None, check_every: int = 1, stream=None,
-              tensors=None, out=None):
+              tensors=None, out=None, stall_checks: int = 0):
         """Solve a Workload on the GPU; returns a dict of device tensors."""
         torch = self.torch
         tensors = tensors if tensors is not None else self.device_inputs(w)
@@ -403,7 +407,8 @@ class Solver:
         B = int(np.asarray(w.seg_offset).shape[0] - 1)
         S = int(np.asarray(w.seg_offset)[-1])
         out = out if out is not None else self.alloc_result(B, S, K, history)
-        pb = self.make_problem(w, tensors, TOP_MEM_DEVICE, max_iters=K, eps=eps, check_every=check_every)
+        pb = self.make_problem(w, tensors, TOP_MEM_DEVICE, max_iters=K, eps=eps, check_every=check_every,
+                               stall_checks=stall_checks)
         r = self.result_struct(out)
         s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
         rc = top_solve(self.handle, pb, r, s)

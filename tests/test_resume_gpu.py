@@ -126,3 +126,56 @@ def test_resume_rejects_what_it_cannot_save(T):
         st.resume(w)
     assert e.value.code == T.TOP_E_NOTSUP
     st.close()
+
+
+def _stall_stop(history, tol, cev, W_, cap):
+    """The stall rule written out: at each check iteration k (k + 1 a multiple
+    of cev), the ratio max(||r_p||, ||r_d||) / tol becomes the best if below 0.99
+    of the best so far, else one more check without progress; the run stops
+    after W_ such checks in a row.  Returns the iteration count at the stop."""
+    best, cnt = 1e300, 0
+    for k in range(cev - 1, cap, cev):
+        rp, rd = history[k]
+        if rp < tol and rd < tol:
+            return None  # converged first
+        ratio = max(rp, rd) / tol
+        if ratio < 0.99 * best:
+            best, cnt = ratio, 0
+        else:
+            cnt += 1
+            if cnt >= W_:
+                return k + 1
+    return None
+
+
+@pytest.mark.parametrize("case", ["single_box", "corridor"])
+def test_stall_rule_stops_where_its_definition_says(T, case):
+    """FP32 at eps = 1e-4 does not reach the tolerance on these workloads (its
+    residual floor): the stall rule stops the trajectory with TOP_STALLED at
+    the iteration the rule's definition gives from the recorded residual
+    history (resident packs for single_box, a cluster for the corridor), and
+    FP64 resumed from that state converges."""
+    w = W.single_box() if case == "single_box" else W.corridor(N=600)
+    cev, W_, cap, eps = 10, 30, 20000, 1e-4
+    s32 = _solver(T, w, "fp32")
+    a, st = s32.resume(w, eps=eps, max_iters=cap, check_every=cev, stall_checks=W_, history=True)
+    s32.close()
+    a = _np(a)
+    assert int(a["status"][0]) == T.TOP_STALLED, a["status"]
+    K1 = int(a["iters"][0])
+    assert K1 == _stall_stop(a["history"][:, 0, :], w.S * eps, cev, W_, cap)
+    s64 = _solver(T, w, "fp64")
+    b, _ = s64.resume(w, start=st, eps=eps, max_iters=cap - K1, check_every=cev, save=False)
+    s64.close()
+    assert int(_np(b)["status"][0]) == T.TOP_CONVERGED
+
+
+def test_stall_rule_off_and_invalid(T):
+    w = W.single_box().with_(max_iters=300)
+    s = _solver(T, w, "fp32")
+    g = _np(s.solve(w, eps=1e-4, check_every=10))  # stall_checks = 0: the run goes to max_iters
+    assert int(g["status"][0]) == T.TOP_NOT_CONVERGED and int(g["iters"][0]) == 300
+    with pytest.raises(T.TopError) as e:
+        s.solve(w, eps=1e-4, stall_checks=-1)
+    assert e.value.code == T.TOP_E_INVAL
+    s.close()
