@@ -570,7 +570,7 @@ def run_suite(args):
                                           w.start_state[b], w.end_state[b])
         return out
 
-    def handoff(w, o_solve, eps, cap, cev=10, stall=50):
+    def handoff(w, o_solve, eps, cap, cev=10, stall=200):
         """Time to eps: FP32 until the stall rule stops it (top_problem.stall_checks:
         no 1 % better residual ratio in `stall` checks, decided inside the
         kernel), then FP64 from the FP32 state (top_resume), against FP64 alone;
