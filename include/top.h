@@ -172,10 +172,10 @@ typedef struct top_problem {
   const double *poly_n;       /* [S][F_poly][3] face normals (any length; rows scale with it) */
   const double *poly_h;       /* [S][F_poly] offsets */
   /* Stall rule (an extension for precision hand-off; the paper has none): with
-   * eps > 0, a trajectory whose residual ratio max(||r_p||, ||r_d||) / (N eps)
-   * has not fallen below 0.99 of its best value for stall_checks consecutive
-   * residual checks stops with status TOP_STALLED (0 = off).  Resident and
-   * cluster-resident forms; the streaming form ignores it. */
+   * eps > 0, a trajectory for which neither ||r_p|| nor ||r_d|| has fallen
+   * below 0.99 of its best value for stall_checks consecutive residual checks
+   * stops with status TOP_STALLED (0 = off).  Resident and cluster-resident
+   * forms; the streaming form ignores it. */
   int32_t stall_checks;
 } top_problem;
 

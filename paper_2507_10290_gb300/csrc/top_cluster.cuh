@@ -220,8 +220,8 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
   const int cev = p.check_every > 0 ? p.check_every : 1;
   const bool periodic = p.eps > 0.0 || res.history != nullptr;
   int done = 0;     // the stop decision, identical in every CTA of the cluster
-  double best = 1e300;  // stall rule (rank 0, thread 0): best residual ratio so far
-  int stc = 0;          // and the checks since it
+  double best_p = 1e300, best_d = 1e300;  // stall rule (rank 0, thread 0): best ||r_p||, ||r_d|| so far
+  int stc = 0;                             // and the checks since either improved
   double rp_last = 0.0, rd_last = 0.0;
   const int warp = tid >> 5, lane = tid & 31;
   const unsigned vmask = __ballot_sync(0xffffffffu, valid);  // lanes of valid segments (a prefix of the warp)
@@ -404,8 +404,10 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) cluster_kernel(
         if (!finite_d(rp) || !finite_d(rd)) st = 2;
         else if (p.eps > 0.0 && rp < tol && rd < tol) st = 0;
         if (st < 0 && p.stall > 0 && p.eps > 0.0) {  // the stall rule (top_problem.stall_checks)
-          const double ratio = fmax(rp, rd) / tol;
-          if (ratio < 0.99 * best) { best = ratio; stc = 0; }
+          const bool bp = rp < 0.99 * best_p, bd = rd < 0.99 * best_d;
+          if (bp) best_p = rp;
+          if (bd) best_d = rd;
+          if (bp || bd) stc = 0;
           else if (++stc >= p.stall) st = 3;
         }
         part[6] = 1.0;

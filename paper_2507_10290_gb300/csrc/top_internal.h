@@ -40,7 +40,7 @@ struct DevProblem {
   double rho_mu, rho_incr, rho_decr;
   int M_poly, F_poly; const double *poly_n, *poly_h;  // polytope corridors
   int *err;       // error word: 1 invalid input, 2 not positive definite, 4 bounds (checked build)
-  int stall;      // stall rule: checks without a 1 % better residual ratio before TOP_STALLED (0 = off)
+  int stall;      // stall rule: checks in which neither residual fell 1 % below its best before TOP_STALLED (0 = off)
 };
 
 // Bounds checks of the checked build (TOP_CHECKED, libtop_checked.so): every
@@ -123,7 +123,7 @@ struct ResLayout {
   size_t red_rp, red_rd, tr_rp, tr_rd;           // double arrays
   size_t p, m, zP, eS, dz, ybox, qball, qvn, tabB, tabQ, tabV, tabP, ch;  // element arrays
   size_t off, done, tid, flag;                   // int arrays
-  size_t rho, fac, best;                         // double arrays (per trajectory)
+  size_t rho, fac, best;                         // double arrays (per trajectory; best: 2 per trajectory)
   size_t stc;                                    // int array (per trajectory): checks since the best ratio
   size_t total;
 };
@@ -168,7 +168,7 @@ __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, 
   o = align_up(o, 8);
   L.rho = o;    o += sizeof(double) * ntp;
   L.fac = o;    o += sizeof(double) * ntp;
-  L.best = o;   o += sizeof(double) * ntp;
+  L.best = o;   o += sizeof(double) * 2 * ntp;
   L.stc = o;    o += sizeof(int) * ntp;
   L.total = align_up(o, 16);
   return L;

@@ -87,8 +87,8 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   int *sflag = (int *)(smem + L.flag);
   double *srho = (double *)(smem + L.rho);  // per-trajectory rho (Eq. 22)
   double *sfac = (double *)(smem + L.fac);  // rho_old / rho_new of the last update
-  double *sbest = (double *)(smem + L.best);  // stall rule: best residual ratio so far
-  int *sstc = (int *)(smem + L.stc);           // stall rule: checks since it
+  double *sbest = (double *)(smem + L.best);  // stall rule: best ||r_p||, ||r_d|| so far ([trajectory][2])
+  int *sstc = (int *)(smem + L.stc);           // stall rule: checks since either improved
 
   const R rho0 = R(p.rho);
   constexpr bool adapt = ADAPT;  // residual balancing of rho (Eq. 22); A.E is non-null
@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   }
   for (int t = l; t < ntp; t += C) {
     tr_rp[t] = 0.0; tr_rd[t] = 0.0; srho[t] = p.rho; sfac[t] = 1.0;
-    sbest[t] = 1e300; sstc[t] = 0;
+    sbest[2 * t] = sbest[2 * t + 1] = 1e300;
+    sstc[t] = 0;
   }
   if (l == 0) *sflag = 0;
   for (int q = l; q < NJ * J; q += C) { sdz[q] = R(0); sp[q] = R(0); }
@@ -406,8 +407,10 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
           if (!finite_d(rp) || !finite_d(rd)) st = 2;
           else if (p.eps > 0.0 && rp < tol && rd < tol) st = 0;
           if (st < 0 && p.stall > 0 && p.eps > 0.0) {  // the stall rule (top_problem.stall_checks)
-            const double ratio = fmax(rp, rd) / tol;
-            if (ratio < 0.99 * sbest[t]) { sbest[t] = ratio; sstc[t] = 0; }
+            const bool bp = rp < 0.99 * sbest[2 * t], bd = rd < 0.99 * sbest[2 * t + 1];
+            if (bp) sbest[2 * t] = rp;
+            if (bd) sbest[2 * t + 1] = rd;
+            if (bp || bd) sstc[t] = 0;
             else if (++sstc[t] >= p.stall) st = 3;
           }
           if (st >= 0) {

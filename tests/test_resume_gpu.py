@@ -130,17 +130,22 @@ def test_resume_rejects_what_it_cannot_save(T):
 
 def _stall_stop(history, tol, cev, W_, cap):
     """The stall rule written out: at each check iteration k (k + 1 a multiple
-    of cev), the ratio max(||r_p||, ||r_d||) / tol becomes the best if below 0.99
-    of the best so far, else one more check without progress; the run stops
-    after W_ such checks in a row.  Returns the iteration count at the stop."""
-    best, cnt = 1e300, 0
+    of cev), each of ||r_p||, ||r_d|| that falls below 0.99 of its own best so
+    far becomes the new best; a check where neither does is one more check
+    without progress; the run stops after W_ such checks in a row.  Returns the
+    iteration count at the stop."""
+    bp, bd, cnt = 1e300, 1e300, 0
     for k in range(cev - 1, cap, cev):
         rp, rd = history[k]
         if rp < tol and rd < tol:
             return None  # converged first
-        ratio = max(rp, rd) / tol
-        if ratio < 0.99 * best:
-            best, cnt = ratio, 0
+        ip, id_ = rp < 0.99 * bp, rd < 0.99 * bd
+        if ip:
+            bp = rp
+        if id_:
+            bd = rd
+        if ip or id_:
+            cnt = 0
         else:
             cnt += 1
             if cnt >= W_:
