@@ -52,6 +52,7 @@ struct top_handle {
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   Pack *d_packs = nullptr;    // [max_segments]
   int *d_err = nullptr;       // error flag of the precompute kernel
+  double *d_stall = nullptr;  // [max_batch][3] stall-rule state of the resident kernel
   // staging for TOP_MEM_HOST problems
   unsigned char *d_stage = nullptr;
   size_t stage_bytes = 0;
@@ -375,6 +376,7 @@ void top_destroy(top_handle *h) {
   if (h->join_ev) cudaEventDestroy(h->join_ev);
   cudaFree(h->d_packs);
   cudaFree(h->d_err);
+  cudaFree(h->d_stall);
   cudaFree(h->d_stage);
   cudaFree(h->d_stream);
   cudaFreeHost(h->h_off);
@@ -416,6 +418,7 @@ int top_create(const top_config *cfg, top_handle **out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->G, (size_t)NG * S * rbytes(h));
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_packs, sizeof(Pack) * std::max(S, B));
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_stall, sizeof(double) * 3 * B);
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_copy, sizeof(int) * (2 * (size_t)S + 1));
   if (e == cudaSuccess) {
     h->stage_bytes = stage_plan((int)B, (int)S).total;
@@ -765,6 +768,7 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
     ResidentArgs ra{};
     ra.p = dp; ra.r = dr; ra.G = h->G; ra.packs = h->d_packs; ra.traj_list = h->d_tlist; ra.ntp = ntp;
     ra.tc = tc;
+    ra.stall = pb.stall_checks > 0 ? h->d_stall : nullptr;
     ra.E = adapt ? h->E : nullptr;
     ra.from = fromv; ra.to = tov;
     Range r1("resident packs");

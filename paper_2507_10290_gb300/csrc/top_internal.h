@@ -101,6 +101,7 @@ struct ResidentArgs {
   const int *traj_list; // trajectory ids, grouped by pack
   int ntp;              // trajectory slots per pack (shared-memory sizing)
   int tc;               // 1: the G product of warps that share one inverse on the tensor cores
+  double *stall;        // [B][3] stall-rule state (best ||r_p||, best ||r_d||, checks since), or null
 };
 
 // Cluster-resident form (top_cluster.cuh): one trajectory per thread-block
@@ -123,8 +124,7 @@ struct ResLayout {
   size_t red_rp, red_rd, tr_rp, tr_rd;           // double arrays
   size_t p, m, zP, eS, dz, ybox, qball, qvn, tabB, tabQ, tabV, tabP, ch;  // element arrays
   size_t off, done, tid, flag;                   // int arrays
-  size_t rho, fac, best;                         // double arrays (per trajectory; best: 2 per trajectory)
-  size_t stc;                                    // int array (per trajectory): checks since the best ratio
+  size_t rho, fac;                               // double arrays (per trajectory)
   size_t total;
 };
 
@@ -168,13 +168,13 @@ __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, 
   o = align_up(o, 8);
   L.rho = o;    o += sizeof(double) * ntp;
   L.fac = o;    o += sizeof(double) * ntp;
-  L.best = o;   o += sizeof(double) * 2 * ntp;
-  L.stc = o;    o += sizeof(int) * ntp;
   L.total = align_up(o, 16);
   return L;
 }
 
-// the layout of the resident kernel (top_resident.cuh)
+// the layout of the resident kernel (top_resident.cuh); at 512 FP32 segments
+// with 128 trajectory slots and no sample rows it takes 231,952 of the
+// 232,448 bytes a CTA may opt in to (tests/test_parity_gpu.py checks it fits)
 __host__ __device__ inline ResLayout res_layout_resident(int C, int ntp, int Mb, int Mq, int Mv, int rb,
                                                          bool tc = false) {
   return res_layout(C, ntp, Mb, Mq, Mv, rb, 0, true, tc);

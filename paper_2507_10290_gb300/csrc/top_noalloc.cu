@@ -51,7 +51,8 @@ constexpr size_t kPackBytes = sizeof(Pack) * kMaxBatch;                 // at mo
 constexpr size_t kListOff = round256(kPackOff + kPackBytes);
 constexpr size_t kListBytes = sizeof(int) * kMaxBatch;                  // trajectory list of the packs
 constexpr size_t kErrOff = round256(kListOff + kListBytes);
-constexpr size_t kScratchBytes = kErrOff + 256;
+constexpr size_t kStallOff = round256(kErrOff + 256);                    // [B][3] stall-rule state
+constexpr size_t kScratchBytes = kStallOff + sizeof(double) * 3 * kMaxBatch;
 
 constexpr int kMaxDevices = 64;
 struct DevSlot {
@@ -193,6 +194,7 @@ extern "C" int top_solve_noalloc(const top_problem *pb, top_result *res, int pre
                                  (fam & FAM_VN) ? pb->M_vn : 0, rb);
   ResidentArgs ra{};
   ra.p = dp; ra.r = dr; ra.G = G; ra.packs = d_packs; ra.traj_list = d_list; ra.ntp = ntp;
+  ra.stall = pb->stall_checks > 0 ? (double *)(base + kStallOff) : nullptr;
   const int e = fp64 ? launch_resident_f64(ra, npack, C, L.total, fam, st)
                      : launch_resident_f32(ra, npack, C, L.total, fam, st);
   if (e != 0) return TOP_E_CUDA;

@@ -87,8 +87,6 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   int *sflag = (int *)(smem + L.flag);
   double *srho = (double *)(smem + L.rho);  // per-trajectory rho (Eq. 22)
   double *sfac = (double *)(smem + L.fac);  // rho_old / rho_new of the last update
-  double *sbest = (double *)(smem + L.best);  // stall rule: best ||r_p||, ||r_d|| so far ([trajectory][2])
-  int *sstc = (int *)(smem + L.stc);           // stall rule: checks since either improved
 
   const R rho0 = R(p.rho);
   constexpr bool adapt = ADAPT;  // residual balancing of rho (Eq. 22); A.E is non-null
@@ -113,8 +111,6 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   }
   for (int t = l; t < ntp; t += C) {
     tr_rp[t] = 0.0; tr_rd[t] = 0.0; srho[t] = p.rho; sfac[t] = 1.0;
-    sbest[2 * t] = sbest[2 * t + 1] = 1e300;
-    sstc[t] = 0;
   }
   if (l == 0) *sflag = 0;
   for (int q = l; q < NJ * J; q += C) { sdz[q] = R(0); sp[q] = R(0); }
@@ -131,6 +127,14 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   // the trajectories' segments fill the pack exactly (else the whole block ends)
   if (!TOP_IN_BOUNDS(p.err, soff[pk.ntraj] == pk.nseg)) return;
   for (int t = l; t < pk.ntraj; t += C) sdone[t] = (soff[t + 1] == soff[t]) ? 1 : 0;
+  // stall-rule state of the pack's trajectories (global memory: read and written by the lane
+  // that reduces the trajectory's residuals, on check iterations only)
+  if (A.stall && p.stall > 0)
+    for (int t = l; t < pk.ntraj; t += C) {
+      double *sb = A.stall + 3 * (size_t)stid[t];
+      sb[0] = sb[1] = 1e300;
+      sb[2] = 0.0;
+    }
 
   const bool inside = l < pk.nseg;
   int tb = 0;
@@ -406,12 +410,13 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
           int st = -1;
           if (!finite_d(rp) || !finite_d(rd)) st = 2;
           else if (p.eps > 0.0 && rp < tol && rd < tol) st = 0;
-          if (st < 0 && p.stall > 0 && p.eps > 0.0) {  // the stall rule (top_problem.stall_checks)
-            const bool bp = rp < 0.99 * sbest[2 * t], bd = rd < 0.99 * sbest[2 * t + 1];
-            if (bp) sbest[2 * t] = rp;
-            if (bd) sbest[2 * t + 1] = rd;
-            if (bp || bd) sstc[t] = 0;
-            else if (++sstc[t] >= p.stall) st = 3;
+          if (st < 0 && p.stall > 0 && p.eps > 0.0 && A.stall) {  // the stall rule (top_problem.stall_checks)
+            double *sb = A.stall + 3 * (size_t)bb;  // best ||r_p||, best ||r_d||, checks since
+            const bool bp = rp < 0.99 * sb[0], bd = rd < 0.99 * sb[1];
+            if (bp) sb[0] = rp;
+            if (bd) sb[1] = rd;
+            sb[2] = (bp || bd) ? 0.0 : sb[2] + 1.0;
+            if (sb[2] >= double(p.stall)) st = 3;
           }
           if (st >= 0) {
             sdone[t] = 1;

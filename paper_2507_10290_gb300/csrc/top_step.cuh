@@ -498,11 +498,14 @@ __device__ __forceinline__ R dot24(const R (&x)[AX][NC], const R (&y)[AX][NC]) {
   return acc;
 }
 
-// returns the L-BFGS iteration count; ch receives the minimiser, y is advanced
-template <class R>
+// returns the L-BFGS iteration count; ch receives the minimiser, y is advanced.
+// DEFER: only the start and its bound check, -1 where a bound is violated (the
+// caller hands the segment to the warp-cooperative solver); the L-BFGS code is
+// then not compiled into the caller, which keeps its register count low.
+template <class R, bool DEFER = false>
 __device__ int numeric_step(const SegConst<R> &sc, const R (&w)[AX][2][ND], R rho, bool first, bool last, R *yg,
                             int stride, const R *tabV, const R *tabA, int Mg, R vmax, R amax, int mem, int max_it,
-                            R tol, R (&ch)[AX][NC], bool defer = false) {
+                            R tol, R (&ch)[AX][NC]) {
   // start: minimiser of the quadratic part (the closed-form step without constraint rows)
   R rhs[AX][NC];
 #pragma unroll
@@ -541,8 +544,9 @@ __device__ int numeric_step(const SegConst<R> &sc, const R (&w)[AX][2][ND], R rh
       }
     }
     if (!violated) return 0;
-    if (defer) return -1;  // the caller hands the segment to the warp-cooperative solver
+    if constexpr (DEFER) return -1;
   }
+  if constexpr (DEFER) return -1;  // (not reached: keeps the L-BFGS code out of DEFER instances)
   R scale = dot24(rhs, ch);  // rhs^T G rhs: size of the linear term in the G metric
   if (!(scale > R(0))) scale = R(1);
   R g[AX][NC], gn[AX][NC], d[AX][NC], xn[AX][NC];

@@ -97,9 +97,13 @@ __global__ void stream_init(const StreamArgs A) {
   }
 }
 
+// F may carry kDeferNumeric with FAM_GEN: the numerical step's segments whose
+// bound is violated go to the work list of stream_numeric_warp (the warp form)
+constexpr int kDeferNumeric = 32;
 template <class R, int F>
 __global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
   constexpr bool BOX = (F & FAM_BOX) != 0, BALL = (F & FAM_BALL) != 0, VN = (F & FAM_VN) != 0;
+  constexpr bool DEFER = (F & kDeferNumeric) != 0;
   const DevProblem &p = A.p;
   extern __shared__ __align__(16) unsigned char smem[];
   const int Mb = BOX ? p.M_box : 0, Mq = BALL ? p.M_ball : 0, Mv = VN ? p.M_vn : 0;
@@ -155,10 +159,9 @@ __global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
       }
     R ch[AX][NC];
     if (GEN) {
-      const bool defer = A.nwork != nullptr;
-      const int its = numeric_step<R>(sc, w, rho, first, last, (R *)A.ygen + g, A.S, tabGV, tabGA, Mg,
-                                      R(p.gen_vmax[b]), R(p.gen_amax[b]), p.lbfgs_mem, p.lbfgs_max_iters,
-                                      R(p.lbfgs_tol), ch, defer);
+      const int its = numeric_step<R, DEFER>(sc, w, rho, first, last, (R *)A.ygen + g, A.S, tabGV, tabGA, Mg,
+                                             R(p.gen_vmax[b]), R(p.gen_amax[b]), p.lbfgs_mem, p.lbfgs_max_iters,
+                                             R(p.lbfgs_tol), ch);
       if (its < 0) {  // a violated bound: one warp per such segment solves it (stream_numeric_warp)
         A.work[atomicAdd(A.nwork, 1)] = x;
         continue;
@@ -526,6 +529,7 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
 #undef TOP_ST_CASE
     default: return (int)cudaErrorInvalidValue;
   }
+  if (fam == FAM_GEN && A.nwork) local = stream_local<R, FAM_GEN | kDeferNumeric>;  // the warp form
   init<<<blocks, threads, 0, st>>>(A);
   long long nl = 1;  // kernel launches, for the handle's count
   const int K = p.max_iters;

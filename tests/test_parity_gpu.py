@@ -368,3 +368,13 @@ def test_pin_with_box_rows_does_not_converge(T, precision):
     assert g["status"][0] == T.TOP_NOT_CONVERGED and g["iters"][0] == 3000
     assert np.all(np.isfinite(g["coeffs"])) and g["r_primal"][0] > 1.0
     compare(g, o, w, TOL[precision])
+
+
+def test_full_capacity_fits_shared_memory(T):
+    """The 512-segment resident CTA (FP32, no inequality rows, 128 trajectory
+    slots) fits the opt-in shared memory: the autotuner can time it."""
+    w = W.batch(B=32)
+    s = T.Solver(max_batch=w.B, max_segments=w.S, precision="fp32")
+    best, caps = s.autotune(w, iters=3)
+    s.close()
+    assert caps[512] > 0, caps
