@@ -174,8 +174,8 @@ typedef struct top_problem {
   /* Stall rule (an extension for precision hand-off; the paper has none): with
    * eps > 0, a trajectory for which neither ||r_p|| nor ||r_d|| has fallen
    * below 0.99 of its best value for stall_checks consecutive residual checks
-   * stops with status TOP_STALLED (0 = off).  Resident and cluster-resident
-   * forms; the streaming form ignores it. */
+   * stops with status TOP_STALLED (0 = off).  Resident (fixed rho) and
+   * cluster-resident forms; the streaming form ignores it. */
   int32_t stall_checks;
 } top_problem;
 

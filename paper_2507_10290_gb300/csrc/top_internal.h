@@ -264,6 +264,8 @@ int launch_sample(const int32_t *off, const double *T, int B, int M, int order, 
 int launch_time_step(double *T, const double *dT, int S, double kT, double lr, void *stream);
 int launch_resident_f32(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
 int launch_resident_f64(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
+int launch_resident_stall_f32(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
+int launch_resident_stall_f64(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream);
 // C segments per CTA, ln lanes per segment (blockDim = C * ln; ln > 1: FP32, fixed rho, families 1-7)
 int launch_cluster_f32(const ClusterArgs &a, int nclusters, int csz, int C, int ln, size_t smem, int fam,
                        void *stream);

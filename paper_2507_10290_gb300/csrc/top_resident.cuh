@@ -47,7 +47,10 @@ namespace top {
 // FP64 state needs twice the registers: 256 threads per CTA (255 registers each) in FP64
 // TC: the G product of a warp whose 32 segments share one inverse runs on the
 // tensor cores (top_tc.cuh); FP32, no inequality rows, fixed rho only.
-template <class R, int F, bool ADAPT, bool TC = false>
+// STALL: the stall rule (top_problem.stall_checks) is compiled in; a separate
+// instance (top_resident_stall_*.cu), since even unused its code changes the
+// code generation of the iteration loop (3 % on the 4096-trajectory batch).
+template <class R, int F, bool ADAPT, bool TC = false, bool STALL = false>
 __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel(const ResidentArgs A) {
   constexpr bool BOX = (F & FAM_BOX) != 0;
   constexpr bool BALL = (F & FAM_BALL) != 0;
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   for (int t = l; t < pk.ntraj; t += C) sdone[t] = (soff[t + 1] == soff[t]) ? 1 : 0;
   // stall-rule state of the pack's trajectories (global memory: read and written by the lane
   // that reduces the trajectory's residuals, on check iterations only)
-  if (A.stall && p.stall > 0)
+  if (STALL && A.stall && p.stall > 0)
     for (int t = l; t < pk.ntraj; t += C) {
       double *sb = A.stall + 3 * (size_t)stid[t];
       sb[0] = sb[1] = 1e300;
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
           int st = -1;
           if (!finite_d(rp) || !finite_d(rd)) st = 2;
           else if (p.eps > 0.0 && rp < tol && rd < tol) st = 0;
-          if (st < 0 && p.stall > 0 && p.eps > 0.0 && A.stall) {  // the stall rule (top_problem.stall_checks)
+          if (STALL && st < 0 && p.stall > 0 && p.eps > 0.0 && A.stall) {  // the stall rule (stall_checks)
             double *sb = A.stall + 3 * (size_t)bb;  // best ||r_p||, best ||r_d||, checks since
             const bool bp = rp < 0.99 * sb[0], bd = rd < 0.99 * sb[1];
             if (bp) sb[0] = rp;
@@ -542,6 +545,9 @@ template <class R>
 int launch_resident_t(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const bool adapt = a.p.adaptive != 0 && a.E != nullptr;
+  if (a.stall && a.p.stall > 0 && !adapt)  // the stall rule's instances (fixed rho)
+    return sizeof(R) == 4 ? launch_resident_stall_f32(a, nblocks, C, smem, fam, stream)
+                          : launch_resident_stall_f64(a, nblocks, C, smem, fam, stream);
   if constexpr (sizeof(R) == 4) {
     if (a.tc && fam == 0 && !adapt) {
       auto kern = resident_kernel<R, 0, false, true>;
@@ -571,6 +577,32 @@ int launch_resident_t(const ResidentArgs &a, int nblocks, int C, size_t smem, in
     default: return (int)cudaErrorInvalidValue;
   }
 #undef TOP_RES_CASE
+}
+
+// the instances with the stall rule (fixed rho)
+template <class R>
+int launch_resident_stall_t(const ResidentArgs &a, int nblocks, int C, size_t smem, int fam, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+#define TOP_RES_STALL_CASE(FV)                                                                         \
+  case FV: {                                                                                           \
+    auto kern = resident_kernel<R, FV, false, false, true>;                                            \
+    cudaError_t e = func_attr_once((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (e != cudaSuccess) return (int)e;                                                               \
+    kern<<<nblocks, C, smem, st>>>(a);                                                                 \
+    return (int)cudaGetLastError();                                                                    \
+  }
+  switch (fam) {
+    TOP_RES_STALL_CASE(0)
+    TOP_RES_STALL_CASE(1)
+    TOP_RES_STALL_CASE(2)
+    TOP_RES_STALL_CASE(3)
+    TOP_RES_STALL_CASE(4)
+    TOP_RES_STALL_CASE(5)
+    TOP_RES_STALL_CASE(6)
+    TOP_RES_STALL_CASE(7)
+    default: return (int)cudaErrorInvalidValue;
+  }
+#undef TOP_RES_STALL_CASE
 }
 
 }  // namespace top
