@@ -78,13 +78,14 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (arrival time, csv line)
+        self.window = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except FileNotFoundError:
@@ -93,7 +94,18 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def ready(self, timeout: float = 5.0):
+        """Wait until nvidia-smi has produced its first sample (its start-up takes a
+        while), so that the samples cover the region that follows."""
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+
+    def mark(self, t0: float, t1: float):
+        """The timed region, in time.perf_counter() seconds."""
+        self.window = (t0, t1)
 
     def __exit__(self, *a):
         if self.proc:
@@ -106,7 +118,12 @@ class ClockSampler:
     def summary(self):
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        lines = [l for t, l in self.lines]
+        if self.window:  # the samples that arrived inside the timed region (else the nearest after it)
+            inside = [l for t, l in self.lines if self.window[0] <= t <= self.window[1] + 0.05]
+            after = [l for t, l in self.lines if t > self.window[1]]
+            lines = inside if inside else after[:1]
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -269,6 +286,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches0 = top.top_launch_count(solver.handle)
     with ClockSampler(local) as clk:
+        clk.ready()
+        t_clk0 = time.perf_counter()
         for k in range(args.steps):
             flush.zero_()
             starts[k].record(stream)
@@ -279,6 +298,7 @@ def run_ours(args):
             res_ms.append(kt[1])
             cl_ms.append(kt[3])
         torch.cuda.synchronize()
+        clk.mark(t_clk0, time.perf_counter())
     launches = top.top_launch_count(solver.handle) - launches0  # the library's own kernels, timed steps
     top.top_set_profiling(solver.handle, False)
     if world > 1:

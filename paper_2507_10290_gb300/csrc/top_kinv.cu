@@ -109,6 +109,16 @@ __device__ __forceinline__ void add_rho_terms(const DevProblem &p, const double 
 
 // segment g's place in its trajectory and its powers s_r = T^-r; false for a
 // duration that is not positive and finite
+__device__ __forceinline__ bool segment_powers(const DevProblem &p, int g, double (&s)[NC]) {
+  const double T = p.durations[g];
+  if (!(T > 0.0) || !(T < 1e30)) return false;
+  const double it = 1.0 / T;
+  s[0] = 1.0;
+#pragma unroll
+  for (int r = 1; r < NC; ++r) s[r] = s[r - 1] * it;
+  return true;
+}
+
 __device__ __forceinline__ bool segment_setup(const DevProblem &p, int g, bool &first, bool &last,
                                               double (&s)[NC]) {
   const int b = find_traj(p.seg_offset, p.B, g);
@@ -188,7 +198,10 @@ __device__ __forceinline__ void store_inverse(const double (&A)[NG], const doubl
 // interior segment have the same local matrix (it depends on T, rho, the
 // sample counts and the end masks only).  kinv_mark_kernel marks them
 // copy[g] = that segment and lists every other segment in `list` (list[0] =
-// count, warp-aggregated appends, so a warp's entries stay in segment order);
+// count, warp-aggregated appends, so a warp's entries stay in segment order;
+// an entry is g with the segment's first / last flags in bits 30 / 31, so the
+// inversion kernel needs no search of the offsets; g < 2^30 since the host
+// keeps 108 S below 2^31);
 // kinv_kernel then inverts the listed segments only and kinv_copy_kernel
 // fills in the rest: a trajectory whose segments share one duration costs
 // three inversions instead of N.
@@ -198,18 +211,20 @@ __global__ void kinv_mark_kernel(const DevProblem p, int *__restrict__ copy, int
        w0 += (long long)gridDim.x * blockDim.x) {
     const int g = int(w0) + lane;
     bool rep = false;
+    unsigned entry = 0u;
     if (g < S) {
       const int b = find_traj(p.seg_offset, p.B, g);
       const int g0 = p.seg_offset[b], N = p.seg_offset[b + 1] - g0, i = g - g0;
       const bool same = i >= 2 && i <= N - 2 && p.durations[g] == p.durations[g0 + 1];
       copy[g] = same ? g0 + 1 : -1;
       rep = !same;
+      entry = unsigned(g) | (i == 0 ? 1u << 30 : 0u) | (i == N - 1 ? 1u << 31 : 0u);
     }
     const unsigned m = __ballot_sync(0xffffffffu, rep);
     int base = 0;
     if (lane == 0 && m) base = atomicAdd(list, __popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
-    if (rep) list[1 + base + __popc(m & ((1u << lane) - 1u))] = g;
+    if (rep) list[1 + base + __popc(m & ((1u << lane) - 1u))] = int(entry);
   }
 }
 
@@ -222,11 +237,12 @@ __global__ void __launch_bounds__(128) kinv_kernel(const DevProblem p, double rh
   const int n = list ? list[0] : S;
   if (!TOP_IN_BOUNDS(p.err, n >= 0 && n <= S)) return;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
-    const int g = list ? list[1 + x] : x;
+    const unsigned e = list ? unsigned(list[1 + x]) : 0u;
+    const int g = list ? int(e & 0x3fffffffu) : x;
     if (!TOP_IN_BOUNDS(p.err, g >= 0 && g < S)) continue;
-    bool first, last;
+    bool first = (e >> 30) & 1u, last = (e >> 31) & 1u;
     double s[NC];
-    if (!segment_setup(p, g, first, last, s)) {
+    if (!(list ? segment_powers(p, g, s) : segment_setup(p, g, first, last, s))) {
       atomicOr(err, 1);
       continue;
     }

@@ -186,3 +186,33 @@ def test_bad_rule_parameters_are_rejected(T):
         with pytest.raises(T.TopError) as e:
             s.solve(w.with_(**bad))
         assert e.value.code == T.TOP_E_INVAL
+
+
+def test_full_batch_adaptive_to_tolerance_sampled(T):
+    """The 4096-trajectory FREE batch with residual balancing run to eps = 1e-4
+    in FP32 (the benchmark's `full_adaptive` run), held at six sampled
+    trajectories (three short, three long) to the FP64 oracle run on those
+    trajectories alone.  Trajectories are independent (their rho, residual
+    sums and stop decisions are per trajectory, summed in an order fixed by
+    the trajectory's own segments), so each sample is the same problem in
+    both.  Near the threshold FP32 and FP64 may stop a few checks apart: both
+    must converge, within 25 % of each other's iteration count, to
+    coefficients that agree to the accuracy the stopping rule allows (1e-2
+    time-normalised; the converged FREE solutions are the same polynomial)."""
+    w = W.batch(seed=0).with_(mode="free", eps=1e-4, max_iters=30000, adaptive_rho=True)
+    s = T.Solver(max_batch=w.B, max_segments=w.S, precision="fp32", max_samples=0)
+    g = to_np(s.solve(w))
+    s.close()
+    Nb = np.diff(w.seg_offset)
+    ids = [int(b) for b in np.where(Nb <= 40)[0][:3]] + [int(b) for b in np.where(Nb >= 400)[0][:2]] + \
+        [int(b) for b in np.where((Nb >= 150) & (Nb < 250))[0][:1]]
+    assert (g["status"] == 0).sum() >= 4090
+    for b in ids:
+        o = oracle.solve(w.subset([b]))
+        assert int(o["status"][0]) == 0 and int(g["status"][b]) == 0, (b, o["status"], g["status"][b])
+        gi, oi = int(g["iters"][b]), int(o["iters"][0])
+        assert abs(gi - oi) <= 0.25 * oi, (b, gi, oi)
+        s0, s1 = int(w.seg_offset[b]), int(w.seg_offset[b + 1])
+        T_b = w.durations[s0:s1][:, None, None] ** np.arange(8)[None, None, :]
+        a, r = g["coeffs"][s0:s1] * T_b, o["coeffs"] * T_b
+        assert np.linalg.norm(a - r) <= 1e-2 * np.linalg.norm(r), (b, np.linalg.norm(a - r) / np.linalg.norm(r))
