@@ -123,7 +123,7 @@ constexpr int kClusterNtp = 8;  // res_layout's trajectory slots for the cluster
 struct ResLayout {
   size_t red_rp, red_rd, tr_rp, tr_rd;           // double arrays
   size_t p, m, zP, eS, dz, ybox, qball, qvn, tabB, tabQ, tabV, tabP, ch;  // element arrays
-  size_t off, done, tid, flag;                   // int arrays
+  size_t off, done, tid, flag, ndone;            // int arrays (ndone: trajectories of the pack stopped)
   size_t rho, fac;                               // double arrays (per trajectory)
   size_t total;
 };
@@ -165,6 +165,7 @@ __host__ __device__ inline ResLayout res_layout(int C, int ntp, int Mb, int Mq, 
   L.done = o;   o += sizeof(int) * ntp;
   L.tid = o;    o += sizeof(int) * ntp;
   L.flag = o;   o += sizeof(int);
+  L.ndone = o;  o += sizeof(int);
   o = align_up(o, 8);
   L.rho = o;    o += sizeof(double) * ntp;
   L.fac = o;    o += sizeof(double) * ntp;

@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   int *sdone = (int *)(smem + L.done);
   int *stid = (int *)(smem + L.tid);
   int *sflag = (int *)(smem + L.flag);
+  int *sndone = (int *)(smem + L.ndone);  // trajectories of the pack that have stopped
   double *srho = (double *)(smem + L.rho);  // per-trajectory rho (Eq. 22)
   double *sfac = (double *)(smem + L.fac);  // rho_old / rho_new of the last update
 
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   for (int t = l; t < ntp; t += C) {
     tr_rp[t] = 0.0; tr_rd[t] = 0.0; srho[t] = p.rho; sfac[t] = 1.0;
   }
-  if (l == 0) *sflag = 0;
+  if (l == 0) { *sflag = 0; *sndone = 0; }
   for (int q = l; q < NJ * J; q += C) { sdz[q] = R(0); sp[q] = R(0); }
   for (int q = l; q < NJ * ntp; q += C) sm[q] = R(0);
   for (int q = l; q < 24 * C; q += C) sch[q] = R(0);
@@ -129,7 +130,10 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
   __syncthreads();
   // the trajectories' segments fill the pack exactly (else the whole block ends)
   if (!TOP_IN_BOUNDS(p.err, soff[pk.ntraj] == pk.nseg)) return;
-  for (int t = l; t < pk.ntraj; t += C) sdone[t] = (soff[t + 1] == soff[t]) ? 1 : 0;
+  for (int t = l; t < pk.ntraj; t += C) {
+    sdone[t] = (soff[t + 1] == soff[t]) ? 1 : 0;
+    if (sdone[t]) atomicAdd(sndone, 1);
+  }
   // stall-rule state of the pack's trajectories (global memory: read and written by the lane
   // that reduces the trajectory's residuals, on check iterations only)
   if (STALL && A.stall && p.stall > 0)
@@ -423,6 +427,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
           }
           if (st >= 0) {
             sdone[t] = 1;
+            atomicAdd(sndone, 1);
             res.iters[bb] = k + 1;
             res.status[bb] = st;
           } else if (adapt) {
@@ -436,6 +441,8 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, 1) resident_kernel
         }
       }
       __syncthreads();
+      // every trajectory of the pack has stopped: the CTA leaves the loop and frees its SM
+      if (*sndone >= pk.ntraj) break;
       // ---- 5. after a change of rho: keep the unscaled duals, new local inverse ----
       if (adapt && *sflag && k + 1 < K) {
         if (valid && !sdone[tb] && sfac[tb] != 1.0) {

@@ -378,3 +378,14 @@ def test_full_capacity_fits_shared_memory(T):
     best, caps = s.autotune(w, iters=3)
     s.close()
     assert caps[512] > 0, caps
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_capacity_edges(T, precision):
+    """Lengths at the edges of a resident CTA (FP32 holds 512 segments, FP64
+    256): 255, 256, 257, 511, 512 and 513 segments with a single segment
+    between them, so each form boundary (resident, 2-CTA cluster) is crossed."""
+    w = W.tiny(seed=31, N=[255, 1, 256, 257, 511, 512, 513], mode="pin").with_(max_iters=40)
+    o = oracle.solve(w)
+    g = to_np(solver(T, precision).solve(w))
+    compare(g, o, w, TOL[precision])
