@@ -773,8 +773,7 @@ def speed_bound_comparison(top, oracle):
     line = {"suite": "speed bound: projection (Eq. 14, 18f-g) vs numerical step (Eq. 15-17)",
             "workload": f"speed_limit N={N}, M=16, FREE, v_max = 1.6 x end-to-end mean speed; numerical "
                         "step with the library's L-BFGS defaults (50 iterations, tol 1e-6 FP32 / 1e-12 FP64); "
-                        "numerical step one warp per segment in FP64, one thread per segment in FP32 "
-                        "(fp32_warp: the warp form in FP32)",
+                        "numerical step one warp per segment (fp32_thread: one thread per segment in FP32)",
             "segments": N, "to_tolerance": {"eps": eps, "cap": cap}}
     sols = {}
     for inner in ("closed", "numeric"):
@@ -783,7 +782,7 @@ def speed_bound_comparison(top, oracle):
         t0 = time.perf_counter()
         oracle.solve(w.with_(max_iters=20), lbfgs_tol=1e-12, lbfgs_max_iters=50)
         entry = {"oracle_ms_per_iteration_1_core": 1000 * (time.perf_counter() - t0) / 20}
-        forms = [("fp32", "auto"), ("fp64", "auto")] + ([("fp32", "warp")] if inner == "numeric" else [])
+        forms = [("fp32", "auto"), ("fp64", "auto")] + ([("fp32", "thread")] if inner == "numeric" else [])
         for prec, form in forms:
             s = top.Solver(max_batch=1, max_segments=N, precision=prec, max_samples=16, numeric_form=form)
             tensors = s.device_inputs(w)

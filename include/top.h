@@ -99,10 +99,10 @@ typedef struct top_config {
   int32_t numeric_form;   /* how the numerical local step (Sec. III-C.3) runs, enum top_numeric_form:
                              TOP_NUMERIC_WARP: a segment whose general bound is violated at the minimiser
                              of the quadratic part is solved by one warp (lanes over axis x coefficient and
-                             over the (sample, bound) pairs), at the price of one more launch per iteration;
-                             TOP_NUMERIC_THREAD: one thread per segment, no extra launch;
-                             TOP_NUMERIC_AUTO: WARP in FP64, THREAD in FP32.  Results agree within the
-                             L-BFGS tolerance, not bit for bit. */
+                             over the (sample, bound) pairs), at the price of one more (short) launch per
+                             iteration; TOP_NUMERIC_THREAD: one thread per segment, no extra launch;
+                             TOP_NUMERIC_AUTO: WARP.  Results agree within the L-BFGS tolerance, not bit
+                             for bit (identical where no bound is violated). */
   int32_t gemm_form;      /* enum top_gemm_form, for the product (D K D)^-1 rhs of the closed-form local
                              step (Eq. 18a) in the resident form: where all 32 segments of a warp share one
                              inverse (interior segments of one trajectory with one duration, Sec. III-D.1)

@@ -886,7 +886,7 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
       if (nb > 0 && (cap == 0 || nb > cap) && !(any_cluster && placement(nb) > 0)) ++n_stream_traj;
     }
   if (n_stream_traj > 0) {
-    int nl = 0, total = 0;
+    int nl = 0, total = 0, nchunk = 1;
     h->h_lt[0] = 0;  // h_lt = [lt_b (B) | lt_prefix (B+1)]
     int *lt_b = h->h_lt, *lt_pre = h->h_lt + h->cfg.max_batch;
     lt_pre[0] = 0;
@@ -896,6 +896,7 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
         lt_b[nl] = b;
         total += nb;
         lt_pre[++nl] = total;
+        nchunk = std::max(nchunk, (nb + kReduceChunk - 1) / kReduceChunk);
       }
     }
     const size_t rb = rbytes(h);
@@ -918,6 +919,7 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
     const size_t o_kc = take(sizeof(int) * nl);
     const size_t o_nw = take(sizeof(int) * (Mg > 0 ? (size_t)total + 1 : 1));
     const size_t o_lt = take(sizeof(int) * (2 * (size_t)nl + 1));
+    const size_t o_part = take(sizeof(double) * 2 * (size_t)nl * nchunk), o_tk = take(sizeof(int) * nl);
     if (o > h->stream_bytes) {
       cudaFree(h->d_stream);
       h->d_stream = nullptr;
@@ -948,10 +950,10 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
     sa.done = (int *)(base + o_done); sa.tr_rp = (double *)(base + o_trp); sa.tr_rd = (double *)(base + o_trd);
     sa.rho_t = (double *)(base + o_rho); sa.fac_t = (double *)(base + o_fac);
     sa.kcount = (int *)(base + o_kc); sa.cev = 1;
-    // segments with a violated general bound: one warp each (an extra launch per
-    // iteration, which only pays where bounds are active), or one thread each
-    const bool warp_num = Mg > 0 && (h->cfg.numeric_form == TOP_NUMERIC_WARP ||
-                                     (h->cfg.numeric_form == TOP_NUMERIC_AUTO && fp64));
+    sa.part = (double *)(base + o_part); sa.ticket = (int *)(base + o_tk); sa.nchunk = nchunk;
+    // segments with a violated general bound: one warp each (an extra, short
+    // launch per iteration; the default), or one thread each
+    const bool warp_num = Mg > 0 && h->cfg.numeric_form != TOP_NUMERIC_THREAD;
     sa.nwork = warp_num ? (int *)(base + o_nw) : nullptr;
     sa.work = warp_num ? (int *)(base + o_nw) + 1 : nullptr;
     sa.E = adapt ? h->E : nullptr;

@@ -181,6 +181,9 @@ __host__ __device__ inline ResLayout res_layout_resident(int C, int ntp, int Mb,
   return res_layout(C, ntp, Mb, Mq, Mv, rb, 0, true, tc);
 }
 
+// segments per block of the streaming residual sums (stream_reduce)
+constexpr int kReduceChunk = 2048;
+
 // Streaming form (trajectories longer than a resident CTA): state in global
 // memory.  Compact segment index x over the streaming trajectories:
 // lt_prefix[t] .. lt_prefix[t+1]-1 belong to trajectory lt_b[t].
@@ -211,6 +214,9 @@ struct StreamArgs {
   int *kcount;             // [nl] periodic residual evaluations so far (or null)
   int cev;                 // iterations between periodic evaluations
   int *nwork, *work;       // numerical step: count and compact indices of segments with a violated bound
+  double *part;            // [nl][nchunk][2] residual sums per chunk of kReduceChunk segments (or null)
+  int *ticket;             // [nl] chunks of the current evaluation summed so far (or null)
+  int nchunk;              // chunks of the longest streaming trajectory
   long long *launches;     // host counter of kernel launches (or null); never read on the device
 };
 

@@ -6,9 +6,10 @@
 //                    inverses), end derivatives to global memory
 //   stream_junction  every segment's end junction: consensus average, scaled
 //                    duals, primal-residual share, consensus change
-//   stream_reduce    on check iterations: dual-residual shares, then one block
-//                    per trajectory sums the shares in a fixed order, records
-//                    the history and applies the stopping rule
+//   stream_reduce    on check iterations: dual-residual shares, then blocks of
+//                    kReduceChunk segments sum the shares in a fixed order and
+//                    the last block of each trajectory adds the chunk sums,
+//                    records the history and applies the stopping rule
 //   stream_output    coefficients in the paper's basis and per-trajectory cost
 // Segments are addressed through a compact index x over the long
 // trajectories (lt_prefix[t] .. lt_prefix[t+1]-1 belong to trajectory lt_b[t]);
@@ -86,9 +87,11 @@ __global__ void stream_init(const StreamArgs A) {
       for (int q = 0; q < 2 * p.M_gen; ++q) ((R *)A.ygen)[(size_t)q * A.S + g] = R(0);
       if (A.inner_iters) A.inner_iters[g] = 0;
     }
+    if (x == 0 && A.nwork) *A.nwork = 0;  // the first iteration's work list starts empty
     if (first) {
       A.done[t] = 0;
       if (A.kcount) A.kcount[t] = 0;
+      if (A.ticket) A.ticket[t] = 0;
       A.tr_rp[t] = 0.0;
       A.tr_rd[t] = 0.0;
       A.rho_t[t] = p.rho;
@@ -218,6 +221,8 @@ __global__ void __launch_bounds__(256) stream_numeric_warp(const StreamArgs A) {
   const int Mg = p.M_gen;
   R *tabGV = (R *)smem, *tabGA = tabGV + 8 * Mg;
   R *wsc = tabGA + 8 * Mg + (threadIdx.x >> 5) * 96;  // this warp's [3][32] gradient scratch
+  const int n = *A.nwork;
+  if (blockIdx.x * (blockDim.x >> 5) >= n) return;  // no listed segment for this block (uniform in the block)
   fill_sample_table(tabGV, Mg, 1, threadIdx.x, blockDim.x);
   fill_accel_table(tabGA, Mg, threadIdx.x, blockDim.x);
   __syncthreads();
@@ -228,7 +233,6 @@ __global__ void __launch_bounds__(256) stream_numeric_warp(const StreamArgs A) {
   const int lane = threadIdx.x & 31, k = lane & 7, a = lane >> 3;
   const bool live = lane < 24;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int n = *A.nwork;
   for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < n; item += nwarps) {
     const int x = A.work[item];
     int t, b, i, N, g;
@@ -274,12 +278,17 @@ __global__ void __launch_bounds__(256) stream_numeric_warp(const StreamArgs A) {
   }
 }
 
+// Every junction value one axis needs is loaded before any of that axis's
+// updates is stored, so the loads of an axis are in flight together (a store
+// to z, uL or uRp would otherwise order the next row's loads behind it).
 template <class R>
 __global__ void __launch_bounds__(256) stream_junction(const StreamArgs A, int check) {
   const DevProblem &p = A.p;
   R *z = (R *)A.z, *uL = (R *)A.uL, *uRp = (R *)A.uRp, *dz = (R *)A.dz, *uR0 = (R *)A.uR0;
   const R *eS = (const R *)A.eS, *eE = (const R *)A.eE;
   const bool pin = p.mode == 0;
+  // stream_numeric_warp of this iteration has read its work list: the next local step starts a new one
+  if (A.nwork && blockIdx.x == 0 && threadIdx.x == 0) *A.nwork = 0;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < A.total; x += gridDim.x * blockDim.x) {
     int t, b, i, N, g;
     if (!stream_locate(A, x, t, b, i, N, g)) continue;
@@ -288,37 +297,48 @@ __global__ void __launch_bounds__(256) stream_junction(const StreamArgs A, int c
     const int jS = g + b, jE = g + b + 1;
     R rp2 = R(0);
 #pragma unroll
-    for (int a = 0; a < AX; ++a)
+    for (int a = 0; a < AX; ++a) {
+      R ee[ND], en[ND], zE[ND], uE[ND], es[PO], zS[PO], u0[PO];
+      R up = R(0);
 #pragma unroll
       for (int r = 0; r < ND; ++r) {
         const size_t row = (size_t)(a * ND + r) * A.Jn;
-        const R ee = eE[(size_t)(a * ND + r) * A.S + g];
+        ee[r] = eE[(size_t)(a * ND + r) * A.S + g];
+        en[r] = last ? R(0) : eS[(size_t)(a * ND + r) * A.S + g + 1];
+        zE[r] = (!last || r < PO) ? z[row + jE] : R(0);
+        uE[r] = (!last || r < PO) ? uL[row + jE] : R(0);
+        if (r < PO) {
+          es[r] = first ? eS[(size_t)(a * ND + r) * A.S + g] : R(0);
+          zS[r] = first ? z[row + jS] : R(0);
+          u0[r] = first ? uR0[(size_t)(a * PO + r) * p.B + b] : R(0);
+        }
+      }
+      if (pin && !last) up = uRp[(size_t)a * A.Jn + jE];
+#pragma unroll
+      for (int r = 0; r < ND; ++r) {
+        const size_t row = (size_t)(a * ND + r) * A.Jn;
         if (!last) {
-          const R en = eS[(size_t)(a * ND + r) * A.S + g + 1];
           if (check) {
-            const R gap = ee - en;
+            const R gap = ee[r] - en[r];
             rp2 += gap * gap;
           }
           if (pin && r == 0) {
-            const R P = z[row + jE];
-            uL[row + jE] += ee - P;
-            uRp[(size_t)a * A.Jn + jE] += en - P;
+            const R P = zE[r];
+            uL[row + jE] = uE[r] + (ee[r] - P);
+            uRp[(size_t)a * A.Jn + jE] = up + (en[r] - P);
             if (check) dz[row + jE] = R(0);
           } else {
-            const R zo = z[row + jE];
-            const R zn = R(0.5) * (ee + en);
-            uL[row + jE] += ee - zn;
+            const R zn = R(0.5) * (ee[r] + en[r]);
+            uL[row + jE] = uE[r] + (ee[r] - zn);
             z[row + jE] = zn;
-            if (check) dz[row + jE] = zn - zo;
+            if (check) dz[row + jE] = zn - zE[r];
           }
         } else if (r < PO) {
-          uL[row + jE] += ee - z[row + jE];
+          uL[row + jE] = uE[r] + (ee[r] - zE[r]);
         }
-        if (first && r < PO) {
-          const R es = eS[(size_t)(a * ND + r) * A.S + g];
-          uR0[(size_t)(a * PO + r) * p.B + b] += es - z[row + jS];
-        }
+        if (first && r < PO) uR0[(size_t)(a * PO + r) * p.B + b] = u0[r] + (es[r] - zS[r]);
       }
+    }
     if (check) A.rp2[x] = double(rp2);
   }
 }
@@ -356,25 +376,29 @@ __global__ void __launch_bounds__(256) stream_dual(const StreamArgs A) {
   }
 }
 
-// one block per streaming trajectory: fixed-order sums, history, stopping rule.
+// The residual sums of Eq. 19-20 for the streaming trajectories, in FP64 and
+// in a fixed order.  Block (t, c) sums chunk c (kReduceChunk segments) of
+// trajectory t and stores the two chunk sums; the block that completes the
+// trajectory's last chunk (an atomic ticket, no waiting) adds the chunk sums in
+// chunk order, records the history and applies the stopping rule (Eq. 21).
 // k >= 0: the iteration; k < 0: a periodic evaluation, the n-th of which (kept
 // per trajectory in kcount) falls on iteration (n + 1) cev - 1, so the same
 // launch serves every iteration of a recorded graph.
 template <class R>
 __global__ void __launch_bounds__(256) stream_reduce(const StreamArgs A, int k) {
   __shared__ double s1[256], s2[256];
-  const int t = blockIdx.x;
+  __shared__ int closing;
+  const int t = blockIdx.x, c = blockIdx.y;
   if (t >= A.nl || A.done[t]) return;
-  if (k < 0) {
-    k = (A.kcount[t] + 1) * A.cev - 1;
-    __syncthreads();  // every thread has k before thread 0 advances the count
-    if (threadIdx.x == 0) A.kcount[t] += 1;
-  }
   const int b = A.lt_b[t];
   const int x0 = A.lt_prefix[t], x1 = A.lt_prefix[t + 1];
   if (!TOP_IN_BOUNDS(A.p.err, b >= 0 && b < A.p.B && x0 >= 0 && x0 <= x1 && x1 <= A.total)) return;
+  const int nch = max(1, (x1 - x0 + kReduceChunk - 1) / kReduceChunk);
+  if (c >= nch) return;
+  if (!TOP_IN_BOUNDS(A.p.err, nch <= A.nchunk)) return;
+  const int c0 = x0 + c * kReduceChunk, c1 = min(x1, c0 + kReduceChunk);
   double a1 = 0.0, a2 = 0.0;
-  for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) { a1 += A.rp2[x]; a2 += A.rd2[x]; }
+  for (int x = c0 + threadIdx.x; x < c1; x += blockDim.x) { a1 += A.rp2[x]; a2 += A.rd2[x]; }
   s1[threadIdx.x] = a1;
   s2[threadIdx.x] = a2;
   __syncthreads();
@@ -383,26 +407,42 @@ __global__ void __launch_bounds__(256) stream_reduce(const StreamArgs A, int k) 
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double rp = sqrt(s1[0]), rd = sqrt(s2[0]);
-    A.tr_rp[t] = rp;
-    A.tr_rd[t] = rd;
-    if (A.r.history) {
-      A.r.history[((size_t)k * A.p.B + b) * 2 + 0] = rp;
-      A.r.history[((size_t)k * A.p.B + b) * 2 + 1] = rd;
-    }
-    const double tol = double(x1 - x0) * A.p.eps;
-    int st = -1;
-    if (!finite_d(rp) || !finite_d(rd)) st = 2;
-    else if (A.p.eps > 0.0 && rp < tol && rd < tol) st = 0;
-    if (st >= 0) {
-      A.done[t] = 1;
-      A.r.iters[b] = k + 1;
-      A.r.status[b] = st;
-    } else if (A.p.adaptive && A.E) {  // UpdateRho (Eq. 22)
-      const double ro = A.rho_t[t], rn = next_rho(A.p, ro, rp, rd);
-      A.fac_t[t] = ro / rn;
-      A.rho_t[t] = rn;
-    }
+    double *pt = A.part + ((size_t)t * A.nchunk + c) * 2;
+    pt[0] = s1[0];
+    pt[1] = s2[0];
+    __threadfence();  // the chunk sums are visible before the ticket is taken
+    closing = atomicAdd(&A.ticket[t], 1) == nch - 1;
+  }
+  __syncthreads();
+  if (!closing || threadIdx.x != 0) return;
+  __threadfence();
+  A.ticket[t] = 0;  // for the next evaluation
+  const volatile double *pt = A.part + (size_t)t * A.nchunk * 2;
+  double q1 = 0.0, q2 = 0.0;
+  for (int q = 0; q < nch; ++q) { q1 += pt[2 * q]; q2 += pt[2 * q + 1]; }
+  if (k < 0) {
+    k = (A.kcount[t] + 1) * A.cev - 1;
+    A.kcount[t] += 1;
+  }
+  const double rp = sqrt(q1), rd = sqrt(q2);
+  A.tr_rp[t] = rp;
+  A.tr_rd[t] = rd;
+  if (A.r.history) {
+    A.r.history[((size_t)k * A.p.B + b) * 2 + 0] = rp;
+    A.r.history[((size_t)k * A.p.B + b) * 2 + 1] = rd;
+  }
+  const double tol = double(x1 - x0) * A.p.eps;
+  int st = -1;
+  if (!finite_d(rp) || !finite_d(rd)) st = 2;
+  else if (A.p.eps > 0.0 && rp < tol && rd < tol) st = 0;
+  if (st >= 0) {
+    A.done[t] = 1;
+    A.r.iters[b] = k + 1;
+    A.r.status[b] = st;
+  } else if (A.p.adaptive && A.E) {  // UpdateRho (Eq. 22)
+    const double ro = A.rho_t[t], rn = next_rho(A.p, ro, rp, rd);
+    A.fac_t[t] = ro / rn;
+    A.rho_t[t] = rn;
   }
 }
 
@@ -475,16 +515,24 @@ __global__ void __launch_bounds__(256) stream_output(const StreamArgs A) {
   }
 }
 
+// per streaming trajectory: the cost (Eq. 4) summed like the residuals of
+// stream_reduce (chunk sums, then the closing block in chunk order), the last
+// residuals and the iteration count of a trajectory that did not stop
 template <class R>
 __global__ void __launch_bounds__(256) stream_finish(const StreamArgs A, int K) {
   __shared__ double s1[256];
-  const int t = blockIdx.x;
+  __shared__ int closing;
+  const int t = blockIdx.x, c = blockIdx.y;
   if (t >= A.nl) return;
   const int b = A.lt_b[t];
   const int x0 = A.lt_prefix[t], x1 = A.lt_prefix[t + 1];
   if (!TOP_IN_BOUNDS(A.p.err, b >= 0 && b < A.p.B && x0 >= 0 && x0 <= x1 && x1 <= A.total)) return;
+  const int nch = max(1, (x1 - x0 + kReduceChunk - 1) / kReduceChunk);
+  if (c >= nch) return;
+  if (!TOP_IN_BOUNDS(A.p.err, nch <= A.nchunk)) return;
+  const int c0 = x0 + c * kReduceChunk, c1 = min(x1, c0 + kReduceChunk);
   double a1 = 0.0;
-  for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) a1 += A.rp2[x];
+  for (int x = c0 + threadIdx.x; x < c1; x += blockDim.x) a1 += A.rp2[x];
   s1[threadIdx.x] = a1;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -492,14 +540,24 @@ __global__ void __launch_bounds__(256) stream_finish(const StreamArgs A, int K) 
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    A.r.cost[b] = s1[0];
-    A.r.r_primal[b] = A.tr_rp[t];
-    A.r.r_dual[b] = A.tr_rd[t];
-    if (A.r.rho) A.r.rho[b] = A.rho_t[t];
-    if (!A.done[t]) {
-      A.r.iters[b] = K;
-      A.r.status[b] = 1;
-    }
+    A.part[((size_t)t * A.nchunk + c) * 2] = s1[0];
+    __threadfence();
+    closing = atomicAdd(&A.ticket[t], 1) == nch - 1;
+  }
+  __syncthreads();
+  if (!closing || threadIdx.x != 0) return;
+  __threadfence();
+  A.ticket[t] = 0;
+  const volatile double *pt = A.part + (size_t)t * A.nchunk * 2;
+  double cost = 0.0;
+  for (int q = 0; q < nch; ++q) cost += pt[2 * q];
+  A.r.cost[b] = cost;
+  A.r.r_primal[b] = A.tr_rp[t];
+  A.r.r_dual[b] = A.tr_rd[t];
+  if (A.r.rho) A.r.rho[b] = A.rho_t[t];
+  if (!A.done[t]) {
+    A.r.iters[b] = K;
+    A.r.status[b] = 1;
   }
 }
 
@@ -541,19 +599,25 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
   // one iteration; `first` selects the Init-dependent local step, the
   // final iteration's evaluation names its k unless it is a periodic one
   const bool gen = (fam & FAM_GEN) != 0 && A.nwork;
-  int wblocks = (A.total + 7) / 8;  // 8 warps per block, one warp per deferred segment
-  if (wblocks > sm_count() * 16) wblocks = sm_count() * 16;
+  // the warp form's grid: as many blocks as are resident at once (8 warps each,
+  // the warps stride over the work list); the blocks past the list's length
+  // leave at once, so an iteration without violated bounds costs one short launch
+  const size_t wsmem = sizeof(R) * (16 * (size_t)p.M_gen + 8 * 96);
+  int wocc = 0;
+  if (gen && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wocc, stream_numeric_warp<R>, 256, wsmem) != cudaSuccess)
+    cudaGetLastError();
+  int wblocks = sm_count() * (wocc > 0 ? wocc : 1);
+  if (wblocks > (A.total + 7) / 8) wblocks = (A.total + 7) / 8;
   auto iteration = [&](cudaStream_t s, int k, bool first) {
     const bool per = periodic && ((k + 1) % cev == 0);
     const bool check = per || (k == K - 1);
-    if (gen) cudaMemsetAsync(Ak.nwork, 0, sizeof(int), s);
     local<<<blocks, threads, tab_bytes, s>>>(Ak, first ? 0 : 1);
-    if (gen) stream_numeric_warp<R><<<wblocks, 256, sizeof(R) * (16 * (size_t)p.M_gen + 8 * 96), s>>>(Ak);
+    if (gen) stream_numeric_warp<R><<<wblocks, 256, wsmem, s>>>(Ak);
     stream_junction<R><<<blocks, threads, 0, s>>>(Ak, check ? 1 : 0);
     nl += gen ? 3 : 2;
     if (check) {
       stream_dual<R><<<blocks, threads, 0, s>>>(Ak);
-      stream_reduce<R><<<Ak.nl, 256, 0, s>>>(Ak, per ? -1 : k);
+      stream_reduce<R><<<dim3(Ak.nl, Ak.nchunk), 256, 0, s>>>(Ak, per ? -1 : k);
       nl += 2;
     }
     if (adapt && k + 1 < K) {
@@ -600,7 +664,7 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
   }
   for (; k < K; ++k) iteration(st, k, false);
   stream_output<R><<<blocks, threads, 0, st>>>(A);
-  stream_finish<R><<<A.nl, 256, 0, st>>>(A, K);
+  stream_finish<R><<<dim3(A.nl, A.nchunk), 256, 0, st>>>(A, K);
   if (A.launches) *A.launches += nl + 2;
   return (int)cudaGetLastError();
 }

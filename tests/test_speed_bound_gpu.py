@@ -32,11 +32,11 @@ def test_each_path_against_the_oracle(T, precision, inner):
     compare(g, o, w, TOL[precision])
 
 
-@pytest.mark.parametrize("precision,form", [("fp32", "warp"), ("fp64", "thread")])
+@pytest.mark.parametrize("precision,form", [("fp32", "thread"), ("fp64", "thread"), ("fp32", "warp")])
 def test_numerical_step_in_the_other_form(T, precision, form):
-    """The warp-per-segment and thread-per-segment forms of the numerical
-    step (TOP_NUMERIC_WARP / TOP_NUMERIC_THREAD) in the precision whose default
-    is the other one, held to the oracle like the default forms."""
+    """The thread-per-segment form of the numerical step (TOP_NUMERIC_THREAD;
+    the default is one warp per segment) in both precisions, and the warp form
+    named explicitly, held to the oracle like the default form."""
     from test_parity_gpu import _solvers
     key = ("numeric-form", precision, form)
     if key not in _solvers:
