@@ -551,7 +551,55 @@ def time_to_tolerance(top, B, rank, world, eps=1e-4, cap=30000, fp64_B=256, pin_
                                       "max": float(rho.max())}
             res[f"{tag}_{prec}"] = entry
             s.close()
+    res["full_handoff"] = full_handoff(top, B, rank, world, eps, cap, check_every)
     return res
+
+
+def full_handoff(top, B, rank, world, eps, cap, check_every, stall=200):
+    """The FREE batch to eps through the FP32 -> FP64 hand-off: FP32 with the
+    stall rule (top_problem.stall_checks: a trajectory whose residuals have not
+    improved by 1 % on their own best in `stall` checks stops with
+    TOP_STALLED), its state saved, then FP64 from that state (top_resume) on
+    the whole batch; the trajectories FP32 brought to eps stop again at their
+    first FP64 check."""
+    import torch
+    w = W.batch(seed=rank, B=B).with_(mode="free", eps=eps, max_iters=cap)
+    Nb = np.diff(w.seg_offset)
+    s32 = top.Solver(max_batch=B, max_segments=w.S, precision="fp32", max_samples=0)
+    s64 = top.Solver(max_batch=B, max_segments=w.S, precision="fp64", max_samples=0)
+    t32, t64 = s32.device_inputs(w), s64.device_inputs(w)
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        r = fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    s32.resume(w, tensors=t32, max_iters=5)  # warm-up of both handles
+    s64.resume(w, tensors=t64, max_iters=5, save=False)
+    (a, state), ms32 = timed(lambda: s32.resume(w, tensors=t32, eps=eps, max_iters=cap, check_every=check_every,
+                                                 stall_checks=stall))
+    st32 = a["status"].cpu().numpy()
+    it32 = a["iters"].cpu().numpy()
+    (b, _), ms64 = timed(lambda: s64.resume(w, start=state, tensors=t64, eps=eps, max_iters=cap,
+                                            check_every=check_every, save=False))
+    st64 = b["status"].cpu().numpy()
+    it64 = b["iters"].cpu().numpy()
+    conv = int((st64 == 0).sum())
+    entry = {"trajectories": B, "segments": int(w.S), "stall_checks": stall, "check_every": check_every,
+             "fp32_ms": ms32, "fp32_converged": int((st32 == 0).sum()), "fp32_stalled": int((st32 == 3).sum()),
+             "fp32_mean_iterations": float(it32.mean()),
+             "fp64_ms": ms64, "fp64_mean_iterations": float(it64.mean()), "fp64_max_iterations": int(it64.max()),
+             "fp64_iterations_of_the_stalled": float(it64[st32 == 3].mean()) if (st32 == 3).any() else 0.0,
+             "ms": ms32 + ms64, "converged": conv, "trajectories_per_s": world * conv / ((ms32 + ms64) / 1000.0),
+             "segment_iterations_per_s_fp32": world * float(np.sum(Nb * it32)) / (ms32 / 1000.0)}
+    s32.close()
+    s64.close()
+    return entry
 
 
 def run_suite(args):
