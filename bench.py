@@ -765,6 +765,8 @@ def run_suite(args):
         gpu_case("batch with one duration per trajectory (64-trajectory subset for the oracle)",
                  W.batch(shared_T=True).subset(list(range(64))), precs=("fp32", "fp64"))
         shared_duration_line(top)
+    if want("batch_stream"):
+        batch_stream_line(top)
 
 
 def shared_duration_line(top):
@@ -989,6 +991,54 @@ def general_full_line(top, args):
         s.close()
 
 
+# the streaming form's algorithmic bytes per segment-iteration without inequality rows, FP32: reads z and u
+# at the two ends (42), the fixed start/end rows (3), the packed inverse (36) and T (1); writes the segment's
+# end values and coefficients as the next phase reads them (45)
+BATCH_STREAM_BYTES_PER_SEG_IT = 4 * (42 + 3 + 36 + 1 + 45)
+
+
+def batch_stream_line(top):
+    """The 4096-trajectory benchmark batch in the streaming form (schedule
+    "stream": every trajectory's state in global memory, one launch per
+    phase) beside the resident form, FP32, 300 iterations: time per
+    iteration, the streaming kernels against the HBM roofline, and the
+    difference of the two forms' coefficients."""
+    import torch
+    w = W.batch()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    line = {"suite": "batch 4096 in the streaming form (schedule stream) beside the resident form, FP32, "
+                     "300 iterations", "segments": int(w.S)}
+    coeffs = {}
+    for sched in ("auto", "stream"):
+        s = top.Solver(max_batch=w.B, max_segments=w.S, precision="fp32", max_samples=0, schedule=sched)
+        tensors = s.device_inputs(w)
+        out = s.alloc_result(w.B, w.S, w.max_iters)
+        s.solve(w, tensors=tensors, out=out, max_iters=5)
+        top.top_set_profiling(s.handle, True)
+        ms = [_timed_solve(s, w, tensors, out) for _ in range(3)]
+        kt = top.top_kernel_times(s.handle, 4)[1]
+        top.top_set_profiling(s.handle, False)
+        coeffs[sched] = out["coeffs"].cpu().numpy()
+        m = float(np.median(ms))
+        e = {"ms": m, "us_per_iteration": 1000 * m / w.max_iters,
+             "kernel_ms": {"precompute": kt[0], "resident": kt[1], "streaming": kt[2], "cluster": kt[3]},
+             "segment_iterations_per_s": w.S * w.max_iters / (m / 1000)}
+        if sched == "stream":
+            it_s = kt[2] / 1000 / w.max_iters
+            hbm = BATCH_STREAM_BYTES_PER_SEG_IT * w.S / it_s / 1e9
+            e["roofline"] = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": hbm / peaks["hbm_gbs"],
+                             "bytes_per_segment_iteration": BATCH_STREAM_BYTES_PER_SEG_IT}
+        line["resident" if sched == "auto" else "stream"] = e
+        s.close()
+    sc = np.asarray(w.durations)[:, None, None] ** np.arange(8)[None, None, :]
+    a, b = coeffs["stream"] * sc, coeffs["auto"] * sc
+    line["stream_vs_resident_coeff_rel_diff"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    print(json.dumps(line), flush=True)
+    torch.cuda.synchronize()
+
+
 KERNEL_SOURCES = ["top_resident.cuh", "top_step.cuh", "top_math.cuh", "top_internal.h"]
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "resident_kernel_batch512_fp32.md")
 
@@ -1030,7 +1080,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the top_grad measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep 512 segments per CTA (skip top_autotune)")
     ap.add_argument("--only", default="", help="with --suite: comma-separated subset of single_box, corridor, "
-                    "batch, adaptive, general, polytope, speed, segments, timealloc, grad, general_full, shared")
+                    "batch, adaptive, general, polytope, speed, segments, timealloc, grad, general_full, shared, "
+                    "batch_stream")
     ap.add_argument("--suite", action="store_true",
                     help="one JSON line per benchmark workload (single_box, corridor, batch, grad_batch, general)")
     ap.add_argument("--trajectories", type=int, default=4096,
