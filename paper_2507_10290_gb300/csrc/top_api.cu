@@ -920,6 +920,7 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
     const size_t o_nw = take(sizeof(int) * (Mg > 0 ? (size_t)total + 1 : 1));
     const size_t o_lt = take(sizeof(int) * (2 * (size_t)nl + 1));
     const size_t o_part = take(sizeof(double) * 2 * (size_t)nl * nchunk), o_tk = take(sizeof(int) * nl);
+    const size_t o_segt = take(sizeof(int) * (size_t)total);
     if (o > h->stream_bytes) {
       cudaFree(h->d_stream);
       h->d_stream = nullptr;
@@ -951,6 +952,8 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
     sa.rho_t = (double *)(base + o_rho); sa.fac_t = (double *)(base + o_fac);
     sa.kcount = (int *)(base + o_kc); sa.cev = 1;
     sa.part = (double *)(base + o_part); sa.ticket = (int *)(base + o_tk); sa.nchunk = nchunk;
+    // a few trajectories: the search over lt_prefix is as short as the map's extra load
+    sa.seg_t = nl > 4 ? (int *)(base + o_segt) : nullptr;
     // segments with a violated general bound: one warp each (an extra, short
     // launch per iteration; the default), or one thread each
     const bool warp_num = Mg > 0 && h->cfg.numeric_form != TOP_NUMERIC_THREAD;

@@ -195,6 +195,8 @@ struct StreamArgs {
   PolyData poly;           // polytope family (FAM_POLY), else null pointers
   const int *lt_b;         // [nl]
   const int *lt_prefix;    // [nl+1]
+  int *seg_t;              // [total] streaming trajectory of each compact index, filled by stream_map (or null:
+                           // the kernels search lt_prefix)
   int nl, total;           // trajectories, segments in the streaming set
   int S, Jn;               // global segments, global junctions (S + B)
   // state, element type = iteration type; junction arrays indexed like the waypoints

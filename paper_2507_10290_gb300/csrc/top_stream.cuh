@@ -28,18 +28,33 @@ namespace top {
 // false (checked build only) when the derived indices leave their arrays: the
 // caller then skips the segment
 __device__ __forceinline__ bool stream_locate(const StreamArgs &A, int x, int &t, int &b, int &i, int &N, int &g) {
-  int lo = 0, hi = A.nl - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (A.lt_prefix[mid] <= x) lo = mid; else hi = mid - 1;
+  if (A.seg_t) {  // one load instead of a search over the trajectories
+    t = A.seg_t[x];
+    if (!TOP_IN_BOUNDS(A.p.err, t >= 0 && t < A.nl)) return false;
+  } else {
+    int lo = 0, hi = A.nl - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (A.lt_prefix[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    t = lo;
   }
-  t = lo;
   b = A.lt_b[t];
   if (!TOP_IN_BOUNDS(A.p.err, b >= 0 && b < A.p.B)) return false;
   i = x - A.lt_prefix[t];
   N = A.lt_prefix[t + 1] - A.lt_prefix[t];
   g = A.p.seg_offset[b] + i;
   return TOP_IN_BOUNDS(A.p.err, i >= 0 && i < N && g >= 0 && g < A.S && g + b + 1 < A.Jn);
+}
+
+// the streaming trajectory of every compact index: block t fills trajectory t's range
+template <class R>
+__global__ void __launch_bounds__(256) stream_map(const StreamArgs A) {
+  for (int t = blockIdx.x; t < A.nl; t += gridDim.x) {
+    const int x0 = A.lt_prefix[t], x1 = A.lt_prefix[t + 1];
+    if (!TOP_IN_BOUNDS(A.p.err, x0 >= 0 && x0 <= x1 && x1 <= A.total)) continue;
+    for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) A.seg_t[x] = t;
+  }
 }
 
 template <class R, int F>
@@ -588,8 +603,12 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
     default: return (int)cudaErrorInvalidValue;
   }
   if (fam == FAM_GEN && A.nwork) local = stream_local<R, FAM_GEN | kDeferNumeric>;  // the warp form
-  init<<<blocks, threads, 0, st>>>(A);
   long long nl = 1;  // kernel launches, for the handle's count
+  if (A.seg_t) {
+    stream_map<R><<<A.nl < 65535 ? A.nl : 65535, 256, 0, st>>>(A);
+    nl += 1;
+  }
+  init<<<blocks, threads, 0, st>>>(A);
   const int K = p.max_iters;
   const bool adapt = p.adaptive && A.E;
   const int cev = adapt ? 1 : (p.check_every > 0 ? p.check_every : 1);
