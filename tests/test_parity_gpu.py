@@ -342,6 +342,52 @@ def test_general_bounds_long_trajectory(T, precision):
     compare(g, o, w, TOL[precision])
 
 
+@pytest.mark.parametrize("B,N", [(2, 4500), (6, 2300)])
+def test_streaming_sums_over_several_chunks(T, B, N):
+    """Streaming trajectories longer than one block of the residual sums
+    (2048 segments, FP64, residuals every 10 iterations): the residuals of
+    every evaluated iteration, the iteration at which the stopping rule
+    (Eq. 21) fires and the coefficients there agree with the oracle.  With six
+    streaming trajectories the kernels also find each segment's trajectory
+    through the per-solve map instead of the search."""
+    key = ("stream-chunks", B, N)
+    if key not in _solvers:
+        _solvers[key] = T.Solver(B, B * N, precision="fp64", max_samples=0, schedule="stream")
+    s = _solvers[key]
+    K, cev = 80, 10
+    w = W.batch(seed=3, B=B, fixed_N=N).with_(mode="free", max_iters=K)
+    o = oracle.solve(w, history=True)  # eps = 0: the residuals of every iteration
+    checks = np.arange(cev - 1, K, cev)
+    m = o["history"][:, :, :].max(axis=2)  # [K, B]: the larger residual
+    # a threshold that trajectory 0 first meets at a check inside the run
+    j = 1 + int(np.argmin(m[checks[1:-1], 0]))
+    assert m[checks[j], 0] < m[checks[:j], 0].min()
+    eps = m[checks[j], 0] * (1 + 1e-6) / N
+    expect_it = np.full(B, K)
+    expect_st = np.ones(B, np.int32)
+    for b in range(B):
+        hit = [k for k in checks if m[k, b] < N * eps]
+        if hit:
+            expect_it[b], expect_st[b] = hit[0] + 1, 0
+    assert expect_it[0] == checks[j] + 1 < K
+    g = to_np(s.solve(w.with_(eps=eps), history=True, check_every=cev))
+    assert np.array_equal(g["iters"], expect_it) and np.array_equal(g["status"], expect_st)
+    for b in range(B):
+        ks = [k for k in checks if k < expect_it[b]]
+        scale = np.abs(o["history"][ks, b]).max(axis=0)
+        assert np.all(np.abs(g["history"][ks, b] - o["history"][ks, b]) <= 1e-9 * scale)
+    # the coefficients where each trajectory stopped
+    for it in sorted(set(expect_it.tolist())):
+        sel = [b for b in range(B) if expect_it[b] == it]
+        ws = w.subset(sel).with_(max_iters=int(it))
+        os_ = oracle.solve(ws)
+        off = np.asarray(w.seg_offset)
+        gs = {"coeffs": np.concatenate([g["coeffs"][off[b]:off[b + 1]] for b in sel]),
+              "cost": g["cost"][sel], "r_primal": g["r_primal"][sel], "r_dual": g["r_dual"][sel],
+              "iters": os_["iters"], "status": os_["status"]}
+        compare(gs, os_, ws, TOL["fp64"])
+
+
 def test_large_host_memory_results_equal_device_results(T):
     """138,519 segments (26.6 MB of coefficients staged back to the host): the
     host-buffer call returns exactly what the device-buffer call does."""
