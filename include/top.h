@@ -79,6 +79,7 @@ enum top_memory    { TOP_MEM_DEVICE = 0, TOP_MEM_HOST = 1 };
 enum top_schedule  { TOP_SCHED_AUTO = 0, TOP_SCHED_RESIDENT = 1, TOP_SCHED_STREAM = 2 };
 enum top_numeric_form { TOP_NUMERIC_AUTO = 0, TOP_NUMERIC_WARP = 1, TOP_NUMERIC_THREAD = 2 };
 enum top_gemm_form { TOP_GEMM_CUDA_CORES = 0, TOP_GEMM_TENSOR = 1 };
+enum top_stream_form { TOP_STREAM_FUSED = 0, TOP_STREAM_PHASES = 1 };
 
 typedef struct top_handle top_handle;
 
@@ -110,7 +111,14 @@ typedef struct top_config {
                              with the operands split into high and low TF32 parts (FP32 accuracy);
                              TOP_FP32, no inequality rows and fixed rho only, elsewhere ignored.
                              TOP_GEMM_CUDA_CORES (the default) keeps every product on the FP32 pipe. */
-  int32_t reserved[7];    /* must be zero */
+  int32_t stream_form;    /* enum top_stream_form, for trajectories in the streaming form:
+                             TOP_STREAM_FUSED (the default): between two residual evaluations one launch
+                             per iteration applies the previous iteration's junction update (Eq. 18b-c)
+                             and then the local step, the junction state and the segments' end values
+                             alternating between two halves of the workspace;
+                             TOP_STREAM_PHASES: one launch per phase (local step, junction update).
+                             Both give the same results bit for bit. */
+  int32_t reserved[6];    /* must be zero */
 } top_config;
 
 /* One batch.  Pointers are device pointers for TOP_MEM_DEVICE and host

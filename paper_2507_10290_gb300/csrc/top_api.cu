@@ -404,7 +404,8 @@ int top_create(const top_config *cfg, top_handle **out) {
   if (cfg->schedule < TOP_SCHED_AUTO || cfg->schedule > TOP_SCHED_STREAM) return TOP_E_INVAL;
   if (cfg->numeric_form < TOP_NUMERIC_AUTO || cfg->numeric_form > TOP_NUMERIC_THREAD) return TOP_E_INVAL;
   if (cfg->gemm_form != TOP_GEMM_CUDA_CORES && cfg->gemm_form != TOP_GEMM_TENSOR) return TOP_E_INVAL;
-  for (int q = 0; q < 7; ++q)
+  if (cfg->stream_form != TOP_STREAM_FUSED && cfg->stream_form != TOP_STREAM_PHASES) return TOP_E_INVAL;
+  for (int q = 0; q < 6; ++q)
     if (cfg->reserved[q] != 0) return TOP_E_INVAL;
   top_handle *h = new (std::nothrow) top_handle;
   if (!h) return TOP_E_NOMEM;
@@ -917,7 +918,12 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
     const size_t o_done = take(sizeof(int) * nl), o_trp = take(sizeof(double) * nl), o_trd = take(sizeof(double) * nl);
     const size_t o_rho = take(sizeof(double) * nl), o_fac = take(sizeof(double) * nl);
     const size_t o_kc = take(sizeof(int) * nl);
-    const size_t o_nw = take(sizeof(int) * (Mg > 0 ? (size_t)total + 1 : 1));
+    const size_t o_nw = take(sizeof(int) * (Mg > 0 ? (size_t)total + 2 : 2));
+    // fused iterations: second halves of the junction state and of the end values
+    const bool fuse = h->cfg.stream_form == TOP_STREAM_FUSED;
+    const size_t o_zB = take(fuse ? rb * 21 * Jn : 0), o_uLB = take(fuse ? rb * 21 * Jn : 0);
+    const size_t o_uRpB = take(fuse ? rb * 3 * Jn : 0);
+    const size_t o_eSB = take(fuse ? rb * 21 * (size_t)S : 0), o_eEB = take(fuse ? rb * 21 * (size_t)S : 0);
     const size_t o_lt = take(sizeof(int) * (2 * (size_t)nl + 1));
     const size_t o_part = take(sizeof(double) * 2 * (size_t)nl * nchunk), o_tk = take(sizeof(int) * nl);
     const size_t o_segt = take(sizeof(int) * (size_t)total);
@@ -957,8 +963,12 @@ int solve_impl(top_handle *h, const top_problem *pb_in, top_result *res_in, cons
     // segments with a violated general bound: one warp each (an extra, short
     // launch per iteration; the default), or one thread each
     const bool warp_num = Mg > 0 && h->cfg.numeric_form != TOP_NUMERIC_THREAD;
-    sa.nwork = warp_num ? (int *)(base + o_nw) : nullptr;
-    sa.work = warp_num ? (int *)(base + o_nw) + 1 : nullptr;
+    sa.nwork = warp_num ? (int *)(base + o_nw) : nullptr;  // two counts, then the list
+    sa.work = warp_num ? (int *)(base + o_nw) + 2 : nullptr;
+    if (fuse) {
+      sa.zB = base + o_zB; sa.uLB = base + o_uLB; sa.uRpB = base + o_uRpB;
+      sa.eSB = base + o_eSB; sa.eEB = base + o_eEB;
+    }
     sa.E = adapt ? h->E : nullptr;
     sa.launches = &h->launches;
     Range r2("streaming trajectories");

@@ -216,6 +216,14 @@ struct StreamArgs {
   int *kcount;             // [nl] periodic residual evaluations so far (or null)
   int cev;                 // iterations between periodic evaluations
   int *nwork, *work;       // numerical step: count and compact indices of segments with a violated bound
+  // fused iterations (top_config.stream_form): the second halves of the junction state z, uL, uRp and of
+  // the end values eS, eE (null: one launch per phase); a fused local step reads the previous iteration's
+  // end values from eSp, eEp and the junction state from z, uL, uRp, and writes the state after the
+  // previous iteration's junction update to zn, uLn, uRpn
+  void *zB, *uLB, *uRpB, *eSB, *eEB;
+  void *zn, *uLn, *uRpn;
+  const void *eSp, *eEp;
+  int *nwork_next;         // fused iterations: the next iteration's work-list count, cleared by stream_numeric_warp
   double *part;            // [nl][nchunk][2] residual sums per chunk of kReduceChunk segments (or null)
   int *ticket;             // [nl] chunks of the current evaluation summed so far (or null)
   int nchunk;              // chunks of the longest streaming trajectory

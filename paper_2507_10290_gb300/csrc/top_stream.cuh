@@ -77,18 +77,31 @@ __global__ void stream_init(const StreamArgs A) {
           zv = R(p.end_state[((size_t)b * PO + r) * 3 + a]);
         }
         const size_t row = (size_t)(a * ND + r) * A.Jn;
+        const R zs = r < PO ? R(p.start_state[((size_t)b * PO + r) * 3 + a]) : R(0);
         z[row + jE] = zv;
         uL[row + jE] = R(0);
         dz[row + jE] = R(0);
         if (first) {
-          z[row + jS] = r < PO ? R(p.start_state[((size_t)b * PO + r) * 3 + a]) : R(0);
+          z[row + jS] = zs;
           uL[row + jS] = R(0);
           dz[row + jS] = R(0);
+        }
+        if (A.zB) {  // both halves: the rows no junction update writes stay valid in either
+          ((R *)A.zB)[row + jE] = zv;
+          ((R *)A.uLB)[row + jE] = R(0);
+          if (first) {
+            ((R *)A.zB)[row + jS] = zs;
+            ((R *)A.uLB)[row + jS] = R(0);
+          }
         }
       }
     for (int a = 0; a < 3; ++a) {
       uRp[(size_t)a * A.Jn + jE] = R(0);
       if (first) uRp[(size_t)a * A.Jn + jS] = R(0);
+      if (A.uRpB) {
+        ((R *)A.uRpB)[(size_t)a * A.Jn + jE] = R(0);
+        if (first) ((R *)A.uRpB)[(size_t)a * A.Jn + jS] = R(0);
+      }
     }
     if (first)
       for (int q = 0; q < 12; ++q) uR0[(size_t)q * p.B + b] = R(0);
@@ -102,7 +115,7 @@ __global__ void stream_init(const StreamArgs A) {
       for (int q = 0; q < 2 * p.M_gen; ++q) ((R *)A.ygen)[(size_t)q * A.S + g] = R(0);
       if (A.inner_iters) A.inner_iters[g] = 0;
     }
-    if (x == 0 && A.nwork) *A.nwork = 0;  // the first iteration's work list starts empty
+    if (x == 0 && A.nwork) A.nwork[0] = A.nwork[1] = 0;  // both work-list counts start at zero
     if (first) {
       A.done[t] = 0;
       if (A.kcount) A.kcount[t] = 0;
@@ -115,13 +128,96 @@ __global__ void stream_init(const StreamArgs A) {
   }
 }
 
+// The fused form's first half: the previous iteration's junction update
+// (Eq. 18b-c, the arithmetic of stream_junction) at both ends of segment g,
+// from the previous end values eSp, eEp and the junction state z, uL, uRp,
+// giving the local step's targets w = z - u at both ends.  The segment owns
+// its end junction and stores that junction's new state in zn, uLn, uRpn (and
+// the first segment its trajectory's start duals uR0, in place); its start
+// junction belongs to the previous segment, whose update it repeats in
+// registers with the same operands, so both see the same values.
+template <class R>
+__device__ __forceinline__ void fused_junctions(const StreamArgs &A, bool first, bool last, bool pin, int b, int g,
+                                                int jS, int jE, R (&w)[AX][2][ND]) {
+  const DevProblem &p = A.p;
+  const R *z = (const R *)A.z, *uL = (const R *)A.uL, *uRp = (const R *)A.uRp;
+  const R *eSp = (const R *)A.eSp, *eEp = (const R *)A.eEp;
+  R *zn = (R *)A.zn, *uLn = (R *)A.uLn, *uRpn = (R *)A.uRpn, *uR0 = (R *)A.uR0;
+#pragma unroll
+  for (int a = 0; a < AX; ++a) {
+    R em[ND], es[ND], ee[ND], en[ND], zS[ND], uS[ND], zE[ND], uE[ND];
+    R upS = R(0), upE = R(0);
+#pragma unroll
+    for (int r = 0; r < ND; ++r) {  // every load of the axis first
+      const size_t row = (size_t)(a * ND + r) * A.Jn, er = (size_t)(a * ND + r) * A.S;
+      em[r] = first ? R(0) : eEp[er + g - 1];
+      es[r] = eSp[er + g];
+      ee[r] = eEp[er + g];
+      en[r] = last ? R(0) : eSp[er + g + 1];
+      zS[r] = (!first || r < PO) ? z[row + jS] : R(0);
+      uS[r] = first ? (r < PO ? uR0[(size_t)(a * PO + r) * p.B + b] : R(0)) : uL[row + jS];
+      zE[r] = (!last || r < PO) ? z[row + jE] : R(0);
+      uE[r] = (!last || r < PO) ? uL[row + jE] : R(0);
+    }
+    if (pin && !first) upS = uRp[(size_t)a * A.Jn + jS];
+    if (pin && !last) upE = uRp[(size_t)a * A.Jn + jE];
+#pragma unroll
+    for (int r = 0; r < ND; ++r) {
+      const size_t row = (size_t)(a * ND + r) * A.Jn;
+      // end junction (owned): stream_junction's update, stored
+      if (!last) {
+        if (pin && r == 0) {
+          const R P = zE[r];
+          const R ul = uE[r] + (ee[r] - P);
+          uLn[row + jE] = ul;
+          uRpn[(size_t)a * A.Jn + jE] = upE + (en[r] - P);
+          w[a][1][r] = P - ul;
+        } else {
+          const R zm = R(0.5) * (ee[r] + en[r]);
+          const R ul = uE[r] + (ee[r] - zm);
+          uLn[row + jE] = ul;
+          zn[row + jE] = zm;
+          w[a][1][r] = zm - ul;
+        }
+      } else if (r < PO) {
+        const R ul = uE[r] + (ee[r] - zE[r]);
+        uLn[row + jE] = ul;
+        w[a][1][r] = zE[r] - ul;
+      } else {
+        w[a][1][r] = R(0);
+      }
+      // start junction: the trajectory's start (its duals uR0 kept in place) or the previous segment's end
+      if (first) {
+        if (r < PO) {
+          const R u0 = uS[r] + (es[r] - zS[r]);
+          uR0[(size_t)(a * PO + r) * p.B + b] = u0;
+          w[a][0][r] = zS[r] - u0;
+        } else {
+          w[a][0][r] = R(0);
+        }
+      } else if (pin && r == 0) {
+        const R P = zS[r];
+        w[a][0][r] = P - (upS + (es[r] - P));
+      } else {
+        const R zm = R(0.5) * (em[r] + es[r]);
+        const R ul = uS[r] + (em[r] - zm);
+        w[a][0][r] = zm - (-ul);
+      }
+    }
+  }
+}
+
 // F may carry kDeferNumeric with FAM_GEN: the numerical step's segments whose
-// bound is violated go to the work list of stream_numeric_warp (the warp form)
+// bound is violated go to the work list of stream_numeric_warp (the warp form);
+// with kFused the step begins with the previous iteration's junction update
+// (fused_junctions) instead of reading the state that stream_junction wrote
 constexpr int kDeferNumeric = 32;
+constexpr int kFused = 64;
 template <class R, int F>
-__global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
+__global__ void __launch_bounds__(256, ((F & kFused) && sizeof(R) == 4 && (!(F & FAM_GEN) || (F & kDeferNumeric))) ? 2 : 1)
+stream_local(const StreamArgs A, int k) {
   constexpr bool BOX = (F & FAM_BOX) != 0, BALL = (F & FAM_BALL) != 0, VN = (F & FAM_VN) != 0;
-  constexpr bool DEFER = (F & kDeferNumeric) != 0;
+  constexpr bool DEFER = (F & kDeferNumeric) != 0, FUSED = (F & kFused) != 0;
   const DevProblem &p = A.p;
   extern __shared__ __align__(16) unsigned char smem[];
   const int Mb = BOX ? p.M_box : 0, Mq = BALL ? p.M_ball : 0, Mv = VN ? p.M_vn : 0;
@@ -163,18 +259,22 @@ __global__ void __launch_bounds__(256) stream_local(const StreamArgs A, int k) {
     sc.brad = BALL ? R(p.ball_r[g]) : R(0);
     for (int a = 0; a < 3; ++a) sc.bo[a] = BALL ? R(p.ball_c[(size_t)g * 3 + a]) : R(0);
     R w[AX][2][ND];  // E (z~ - u) at both ends, unscaled
+    if (FUSED) {
+      fused_junctions<R>(A, first, last, pin, b, g, jS, jE, w);
+    } else {
 #pragma unroll
-    for (int a = 0; a < AX; ++a)
+      for (int a = 0; a < AX; ++a)
 #pragma unroll
-      for (int r = 0; r < ND; ++r) {
-        const size_t row = (size_t)(a * ND + r) * A.Jn;
-        R us;
-        if (first) us = (r < PO) ? uR0[(size_t)(a * PO + r) * p.B + b] : R(0);
-        else if (pin && r == 0) us = uRp[(size_t)a * A.Jn + jS];
-        else us = -uL[row + jS];
-        w[a][0][r] = (first && r >= PO) ? R(0) : z[row + jS] - us;
-        w[a][1][r] = (last && r >= PO) ? R(0) : z[row + jE] - uL[row + jE];
-      }
+        for (int r = 0; r < ND; ++r) {
+          const size_t row = (size_t)(a * ND + r) * A.Jn;
+          R us;
+          if (first) us = (r < PO) ? uR0[(size_t)(a * PO + r) * p.B + b] : R(0);
+          else if (pin && r == 0) us = uRp[(size_t)a * A.Jn + jS];
+          else us = -uL[row + jS];
+          w[a][0][r] = (first && r >= PO) ? R(0) : z[row + jS] - us;
+          w[a][1][r] = (last && r >= PO) ? R(0) : z[row + jE] - uL[row + jE];
+        }
+    }
     R ch[AX][NC];
     if (GEN) {
       const int its = numeric_step<R, DEFER>(sc, w, rho, first, last, (R *)A.ygen + g, A.S, tabGV, tabGA, Mg,
@@ -236,6 +336,8 @@ __global__ void __launch_bounds__(256) stream_numeric_warp(const StreamArgs A) {
   const int Mg = p.M_gen;
   R *tabGV = (R *)smem, *tabGA = tabGV + 8 * Mg;
   R *wsc = tabGA + 8 * Mg + (threadIdx.x >> 5) * 96;  // this warp's [3][32] gradient scratch
+  // fused iterations: the next iteration's local step appends to the other count, which nothing reads now
+  if (A.nwork_next && blockIdx.x == 0 && threadIdx.x == 0) *A.nwork_next = 0;
   const int n = *A.nwork;
   if (blockIdx.x * (blockDim.x >> 5) >= n) return;  // no listed segment for this block (uniform in the block)
   fill_sample_table(tabGV, Mg, 1, threadIdx.x, blockDim.x);
@@ -591,10 +693,14 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
   const size_t tab_bytes = sizeof(R) * 8 * (size_t)(Mb + Mq + Mv + 2 * Mg + Mp);
   void (*init)(const StreamArgs) = nullptr;
   void (*local)(const StreamArgs, int) = nullptr;
+  void (*fused)(const StreamArgs, int) = nullptr;
   void (*rescale)(const StreamArgs) = nullptr;
   switch (fam) {
-#define TOP_ST_CASE(FV) \
-  case FV: init = stream_init<R, FV>; local = stream_local<R, FV>; rescale = stream_rescale<R, FV>; break;
+#define TOP_ST_CASE(FV)                                                                               \
+  case FV:                                                                                            \
+    init = stream_init<R, FV>; local = stream_local<R, FV>; fused = stream_local<R, FV | kFused>;     \
+    rescale = stream_rescale<R, FV>;                                                                  \
+    break;
     TOP_ST_CASE(0) TOP_ST_CASE(1) TOP_ST_CASE(2) TOP_ST_CASE(3)
     TOP_ST_CASE(4) TOP_ST_CASE(5) TOP_ST_CASE(6) TOP_ST_CASE(7) TOP_ST_CASE(8)
     TOP_ST_CASE(16) TOP_ST_CASE(17) TOP_ST_CASE(18) TOP_ST_CASE(19)
@@ -602,7 +708,10 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
 #undef TOP_ST_CASE
     default: return (int)cudaErrorInvalidValue;
   }
-  if (fam == FAM_GEN && A.nwork) local = stream_local<R, FAM_GEN | kDeferNumeric>;  // the warp form
+  if (fam == FAM_GEN && A.nwork) {  // the warp form
+    local = stream_local<R, FAM_GEN | kDeferNumeric>;
+    fused = stream_local<R, FAM_GEN | kDeferNumeric | kFused>;
+  }
   long long nl = 1;  // kernel launches, for the handle's count
   if (A.seg_t) {
     stream_map<R><<<A.nl < 65535 ? A.nl : 65535, 256, 0, st>>>(A);
@@ -627,30 +736,67 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
     cudaGetLastError();
   int wblocks = sm_count() * (wocc > 0 ? wocc : 1);
   if (wblocks > (A.total + 7) / 8) wblocks = (A.total + 7) / 8;
+  // Fused iterations: the junction update of an iteration without a residual
+  // evaluation is applied at the start of the next iteration's local step
+  // (stream_local<..., kFused>), which reads the junction state from one half
+  // (ze) and the end values from one half (ee) and writes the other halves;
+  // the numerical step's work list alternates between two counts (wc), the
+  // one not in use cleared by stream_numeric_warp for the next iteration.
+  const bool fuse = A.zB && A.uLB && A.uRpB && A.eSB && A.eEB;
+  void *const Zh[2][3] = {{A.z, A.uL, A.uRp}, {A.zB, A.uLB, A.uRpB}};
+  void *const Eh[2][2] = {{A.eS, A.eE}, {A.eSB, A.eEB}};
+  int ze = 0, ee = 0, wc = 0;
+  auto halves = [&](int zh, int eh) {
+    StreamArgs a = Ak;
+    a.z = Zh[zh][0]; a.uL = Zh[zh][1]; a.uRp = Zh[zh][2];
+    a.eS = Eh[eh][0]; a.eE = Eh[eh][1];
+    if (fuse && gen) { a.nwork = A.nwork + wc; a.nwork_next = A.nwork + (wc ^ 1); }
+    return a;
+  };
   auto iteration = [&](cudaStream_t s, int k, bool first) {
     const bool per = periodic && ((k + 1) % cev == 0);
     const bool check = per || (k == K - 1);
-    local<<<blocks, threads, tab_bytes, s>>>(Ak, first ? 0 : 1);
-    if (gen) stream_numeric_warp<R><<<wblocks, 256, wsmem, s>>>(Ak);
-    stream_junction<R><<<blocks, threads, 0, s>>>(Ak, check ? 1 : 0);
-    nl += gen ? 3 : 2;
+    // the previous iteration's junction update is pending unless that iteration evaluated residuals
+    const bool pending = fuse && !first && !(periodic && k % cev == 0);
+    const int eo = fuse ? (ee ^ 1) : 0;
+    if (pending) {
+      StreamArgs a = halves(ze, eo);
+      a.zn = Zh[ze ^ 1][0]; a.uLn = Zh[ze ^ 1][1]; a.uRpn = Zh[ze ^ 1][2];
+      a.eSp = Eh[ee][0]; a.eEp = Eh[ee][1];
+      fused<<<blocks, threads, tab_bytes, s>>>(a, 1);
+      ze ^= 1;
+    } else {
+      local<<<blocks, threads, tab_bytes, s>>>(halves(ze, eo), first ? 0 : 1);
+    }
+    ee = eo;
+    const StreamArgs cur = halves(ze, ee);
+    if (gen) stream_numeric_warp<R><<<wblocks, 256, wsmem, s>>>(cur);
+    nl += gen ? 2 : 1;
+    if (check || !fuse) {
+      stream_junction<R><<<blocks, threads, 0, s>>>(cur, check ? 1 : 0);
+      nl += 1;
+    }
     if (check) {
-      stream_dual<R><<<blocks, threads, 0, s>>>(Ak);
-      stream_reduce<R><<<dim3(Ak.nl, Ak.nchunk), 256, 0, s>>>(Ak, per ? -1 : k);
+      stream_dual<R><<<blocks, threads, 0, s>>>(cur);
+      stream_reduce<R><<<dim3(Ak.nl, Ak.nchunk), 256, 0, s>>>(cur, per ? -1 : k);
       nl += 2;
     }
     if (adapt && k + 1 < K) {
-      rescale<<<blocks, threads, 0, s>>>(Ak);
+      rescale<<<blocks, threads, 0, s>>>(cur);
       nl += 1;
     }
+    if (fuse && gen) wc ^= 1;
   };
   int k = 0;
   if (K > 0) iteration(st, k++, true);
   // iterations 1 .. K-2 in blocks of G recorded once into a CUDA graph: the
   // launches of a block depend on the iteration only through the pattern of
   // evaluations, which repeats with period cev (G is a multiple of cev and
-  // every block starts at k = 1 mod cev)
-  const int G = cev * ((32 + cev - 1) / cev);
+  // every block starts at k = 1 mod cev); with fused iterations G is a
+  // multiple of 2 cev, so a block switches every half an even number of
+  // times and each replay starts from the halves it was recorded with
+  const int G = fuse ? 2 * cev * ((16 + cev - 1) / cev) : cev * ((32 + cev - 1) / cev);
+  const int ze0 = ze, ee0 = ee, wc0 = wc;
   const int nblk = K >= 2 ? (K - 2) / G : 0;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (nblk >= 2 && A.kcount && cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
@@ -678,6 +824,7 @@ int run_stream_t(const StreamArgs &A, int fam, void *stream) {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (cs) cudaStreamDestroy(cs);
+    ze = ze0; ee = ee0; wc = wc0;  // recording switched them an even number of times, or stopped part-way
     if (!ok) cudaGetLastError();  // no graph: the direct launches below do every iteration
     if (!launched) return (int)cudaErrorLaunchFailure;  // a partly run graph cannot be resumed
   }

@@ -58,13 +58,14 @@ TOP_MEM_DEVICE, TOP_MEM_HOST = 0, 1
 TOP_SCHED_AUTO, TOP_SCHED_RESIDENT, TOP_SCHED_STREAM = 0, 1, 2
 TOP_NUMERIC_AUTO, TOP_NUMERIC_WARP, TOP_NUMERIC_THREAD = 0, 1, 2
 TOP_GEMM_CUDA_CORES, TOP_GEMM_TENSOR = 0, 1
+TOP_STREAM_FUSED, TOP_STREAM_PHASES = 0, 1
 
 
 class top_config(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_batch", C.c_int32), ("max_segments", C.c_int32),
                 ("max_samples", C.c_int32), ("schedule", C.c_int32), ("segs_per_cta", C.c_int32),
                 ("ckpt_interval", C.c_int32), ("numeric_form", C.c_int32), ("gemm_form", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("stream_form", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class top_problem(C.Structure):
@@ -248,7 +249,7 @@ class Solver:
 
     def __init__(self, max_batch: int, max_segments: int, precision: str = "fp32", max_samples: int = 16,
                  schedule: str = "auto", segs_per_cta: int = 0, ckpt_interval: int = 10,
-                 numeric_form: str = "auto", gemm_form: str = "cuda_cores"):
+                 numeric_form: str = "auto", gemm_form: str = "cuda_cores", stream_form: str = "fused"):
         import torch  # device memory and streams only
         self.torch = torch
         cfg = top_config()
@@ -262,6 +263,7 @@ class Solver:
         cfg.numeric_form = {"auto": TOP_NUMERIC_AUTO, "warp": TOP_NUMERIC_WARP,
                             "thread": TOP_NUMERIC_THREAD}[numeric_form]
         cfg.gemm_form = {"cuda_cores": TOP_GEMM_CUDA_CORES, "tensor": TOP_GEMM_TENSOR}[gemm_form]
+        cfg.stream_form = {"fused": TOP_STREAM_FUSED, "phases": TOP_STREAM_PHASES}[stream_form]
         self.precision = precision
         rc, h = top_create(cfg)
         if rc != TOP_OK:

@@ -167,8 +167,11 @@ def test_graph_capture_replays_top_solve(T):
 def test_launch_count(T):
     """top_launch_count: a fixed-rho solve whose trajectories all fit one CTA
     launches fill (the final rho), mark, invert, copy and resident; a long one
-    adds one cluster launch; the streaming form launches at least its two
-    kernels (local step, junction) per iteration plus set-up and output."""
+    adds one cluster launch; the streaming form (three trajectories, 100
+    iterations, residuals on the last only) launches the four precompute
+    kernels, its set-up, one fused local step per iteration (two kernels per
+    iteration, local step and junction, with one launch per phase), the last
+    iteration's junction update and residual evaluation, and the output."""
     s = small_cta_solver(T, "fp32")
     w = W.tiny(seed=2, N=[5, 9, 40], mode="pin").with_(max_iters=30)
     c0 = T.top_launch_count(s.handle)
@@ -182,5 +185,11 @@ def test_launch_count(T):
     st = small_cta_solver(T, "fp32", schedule="stream")
     c0 = T.top_launch_count(st.handle)
     st.solve(w.with_(max_iters=100))
-    assert T.top_launch_count(st.handle) - c0 >= 2 * 100 + 3
+    assert T.top_launch_count(st.handle) - c0 == 4 + 1 + 100 + 3 + 2
+    sp = T.Solver(64, 20000, precision="fp32", max_samples=16, segs_per_cta=64, schedule="stream",
+                  stream_form="phases")
+    c0 = T.top_launch_count(sp.handle)
+    sp.solve(w.with_(max_iters=100))
+    assert T.top_launch_count(sp.handle) - c0 == 4 + 1 + 2 * 100 + 2 + 2
+    sp.close()
     assert T.top_launch_count(None) == -1
