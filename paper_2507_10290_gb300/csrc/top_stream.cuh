@@ -48,6 +48,7 @@ __device__ __forceinline__ bool stream_locate(const StreamArgs &A, int x, int &t
 }
 
 // the streaming trajectory of every compact index: block t fills trajectory t's range
+// (a template like the other kernels, so each precision's translation unit has its own instance)
 template <class R>
 __global__ void __launch_bounds__(256) stream_map(const StreamArgs A) {
   for (int t = blockIdx.x; t < A.nl; t += gridDim.x) {
