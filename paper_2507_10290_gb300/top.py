@@ -50,6 +50,7 @@ TOP_E_LIMIT = _K["TOP_E_LIMIT"]
 TOP_E_BOUNDS = _K["TOP_E_BOUNDS"]
 TOP_NOALLOC_MAX_SEGMENTS = _K["TOP_NOALLOC_MAX_SEGMENTS"]
 TOP_NOALLOC_MAX_BATCH = _K["TOP_NOALLOC_MAX_BATCH"]
+TOP_API_VERSION = _K["TOP_API_VERSION"]
 TOP_CONVERGED, TOP_NOT_CONVERGED, TOP_NONFINITE, TOP_STALLED = 0, 1, 2, 3
 TOP_FP32, TOP_FP64 = 0, 1
 TOP_PIN, TOP_FREE = 0, 1

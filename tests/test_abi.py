@@ -85,8 +85,26 @@ def test_create_rejects_bad_configs_without_touching_the_gpu(top):
     cfg.precision = 7
     assert top.top_create(cfg)[0] == top.TOP_E_INVAL
     cfg.precision = 0
+    cfg.stream_form = 2
+    assert top.top_create(cfg)[0] == top.TOP_E_INVAL
+    cfg.stream_form = 0
     cfg.reserved[3] = 1
     assert top.top_create(cfg)[0] == top.TOP_E_INVAL
+
+
+def test_binding_constants_match_the_header(top):
+    """Every #define TOP_* number and enumerator of include/top.h has the same
+    value in the Python binding."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    values = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(TOP_\w+)\s+\(?(-?\d+)\)?", src)}
+    for body in re.findall(r"enum\s+\w+\s*\{([^}]*)\}", src):
+        for name, val in re.findall(r"(TOP_\w+)\s*=\s*(-?\d+)", body):
+            values[name] = int(val)
+    assert len(values) > 30
+    missing = [n for n in values if not hasattr(top, n)]
+    assert not missing, missing
+    wrong = {n: (getattr(top, n), v) for n, v in values.items() if getattr(top, n) != v}
+    assert not wrong, wrong
 
 
 def test_product_package_does_not_reach_the_oracle():
